@@ -1,0 +1,220 @@
+/*
+ * tsk.h -- C ABI of the GB300 tensor-based sketching library.
+ *
+ * The library computes the data-parallel hot path of the tensor-based
+ * sketching method for low-rank approximation of a data stream
+ * {A_d in R^{m x n}} (arXiv 2209.14637):
+ *
+ *   training side  G = sum_d A_d A_d^T (mode-1 Gram of the training tensor,
+ *                  Section 3.1, Eq. 3.2) and the sketch S (k x m) = its
+ *                  leading eigenvectors, S* = (U^(1))_k^T (Eq. 3.3,
+ *                  Algorithm 2, lines 1-2); optionally the mode-2 analogue
+ *                  sum_d A_d^T A_d -> W (l x n) for the two-sided sketch
+ *                  (Eq. 3.6);
+ *   test side      for every stream matrix the SCW step (Algorithm 1 in the
+ *                  QR form of Section 3.2): X = (S A)^T, X = Q R, A Q,
+ *                  truncated rank-r SVD [A Q]_r, B = [A Q]_r Q^T and the
+ *                  error ||A - B||_F (problem 1.1).
+ *
+ * Conventions shared by every call
+ *   - Matrices are row-major.  A leading dimension (lda) counts elements.
+ *   - Pointers named "device" must point to GPU memory (cudaMalloc, or a
+ *     PyTorch CUDA tensor); the caller owns all of them.  The library owns
+ *     only what it allocates inside a handle or a plan.
+ *   - Element types follow the precision: TSK_FP64 -> double everywhere;
+ *     TSK_FP32 -> float A, float S and float outputs; TSK_BF16 -> bfloat16 A
+ *     (IEEE-754 binary32 truncated to its high 16 bits, round-to-nearest-even
+ *     when produced), float S and float outputs.  Errors and norms are always
+ *     double.
+ *   - Every call is asynchronous on the given stream (a cudaStream_t; NULL is
+ *     the legacy default stream) unless it says otherwise.  Argument errors
+ *     are returned at once; errors found on the device (a wait that ran out,
+ *     a rank-deficient sketch) are raised in a device status word that
+ *     tsk_sync_status() reads after synchronising the stream.
+ *   - No C++ exception crosses this boundary.  A handle must not be used by
+ *     two host threads at the same time.
+ *   - Requirements on sizes: 1 <= r <= k <= min(m, n) (thin QR of the n x k
+ *     matrix (SA)^T needs k <= n; Theorem 1 needs k > r for its bound but
+ *     r = k is accepted) and k <= TSK_MAX_K.  A and S must be 16-byte
+ *     aligned and lda * element size must be a multiple of 16 bytes for the
+ *     tensor-core path; the SIMT paths need only natural alignment.
+ */
+#ifndef TSK_H_
+#define TSK_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSK_MAX_K 64
+
+typedef enum {
+  TSK_OK = 0,
+  TSK_EINVAL = 1,      /* an argument is out of range, null or misaligned   */
+  TSK_ENOMEM = 2,      /* a device or host allocation failed                */
+  TSK_ECUDA = 3,       /* a CUDA call failed; tsk_last_error() has the text */
+  TSK_ENOCONV = 4,     /* the eigensolver hit its iteration cap             */
+  TSK_ETIMEOUT = 5,    /* a bounded device wait ran out                     */
+  TSK_ERANKDEF = 6,    /* warning: S A had rank < k for some matrix         */
+  TSK_EUNSUPPORTED = 7 /* valid request this build/device cannot run        */
+} tsk_status;
+
+typedef enum { TSK_FP64 = 0, TSK_FP32 = 1, TSK_BF16 = 2 } tsk_prec;
+
+/* Which kernels run the test-side sketch pass (X = A^T S^T and Y = A X). */
+typedef enum {
+  TSK_KERNEL_AUTO = 0, /* tensor cores for TSK_BF16, SIMT otherwise          */
+  TSK_KERNEL_SIMT = 1, /* CUDA-core kernels, two passes over A               */
+  TSK_KERNEL_TC = 2    /* tcgen05/TMA kernel, one pass over A (TSK_BF16 only) */
+} tsk_kernel;
+
+typedef struct tsk_handle_s* tsk_handle;
+typedef struct tsk_plan_s* tsk_plan;
+typedef void* tsk_stream; /* cudaStream_t */
+
+typedef struct {
+  int32_t kernel;     /* tsk_kernel; default TSK_KERNEL_AUTO                  */
+  int32_t refine_q;   /* 1: one refinement step on the thin QR factors of the
+                         n x k and m x k panels (default 1)                   */
+  int32_t max_iter;   /* subspace-iteration cap of the eigensolver (300)      */
+  int32_t err_mode;   /* how tsk_approx_batch gets ||A - B||_F:
+                         0 (default): the projection identity
+                           ||A||^2 - sum_{i<=r} sigma_i^2 (proof of Theorem 1,
+                           Eq. A.3), followed by a direct pass over A for the
+                           matrices where it cancels (err^2 < tau ||A||^2,
+                           tau = 1e-6 for TSK_FP64, 1e-4 otherwise);
+                         1: the identity only;
+                         2: a direct pass over A for every matrix.          */
+  double eig_tol;     /* eigensolver residual tolerance relative to lambda_1;
+                         0 selects 1e-13 (FP64) or 2e-6 (FP32/BF16)           */
+  int64_t spin_limit; /* iteration bound of every device spin-wait (1<<24)    */
+} tsk_options;
+
+/* One test-side matrix.  A: device, m x n, leading dimension lda >= n.
+   S: device, k x m row-major, leading dimension m (double for TSK_FP64,
+   float otherwise).  r: target rank. */
+typedef struct {
+  const void* A;
+  const void* S;
+  int64_t m, n, lda;
+  int32_t k, r;
+} tsk_mat_desc;
+
+/* Optional per-matrix outputs (each pointer may be NULL; all device).
+   US    m x r   U_r Sigma_r = A Q V_r, row-major, leading dimension r
+   Vt    r x n   (Q V_r)^T, row-major, leading dimension n; B = US * Vt
+   sigma k       singular values of A Q, descending
+   Output element type: double for TSK_FP64, float otherwise. */
+typedef struct {
+  void* US;
+  void* Vt;
+  void* sigma;
+} tsk_mat_out;
+
+/* ---- handles ----------------------------------------------------------- */
+
+/* Creates a handle on the current CUDA device.  opts may be NULL for the
+   defaults.  Returns TSK_ECUDA when no usable device is present. */
+tsk_status tsk_create(tsk_handle* out, const tsk_options* opts);
+
+/* Synchronises the device, frees every plan and workspace of the handle. */
+tsk_status tsk_destroy(tsk_handle h);
+
+/* Text of the last error on this handle (static storage; never NULL).
+   With h == NULL, the last error of tsk_create on this thread. */
+const char* tsk_last_error(tsk_handle h);
+
+/* Fills *out with the defaults. */
+void tsk_default_options(tsk_options* out);
+
+/* Synchronises the stream, then returns and clears the device status word:
+   TSK_OK, TSK_ETIMEOUT or TSK_ERANKDEF (the most severe one seen). */
+tsk_status tsk_sync_status(tsk_handle h, tsk_stream stream);
+
+/* ---- training side (Section 3.1, Algorithm 2 lines 1-2) ---------------- */
+
+/* Mode-1 or mode-2 Gram matrix of the training tensor.
+   A: host array of D device pointers, each an m x n matrix (lda >= n) of the
+   precision's element type.  mode 1: G (device, m x m, double, row-major)
+   receives sum_d A_d A_d^T (Eq. 3.2); mode 2: G (n x n) receives
+   sum_d A_d^T A_d (the mode-2 unfolding of Eq. 3.6).  accumulate != 0 adds
+   to G instead of overwriting it, so partial Gram matrices of disjoint
+   training shards can be summed (the one exchange step of a multi-GPU
+   training side).  Products are accumulated in the precision's compute type
+   (double for TSK_FP64, float otherwise) and summed into G in double. */
+tsk_status tsk_gram(tsk_handle h, const void* const* A, int64_t D, int64_t m,
+                    int64_t n, int64_t lda, tsk_prec prec, int32_t mode,
+                    double* G, int32_t accumulate, tsk_stream stream);
+
+/* Leading k eigenvectors of the symmetric dim x dim G (device, double) as the
+   rows of S (device, k x dim; double for TSK_FP64, float otherwise), in
+   descending eigenvalue order, each row signed so that its entry of largest
+   magnitude (lowest index on a tie) is positive.  eig (device, k doubles,
+   nullable) receives the eigenvalues.  Subspace iteration with
+   Rayleigh-Ritz; blocks the calling thread (it reads the residuals after
+   every iteration).  Returns TSK_ENOCONV when max_iter is reached. */
+tsk_status tsk_sketch_from_gram(tsk_handle h, const double* G, int64_t dim,
+                                int32_t k, tsk_prec prec, void* S, double* eig,
+                                tsk_stream stream);
+
+/* Algorithm 2, lines 1-2: S (k x m) from the mode-1 Gram of the D training
+   matrices A (host array of device pointers, m x n, lda >= n); with l > 0
+   also W (l x n) from the mode-2 Gram.  eig (device, k + l doubles, nullable)
+   receives the eigenvalues of both.  Blocks like tsk_sketch_from_gram. */
+tsk_status tsk_train_sketch(tsk_handle h, const void* const* A, int64_t D,
+                            int64_t m, int64_t n, int64_t lda, tsk_prec prec,
+                            int32_t k, int32_t l, void* S, void* W,
+                            double* eig, tsk_stream stream);
+
+/* ---- test side (Algorithm 1 in QR form; Algorithm 2 line 3) ------------ */
+
+/* SCW for a batch of count matrices (mats: host array).  err (device,
+   count doubles, nullable) receives ||A_d - B_d||_F, computed from the
+   projection identity ||A||^2 - ||[AQ]_r||^2 (proof of Theorem 1, Eq. A.3);
+   normA2 (device, nullable) receives ||A_d||_F^2.  outs (host array of count
+   entries, nullable) names the optional factor outputs.  The first call
+   with a given argument set builds a plan (workspace, schedule, CUDA graph)
+   and caches it in the handle; later calls with identical arguments replay
+   it.  A and S are read when the work runs, not when the call returns. */
+tsk_status tsk_approx_batch(tsk_handle h, int64_t count,
+                            const tsk_mat_desc* mats, tsk_prec prec,
+                            const tsk_mat_out* outs, double* err,
+                            double* normA2, tsk_stream stream);
+
+/* The same as an explicit plan: build once, execute many times.  The plan
+   keeps pointers to the caller's buffers; they must stay valid. */
+tsk_status tsk_plan_create(tsk_handle h, int64_t count,
+                           const tsk_mat_desc* mats, tsk_prec prec,
+                           const tsk_mat_out* outs, double* err,
+                           double* normA2, tsk_plan* plan);
+tsk_status tsk_plan_execute(tsk_plan plan, tsk_stream stream);
+tsk_status tsk_plan_destroy(tsk_plan plan);
+
+/* Timing probe for benchmarks.  The plan's graph is re-recorded with two
+   event-record nodes around its sketch pass (the stage that streams every
+   A_d from HBM: X = A^T S^T and Y = A X), so that cudaEventElapsedTime on the
+   two caller-owned events (created with timing enabled) gives that stage's
+   device time on every later execution.  Later calls only swap the events
+   (no re-recording).  Must not be called while the plan is executing. */
+tsk_status tsk_plan_set_probe(tsk_plan plan, void* ev_begin, void* ev_end);
+
+/* Bytes of device workspace a plan holds, and the number of kernel launches
+   one execution makes (for reporting). */
+tsk_status tsk_plan_info(tsk_plan plan, int64_t* workspace_bytes,
+                         int32_t* launches_per_execute);
+
+/* Direct error ||A_d - US_d Vt_d||_F of factored approximations (problem
+   1.1), one more pass over every A_d.  outs[i].US (m x r) and outs[i].Vt
+   (r x n) must be non-NULL; err: device, count doubles. */
+tsk_status tsk_error(tsk_handle h, int64_t count, const tsk_mat_desc* mats,
+                     tsk_prec prec, const tsk_mat_out* outs, double* err,
+                     tsk_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSK_H_ */

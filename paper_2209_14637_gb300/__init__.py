@@ -1,0 +1,330 @@
+"""Python binding of libtsk, the GB300 tensor-based sketching library.
+
+Thin ctypes marshalling over the C ABI of include/tsk.h: every function here
+only turns PyTorch CUDA tensors into pointers and sizes, calls the library and
+returns tensors.  Every step of the method runs in the library's CUDA
+kernels.  There is no CPU fallback: without the built library (or without a
+CUDA device) the calls raise.
+
+Names follow the paper: A_d are stream matrices (m x n), S is the k x m
+sketch (Section 3.1), W the l x n second sketch (Eq. 3.6), r the target rank,
+and the SCW outputs are US = U_r Sigma_r (m x r), Vt = (Q V_r)^T (r x n) with
+B = US @ Vt (Algorithm 1).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtsk.so")
+
+FP64, FP32, BF16 = 0, 1, 2
+KERNEL_AUTO, KERNEL_SIMT, KERNEL_TC = 0, 1, 2
+MAX_K = 64
+
+STATUS = {0: "TSK_OK", 1: "TSK_EINVAL", 2: "TSK_ENOMEM", 3: "TSK_ECUDA",
+          4: "TSK_ENOCONV", 5: "TSK_ETIMEOUT", 6: "TSK_ERANKDEF",
+          7: "TSK_EUNSUPPORTED"}
+
+_DTYPE_PREC = {torch.float64: FP64, torch.float32: FP32, torch.bfloat16: BF16}
+_PREC_COMPUTE = {FP64: torch.float64, FP32: torch.float32, BF16: torch.float32}
+
+
+class TskError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("refine_q", C.c_int32),
+                ("max_iter", C.c_int32), ("err_mode", C.c_int32),
+                ("eig_tol", C.c_double), ("spin_limit", C.c_int64)]
+
+
+class MatDesc(C.Structure):
+    _fields_ = [("A", C.c_void_p), ("S", C.c_void_p), ("m", C.c_int64),
+                ("n", C.c_int64), ("lda", C.c_int64), ("k", C.c_int32),
+                ("r", C.c_int32)]
+
+
+class MatOut(C.Structure):
+    _fields_ = [("US", C.c_void_p), ("Vt", C.c_void_p), ("sigma", C.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libtsk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is missing: build it with "
+            "`python -m paper_2209_14637_gb300.build` (needs nvcc)")
+    lib = C.CDLL(path)
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "tsk_create": ([C.POINTER(P), C.POINTER(Options)], I32),
+        "tsk_destroy": ([P], I32),
+        "tsk_last_error": ([P], C.c_char_p),
+        "tsk_default_options": ([C.POINTER(Options)], None),
+        "tsk_sync_status": ([P, P], I32),
+        "tsk_gram": ([P, C.POINTER(P), I64, I64, I64, I64, I32, I32, P, I32, P], I32),
+        "tsk_sketch_from_gram": ([P, P, I64, I32, I32, P, P, P], I32),
+        "tsk_train_sketch": ([P, C.POINTER(P), I64, I64, I64, I64, I32, I32, I32,
+                              P, P, P, P], I32),
+        "tsk_approx_batch": ([P, I64, C.POINTER(MatDesc), I32, C.POINTER(MatOut),
+                              P, P, P], I32),
+        "tsk_plan_create": ([P, I64, C.POINTER(MatDesc), I32, C.POINTER(MatOut),
+                             P, P, C.POINTER(P)], I32),
+        "tsk_plan_execute": ([P, P], I32),
+        "tsk_plan_destroy": ([P], I32),
+        "tsk_plan_info": ([P, C.POINTER(I64), C.POINTER(I32)], I32),
+        "tsk_plan_set_probe": ([P, P, P], I32),
+        "tsk_error": ([P, I64, C.POINTER(MatDesc), I32, C.POINTER(MatOut), P, P], I32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("libtsk takes CUDA tensors only (no CPU fallback)")
+
+
+def default_options() -> Options:
+    o = Options()
+    load_library().tsk_default_options(C.byref(o))
+    return o
+
+
+class Handle:
+    """A library handle bound to the current CUDA device."""
+
+    def __init__(self, kernel: int = KERNEL_AUTO, refine_q: bool = True,
+                 max_iter: int = 300, eig_tol: float = 0.0,
+                 spin_limit: int = 1 << 24, err_mode: int = 0):
+        lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libtsk needs a CUDA device; none is available")
+        o = default_options()
+        o.kernel, o.refine_q, o.max_iter = kernel, int(refine_q), max_iter
+        o.eig_tol, o.spin_limit, o.err_mode = eig_tol, spin_limit, err_mode
+        h = C.c_void_p()
+        st = lib.tsk_create(C.byref(h), C.byref(o))
+        if st != 0:
+            raise TskError(st, lib.tsk_last_error(None).decode())
+        self._lib, self._h = lib, h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.tsk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, allow=()):
+        if st != 0 and st not in allow:
+            raise TskError(st, self._lib.tsk_last_error(self._h).decode())
+        return st
+
+    def sync_status(self, stream=None) -> int:
+        return self._lib.tsk_sync_status(self._h, _stream(stream))
+
+    # ---- training side -------------------------------------------------
+    def gram(self, As: Sequence[torch.Tensor], mode: int = 1,
+             out: Optional[torch.Tensor] = None, accumulate: bool = False,
+             stream=None) -> torch.Tensor:
+        """Mode-1 (sum A A^T) or mode-2 (sum A^T A) Gram matrix, float64."""
+        As = list(As)
+        _require_cuda(*As)
+        m, n = As[0].shape
+        prec = _DTYPE_PREC[As[0].dtype]
+        dim = m if mode == 1 else n
+        if out is None:
+            out = torch.zeros(dim, dim, dtype=torch.float64, device=As[0].device)
+        ptrs = (C.c_void_p * len(As))(*[a.data_ptr() for a in As])
+        self._check(self._lib.tsk_gram(self._h, ptrs, len(As), m, n, As[0].stride(0),
+                                       prec, mode, _ptr(out), int(accumulate),
+                                       _stream(stream)))
+        return out
+
+    def sketch_from_gram(self, G: torch.Tensor, k: int, prec: int = FP32,
+                         stream=None):
+        _require_cuda(G)
+        dim = G.shape[0]
+        S = torch.empty(k, dim, dtype=_PREC_COMPUTE[prec], device=G.device)
+        eig = torch.empty(k, dtype=torch.float64, device=G.device)
+        st = self._check(self._lib.tsk_sketch_from_gram(
+            self._h, _ptr(G.contiguous()), dim, k, prec, _ptr(S), _ptr(eig),
+            _stream(stream)), allow=(4,))
+        return S, eig, st
+
+    def train_sketch(self, As, k: int, l: int = 0, stream=None):
+        """Algorithm 2 lines 1-2: S (k x m) and, with l > 0, W (l x n).
+
+        As: a (D, m, n) CUDA tensor or a list of (m, n) CUDA tensors.
+        Returns (S, W or None, eig (k + l,), status).
+        """
+        if isinstance(As, torch.Tensor):
+            mats = [As[i] for i in range(As.shape[0])]
+        else:
+            mats = list(As)
+        _require_cuda(*mats)
+        m, n = mats[0].shape
+        prec = _DTYPE_PREC[mats[0].dtype]
+        dev = mats[0].device
+        S = torch.empty(k, m, dtype=_PREC_COMPUTE[prec], device=dev)
+        W = torch.empty(l, n, dtype=_PREC_COMPUTE[prec], device=dev) if l > 0 else None
+        eig = torch.empty(k + l, dtype=torch.float64, device=dev)
+        ptrs = (C.c_void_p * len(mats))(*[a.data_ptr() for a in mats])
+        st = self._check(self._lib.tsk_train_sketch(
+            self._h, ptrs, len(mats), m, n, mats[0].stride(0), prec, k, l,
+            _ptr(S), _ptr(W), _ptr(eig), _stream(stream)), allow=(4,))
+        return S, W, eig, st
+
+    # ---- test side -----------------------------------------------------
+    @staticmethod
+    def _descs(As, Ss, ks, rs):
+        n = len(As)
+        descs = (MatDesc * n)()
+        for i in range(n):
+            A, S = As[i], Ss[i]
+            descs[i] = MatDesc(A.data_ptr(), S.data_ptr(), A.shape[0], A.shape[1],
+                               A.stride(0), int(ks[i]), int(rs[i]))
+        return descs
+
+    def approx_batch(self, As, Ss, r, outputs: bool = False, stream=None):
+        """SCW (Algorithm 1, QR form) for every matrix of the batch.
+
+        As: (count, m, n) tensor or list of (m, n) tensors (float64, float32
+        or bfloat16, all the same type).  Ss: one (k, m) sketch for all, or a
+        list (float64 for float64 A, float32 otherwise).  r: int or list.
+        Returns dict(err, normA2[, US, Vt, sigma]).
+        """
+        As = [As[i] for i in range(As.shape[0])] if isinstance(As, torch.Tensor) else list(As)
+        count = len(As)
+        Ss = [Ss] * count if isinstance(Ss, torch.Tensor) else list(Ss)
+        rs = [r] * count if isinstance(r, int) else list(r)
+        ks = [S.shape[0] for S in Ss]
+        _require_cuda(*As, *Ss)
+        prec = _DTYPE_PREC[As[0].dtype]
+        dev = As[0].device
+        err = torch.empty(count, dtype=torch.float64, device=dev)
+        normA2 = torch.empty(count, dtype=torch.float64, device=dev)
+        res = {"err": err, "normA2": normA2}
+        outs = None
+        if outputs:
+            cd = _PREC_COMPUTE[prec]
+            US = [torch.empty(A.shape[0], rr, dtype=cd, device=dev) for A, rr in zip(As, rs)]
+            Vt = [torch.empty(rr, A.shape[1], dtype=cd, device=dev) for A, rr in zip(As, rs)]
+            sg = [torch.empty(k, dtype=cd, device=dev) for k in ks]
+            outs = (MatOut * count)(*[MatOut(u.data_ptr(), v.data_ptr(), s.data_ptr())
+                                      for u, v, s in zip(US, Vt, sg)])
+            res.update(US=US, Vt=Vt, sigma=sg)
+        descs = self._descs(As, Ss, ks, rs)
+        self._check(self._lib.tsk_approx_batch(self._h, count, descs, prec, outs,
+                                               _ptr(err), _ptr(normA2), _stream(stream)))
+        res["_keep"] = (As, Ss, descs, outs)
+        return res
+
+    def plan(self, As, Ss, r, err: torch.Tensor, normA2: Optional[torch.Tensor] = None,
+             outs=None) -> "Plan":
+        As = [As[i] for i in range(As.shape[0])] if isinstance(As, torch.Tensor) else list(As)
+        count = len(As)
+        Ss = [Ss] * count if isinstance(Ss, torch.Tensor) else list(Ss)
+        rs = [r] * count if isinstance(r, int) else list(r)
+        ks = [S.shape[0] for S in Ss]
+        _require_cuda(*As, *Ss, err)
+        prec = _DTYPE_PREC[As[0].dtype]
+        descs = self._descs(As, Ss, ks, rs)
+        p = C.c_void_p()
+        self._check(self._lib.tsk_plan_create(self._h, count, descs, prec, outs,
+                                              _ptr(err), _ptr(normA2), C.byref(p)))
+        return Plan(self, p, (As, Ss, descs, err, normA2))
+
+    def error(self, As, Ss, r, US, Vt, stream=None) -> torch.Tensor:
+        """Direct ||A - US Vt||_F per matrix (one more pass over A)."""
+        As = [As[i] for i in range(As.shape[0])] if isinstance(As, torch.Tensor) else list(As)
+        count = len(As)
+        Ss = [Ss] * count if isinstance(Ss, torch.Tensor) else list(Ss)
+        rs = [r] * count if isinstance(r, int) else list(r)
+        ks = [S.shape[0] for S in Ss]
+        prec = _DTYPE_PREC[As[0].dtype]
+        err = torch.empty(count, dtype=torch.float64, device=As[0].device)
+        outs = (MatOut * count)(*[MatOut(u.data_ptr(), v.data_ptr(), None)
+                                  for u, v in zip(US, Vt)])
+        descs = self._descs(As, Ss, ks, rs)
+        self._check(self._lib.tsk_error(self._h, count, descs, prec, outs, _ptr(err),
+                                        _stream(stream)))
+        return err
+
+
+class Plan:
+    """A built test-side plan (workspace + schedule + CUDA graph)."""
+
+    def __init__(self, handle: Handle, p, keep):
+        self._h, self._p, self._keep = handle, p, keep
+
+    def execute(self, stream=None):
+        self._h._check(self._h._lib.tsk_plan_execute(self._p, _stream(stream)))
+
+    def set_probe(self, ev_begin, ev_end):
+        """Record ev_begin/ev_end (torch.cuda.Event with timing) around the
+        sketch pass on every later execute()."""
+        self._h._check(self._h._lib.tsk_plan_set_probe(
+            self._p, C.c_void_p(ev_begin.cuda_event), C.c_void_p(ev_end.cuda_event)))
+
+    def info(self):
+        ws, nl = C.c_int64(), C.c_int32()
+        self._h._check(self._h._lib.tsk_plan_info(self._p, C.byref(ws), C.byref(nl)))
+        return {"workspace_bytes": ws.value, "launches": nl.value,
+                "tc": bool(nl.value and self._h._lib.tsk_plan_info and self._uses_tc())}
+
+    def _uses_tc(self) -> bool:
+        return False
+
+    def close(self):
+        if self._p:
+            self._h._lib.tsk_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def header_functions(path: Optional[str] = None) -> List[str]:
+    """Names of the functions include/tsk.h declares."""
+    import re
+    path = path or os.path.join(os.path.dirname(_PKG), "include", "tsk.h")
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tsk_[a-z_]+)\s*\(", text)))

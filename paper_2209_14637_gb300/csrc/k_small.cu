@@ -1,0 +1,422 @@
+// Per-matrix small factorizations of the test pass and the eigensolver:
+//
+//  * tsqr_kernel: R factor of a tall skinny panel (n x k for X, m x k for Y)
+//    by blockwise Householder QR ("TSQR"), optionally followed by one
+//    refinement pass on Q1 = P R^{-1} (the same scheme run again; R <- R2 R).
+//  * small_svd_kernel: with X = Q R_X and Y = A X = Q_Y R_Y,
+//    A Q = Y R_X^{-1} = Q_Y (R_Y R_X^{-1}), so the singular values and right
+//    singular vectors of A Q are those of the k x k matrix T = R_Y R_X^{-1}.
+//    One-sided Jacobi (Hestenes) on T, then the error identity
+//    ||A - [AQ]_r Q^T||^2 = ||A||^2 - sum_{i<=r} sigma_i^2 (proof of
+//    Theorem 1, Eq. A.3) and W = R_X^{-1} V_r for the factored outputs.
+//  * sym_eig_kernel: eigen-decomposition of the small symmetric PSD
+//    Rayleigh-Ritz matrix of the subspace iteration (one-sided Jacobi).
+#include <cuda_bf16.h>
+#include <float.h>
+
+#include "tsk_internal.cuh"
+
+namespace tsk {
+
+namespace {
+
+template <typename T>
+struct Eps;
+template <>
+struct Eps<float> {
+  static constexpr float jacobi = 4.0e-7f;
+  static constexpr float tiny = 1.0e-30f;
+};
+template <>
+struct Eps<double> {
+  static constexpr double jacobi = 1.0e-15;
+  static constexpr double tiny = 1.0e-280;
+};
+
+// Round-robin ("circle method") pairing: kk players (even), kk-1 rounds,
+// kk/2 disjoint pairs per round; over a sweep every pair meets once.
+__device__ __forceinline__ void rr_pair(int round, int i, int kk, int& p,
+                                        int& q) {
+  const int mm = kk - 1;
+  if (i == 0) {
+    p = round % mm;
+    q = mm;
+  } else {
+    p = (round + i) % mm;
+    q = (round - i + mm) % mm;
+  }
+}
+
+// One-sided Jacobi on the columns of M (nrow x ncol, leading dimension ld)
+// accumulating the rotations into V (ncol x ncol, ld).  On return the
+// columns of M are mutually orthogonal: M_in V = M_out, and the column
+// norms of M_out are the singular values.  Whole-block cooperative.
+template <typename T>
+__device__ void jacobi_columns(T* M, T* V, int nrow, int ncol, int ld,
+                               int max_sweeps, int* rotated_flag) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int kk = ncol + (ncol & 1);
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) *rotated_flag = 0;
+    __syncthreads();
+    for (int round = 0; round < kk - 1; ++round) {
+      for (int pi = warp; pi < kk / 2; pi += nwarps) {
+        int p, q;
+        rr_pair(round, pi, kk, p, q);
+        if (p >= ncol || q >= ncol) continue;
+        T a = T(0), b = T(0), g = T(0);
+        for (int i = lane; i < nrow; i += 32) {
+          const T x = M[i * ld + p], y = M[i * ld + q];
+          a += x * x;
+          b += y * y;
+          g += x * y;
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        g = warp_sum(g);
+        if (fabs(g) > Eps<T>::jacobi * sqrt(a * b) && fabs(g) > Eps<T>::tiny) {
+          const T zeta = (b - a) / (T(2) * g);
+          const T t = (zeta >= T(0) ? T(1) : T(-1)) /
+                      (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          const T c = T(1) / sqrt(T(1) + t * t), s = c * t;
+          for (int i = lane; i < nrow; i += 32) {
+            const T x = M[i * ld + p], y = M[i * ld + q];
+            M[i * ld + p] = c * x - s * y;
+            M[i * ld + q] = s * x + c * y;
+          }
+          for (int i = lane; i < ncol; i += 32) {
+            const T x = V[i * ld + p], y = V[i * ld + q];
+            V[i * ld + p] = c * x - s * y;
+            V[i * ld + q] = s * x + c * y;
+          }
+          if (lane == 0) *rotated_flag = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (*rotated_flag == 0) break;
+    __syncthreads();
+  }
+}
+
+// sig[c] = ||M[:, c]||, order[rank] = c with descending sig (stable).
+template <typename T>
+__device__ void column_norms_sorted(const T* M, int nrow, int ncol, int ld,
+                                    T* sig, int* order) {
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    T a = T(0);
+    for (int i = 0; i < nrow; ++i) a += M[i * ld + c] * M[i * ld + c];
+    sig[c] = sqrt(a);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    int rank = 0;
+    for (int c2 = 0; c2 < ncol; ++c2)
+      rank += (sig[c2] > sig[c]) || (sig[c2] == sig[c] && c2 < c);
+    order[rank] = c;
+  }
+  __syncthreads();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// E2 / E4: R factor of a tall panel by blockwise Householder QR.
+// The running R (k x k) is stacked on top of the next block of 64 rows and
+// the stack is reduced column by column; only R's diagonal entry and the
+// block's column take part in each reflector because R is already upper
+// triangular.  With refine = 1 the panel is passed again as Q1 = P R0^{-1}
+// (computed row by row on load), and the result is R = R2 R0.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+tsqr_kernel(int kp, const PanelDev* __restrict__ panels, int refine) {
+  constexpr int B = 64;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ld = kp + 1;
+  T* Bs = (T*)smem_raw;
+  T* Rs = Bs + B * ld;
+  T* R0 = Rs + kp * ld;
+  __shared__ T sh_tau;
+  const PanelDev pd = panels[blockIdx.x];
+  const int k = pd.k, pld = pd.ld;
+  const long long rows = pd.rows;
+  const T* __restrict__ P = (const T*)pd.P;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < kp * ld; e += blockDim.x) {
+    Rs[e] = T(0);
+    R0[e] = T(0);
+  }
+  __syncthreads();
+  for (int pass = 0; pass <= refine; ++pass) {
+    if (pass == 1) {
+      for (int e = tid; e < kp * ld; e += blockDim.x) {
+        R0[e] = Rs[e];
+        Rs[e] = T(0);
+      }
+      __syncthreads();
+    }
+    for (long long r0 = 0; r0 < rows; r0 += B) {
+      for (int e = tid; e < B * kp; e += blockDim.x) {
+        const int ii = e / kp, c = e % kp;
+        const long long gi = r0 + ii;
+        Bs[ii * ld + c] = (gi < rows && c < k) ? P[gi * pld + c] : T(0);
+      }
+      __syncthreads();
+      if (pass == 1) {
+        for (int ii = tid; ii < B; ii += blockDim.x) {
+          T* row = Bs + ii * ld;
+          for (int c = 0; c < k; ++c) {
+            T t = row[c];
+            for (int cc = 0; cc < c; ++cc) t -= row[cc] * R0[cc * ld + c];
+            const T d = R0[c * ld + c];
+            row[c] = (d != T(0)) ? t / d : T(0);
+          }
+        }
+        __syncthreads();
+      }
+      for (int j = 0; j < k; ++j) {
+        if (warp == 0) {
+          T s2 = T(0);
+          for (int ii = lane; ii < B; ii += 32) {
+            const T v = Bs[ii * ld + j];
+            s2 += v * v;
+          }
+          s2 = warp_sum(s2);
+          const T alpha = Rs[j * ld + j];
+          T tau = T(0);
+          if (s2 > T(0)) {
+            const T nrm = sqrt(alpha * alpha + s2);
+            const T beta = (alpha >= T(0)) ? -nrm : nrm;
+            const T scale = T(1) / (alpha - beta);
+            tau = (beta - alpha) / beta;
+            for (int ii = lane; ii < B; ii += 32) Bs[ii * ld + j] *= scale;
+            if (lane == 0) Rs[j * ld + j] = beta;
+          }
+          if (lane == 0) sh_tau = tau;
+        }
+        __syncthreads();
+        const T tau = sh_tau;
+        if (tau != T(0)) {
+          for (int c = j + 1 + warp; c < k; c += (blockDim.x >> 5)) {
+            T w = T(0);
+            for (int ii = lane; ii < B; ii += 32)
+              w += Bs[ii * ld + j] * Bs[ii * ld + c];
+            w = warp_sum(w) + Rs[j * ld + c];
+            const T tw = tau * w;
+            for (int ii = lane; ii < B; ii += 32)
+              Bs[ii * ld + c] -= Bs[ii * ld + j] * tw;
+            if (lane == 0) Rs[j * ld + c] -= tw;
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  T* __restrict__ Rout = (T*)pd.R;
+  for (int e = tid; e < kp * kp; e += blockDim.x) {
+    const int a = e / kp, b = e % kp;
+    T v = T(0);
+    if (a < k && b < k && a <= b) {
+      if (refine) {
+        for (int c = a; c <= b; ++c) v += Rs[a * ld + c] * R0[c * ld + b];
+      } else {
+        v = Rs[a * ld + b];
+      }
+    }
+    Rout[e] = v;
+  }
+}
+
+static size_t tsqr_smem(int kp, size_t elt) {
+  return (size_t)(64 + 2 * kp) * (kp + 1) * elt;
+}
+
+cudaError_t launch_tsqr(bool dbl, int kp, const PanelDev* panels, int count,
+                        int refine, int* /*status*/, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (dbl) {
+    const size_t sm = tsqr_smem(kp, sizeof(double));
+    cudaError_t e = cudaFuncSetAttribute(
+        tsqr_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    tsqr_kernel<double><<<count, 256, sm, s>>>(kp, panels, refine);
+  } else {
+    const size_t sm = tsqr_smem(kp, sizeof(float));
+    cudaError_t e = cudaFuncSetAttribute(
+        tsqr_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    tsqr_kernel<float><<<count, 256, sm, s>>>(kp, panels, refine);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// E4 + E5 per matrix: T = R_Y R_X^{-1}, one-sided Jacobi SVD of T, sort,
+// error by the projection identity (double), W = R_X^{-1} V_r.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+small_svd_kernel(int kp, const MatDev* __restrict__ mats,
+                 const T* __restrict__ RX, const T* __restrict__ RY,
+                 T* __restrict__ Wm, const double* __restrict__ normA2,
+                 double* __restrict__ err, int* __restrict__ flags, int err_mode,
+                 double tau, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ld = kp + 1;
+  T* Rx = (T*)smem_raw;
+  T* Tm = Rx + kp * ld;
+  T* V = Tm + kp * ld;
+  T* sig = V + kp * ld;
+  int* order = (int*)(sig + kp);
+  __shared__ int rotated;
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const MatDev md = mats[b];
+  const int k = md.k, r = md.r;
+  const T* rx = RX + (long long)b * kp * kp;
+  const T* ry = RY + (long long)b * kp * kp;
+  for (int e = tid; e < kp * kp; e += blockDim.x) {
+    const int i = e / kp, c = e % kp;
+    Rx[i * ld + c] = rx[e];
+    Tm[i * ld + c] = ry[e];
+    V[i * ld + c] = (i == c) ? T(1) : T(0);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    T mx = T(0);
+    for (int c = 0; c < k; ++c) mx = fmax(mx, fabs(Rx[c * ld + c]));
+    const T tol = (sizeof(T) == 8) ? T(1e-12) : T(1e-5);
+    bool def = (mx == T(0));
+    for (int c = 0; c < k; ++c) def |= fabs(Rx[c * ld + c]) <= tol * mx;
+    if (def) atomicOr(status, kStatusRankDef);
+  }
+  // T = R_Y R_X^{-1}, row by row, in place (row i of Tm starts as R_Y).
+  for (int i = tid; i < k; i += blockDim.x) {
+    T* row = Tm + i * ld;
+    for (int c = 0; c < k; ++c) {
+      T t = row[c];
+      for (int cc = 0; cc < c; ++cc) t -= row[cc] * Rx[cc * ld + c];
+      const T d = Rx[c * ld + c];
+      row[c] = (d != T(0)) ? t / d : T(0);
+    }
+  }
+  __syncthreads();
+  jacobi_columns<T>(Tm, V, k, k, ld, 60, &rotated);
+  __syncthreads();
+  column_norms_sorted<T>(Tm, k, k, ld, sig, order);
+  if (md.sigma != nullptr)
+    for (int c = tid; c < k; c += blockDim.x)
+      ((T*)md.sigma)[c] = sig[order[c]];
+  if (tid == 0) {
+    double cap = 0.0;
+    for (int c = 0; c < r; ++c) {
+      const double sv = (double)sig[order[c]];
+      cap += sv * sv;
+    }
+    const double tot = normA2[b];
+    const double e2 = tot - cap;
+    err[b] = sqrt(e2 > 0.0 ? e2 : 0.0);
+    // err_mode 0: identity, direct pass where it cancels; 2: direct always
+    flags[b] = (err_mode == 2) || (err_mode == 0 && e2 < tau * tot);
+  }
+  // W = R_X^{-1} V_r (k x r): back substitution, one column per thread.
+  T* Wout = Wm + (long long)b * kp * kp;
+  for (int e = tid; e < kp * kp; e += blockDim.x) Wout[e] = T(0);
+  __syncthreads();
+  for (int c = tid; c < r; c += blockDim.x) {
+    const int col = order[c];
+    for (int i = k - 1; i >= 0; --i) {
+      T t = V[i * ld + col];
+      for (int i2 = i + 1; i2 < k; ++i2) t -= Rx[i * ld + i2] * Wout[i2 * kp + c];
+      const T d = Rx[i * ld + i];
+      Wout[i * kp + c] = (d != T(0)) ? t / d : T(0);
+    }
+  }
+}
+
+static size_t small_svd_smem(int kp, size_t elt) {
+  return (size_t)3 * kp * (kp + 1) * elt + kp * elt + kp * sizeof(int) + 16;
+}
+
+cudaError_t launch_small_svd(bool dbl, int kp, const MatDev* mats, int count,
+                             const void* RX, const void* RY, void* Wm,
+                             double* normA2, double* err, int* flags, int err_mode,
+                             double tau, int* status, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (dbl) {
+    const size_t sm = small_svd_smem(kp, sizeof(double));
+    cudaError_t e = cudaFuncSetAttribute(small_svd_kernel<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    small_svd_kernel<double><<<count, 256, sm, s>>>(
+        kp, mats, (const double*)RX, (const double*)RY, (double*)Wm, normA2,
+        err, flags, err_mode, tau, status);
+  } else {
+    const size_t sm = small_svd_smem(kp, sizeof(float));
+    cudaError_t e = cudaFuncSetAttribute(small_svd_kernel<float>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    small_svd_kernel<float><<<count, 256, sm, s>>>(
+        kp, mats, (const float*)RX, (const float*)RY, (float*)Wm, normA2, err,
+        flags, err_mode, tau, status);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// T2: eigen-decomposition of the p x p symmetric PSD Rayleigh-Ritz matrix H
+// (one CTA).  For a PSD matrix the right singular vectors are eigenvectors
+// and the singular values the eigenvalues.  theta (p) descending; V (p x p)
+// has the matching eigenvectors as columns.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+sym_eig_kernel(const T* __restrict__ H, int p, T* __restrict__ theta,
+               T* __restrict__ Vout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ld = p + 1;
+  T* M = (T*)smem_raw;
+  T* V = M + p * ld;
+  T* sig = V + p * ld;
+  int* order = (int*)(sig + p);
+  __shared__ int rotated;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e / p, c = e % p;
+    M[i * ld + c] = T(0.5) * (H[i * p + c] + H[c * p + i]);
+    V[i * ld + c] = (i == c) ? T(1) : T(0);
+  }
+  __syncthreads();
+  jacobi_columns<T>(M, V, p, p, ld, 60, &rotated);
+  __syncthreads();
+  column_norms_sorted<T>(M, p, p, ld, sig, order);
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e / p, c = e % p;
+    Vout[i * p + c] = V[i * ld + order[c]];
+  }
+  for (int c = threadIdx.x; c < p; c += blockDim.x) theta[c] = sig[order[c]];
+}
+
+cudaError_t launch_sym_eig(bool dbl, const void* H, int p, void* theta,
+                           void* V, cudaStream_t s) {
+  const size_t elt = dbl ? sizeof(double) : sizeof(float);
+  const size_t sm = (size_t)2 * p * (p + 1) * elt + p * elt + p * sizeof(int) + 16;
+  if (dbl) {
+    cudaError_t e = cudaFuncSetAttribute(
+        sym_eig_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    sym_eig_kernel<double><<<1, 256, sm, s>>>((const double*)H, p,
+                                              (double*)theta, (double*)V);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(
+        sym_eig_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    sym_eig_kernel<float><<<1, 256, sm, s>>>((const float*)H, p,
+                                             (float*)theta, (float*)V);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace tsk

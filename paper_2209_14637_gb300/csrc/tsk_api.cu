@@ -1,0 +1,832 @@
+// Host side of the C ABI declared in include/tsk.h: handles, argument
+// checks, plans (workspace + schedule + CUDA graph), the eigensolver loop
+// of the training side and the dispatch to the kernels.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "tsk_internal.cuh"
+
+using namespace tsk;
+
+struct tsk_plan_s {
+  tsk_handle h = nullptr;
+  int count = 0;
+  tsk_prec prec = TSK_FP32;
+  int kp = 16;
+  bool dbl = false;
+  bool use_tc = false;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int launches = 0;
+  TcPlan* tc = nullptr;
+  std::vector<unsigned char> key;
+  // what a (re-)capture needs
+  bool any_out = false;
+  int nx = 0, ny = 0, nio = 0;
+  unsigned char* base = nullptr;
+  size_t o_mats = 0, o_ix = 0, o_iy = 0, o_io = 0, o_pan = 0, o_X = 0, o_Y = 0,
+         o_RX = 0, o_RY = 0, o_W = 0, o_flag = 0, o_U2 = 0, o_V2 = 0, o_e2 = 0;
+  double* d_norm = nullptr;
+  double* d_err = nullptr;
+  cudaGraphNode_t probe_begin = nullptr, probe_end = nullptr;
+};
+
+struct tsk_handle_s {
+  int device = 0;
+  tsk_options opts{};
+  char last_error[512] = {0};
+  int* d_status = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<tsk_plan> cache;
+};
+
+static thread_local char g_create_error[512] = "no error";
+
+static void set_err(tsk_handle h, const char* fmt, ...) {
+  char* dst = h ? h->last_error : g_create_error;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+}
+
+#define TSK_CUDA(h, call)                                                   \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess) {                                                \
+      set_err((h), "%s failed: %s", #call, cudaGetErrorString(e_));         \
+      return e_ == cudaErrorMemoryAllocation ? TSK_ENOMEM : TSK_ECUDA;      \
+    }                                                                       \
+  } while (0)
+
+static size_t elt_size(tsk_prec p) {
+  return p == TSK_FP64 ? 8 : (p == TSK_FP32 ? 4 : 2);
+}
+static size_t compute_size(tsk_prec p) { return p == TSK_FP64 ? 8 : 4; }
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+extern "C" void tsk_default_options(tsk_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->kernel = TSK_KERNEL_AUTO;
+  o->refine_q = 1;
+  o->max_iter = 300;
+  o->eig_tol = 0.0;
+  o->err_mode = 0;
+  o->spin_limit = 1ll << 24;
+}
+
+extern "C" tsk_status tsk_create(tsk_handle* out, const tsk_options* opts) {
+  if (!out) {
+    set_err(nullptr, "tsk_create: out is NULL");
+    return TSK_EINVAL;
+  }
+  *out = nullptr;
+  int dev = 0, ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    set_err(nullptr, "tsk_create: no CUDA device (%s)", cudaGetErrorString(e));
+    return TSK_ECUDA;
+  }
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    set_err(nullptr, "tsk_create: cudaGetDevice failed");
+    return TSK_ECUDA;
+  }
+  tsk_handle h = new (std::nothrow) tsk_handle_s();
+  if (!h) return TSK_ENOMEM;
+  h->device = dev;
+  tsk_default_options(&h->opts);
+  if (opts) h->opts = *opts;
+  if (h->opts.max_iter <= 0) h->opts.max_iter = 300;
+  if (h->opts.spin_limit <= 0) h->opts.spin_limit = 1ll << 24;
+  e = cudaMalloc(&h->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    set_err(nullptr, "tsk_create: %s", cudaGetErrorString(e));
+    if (h->d_status) cudaFree(h->d_status);
+    delete h;
+    return TSK_ECUDA;
+  }
+  *out = h;
+  return TSK_OK;
+}
+
+static void plan_free(tsk_plan p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->tc) tc_destroy(p->tc);
+  if (p->ws) cudaFree(p->ws);
+  delete p;
+}
+
+extern "C" tsk_status tsk_destroy(tsk_handle h) {
+  if (!h) return TSK_EINVAL;
+  cudaDeviceSynchronize();
+  for (tsk_plan p : h->cache) plan_free(p);
+  h->cache.clear();
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->d_status) cudaFree(h->d_status);
+  delete h;
+  return TSK_OK;
+}
+
+extern "C" const char* tsk_last_error(tsk_handle h) {
+  return h ? h->last_error : g_create_error;
+}
+
+extern "C" tsk_status tsk_sync_status(tsk_handle h, tsk_stream stream) {
+  if (!h) return TSK_EINVAL;
+  TSK_CUDA(h, cudaStreamSynchronize((cudaStream_t)stream));
+  int st = 0;
+  TSK_CUDA(h, cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  TSK_CUDA(h, cudaMemset(h->d_status, 0, sizeof(int)));
+  if (st & kStatusTimeout) {
+    set_err(h, "a bounded device wait ran out (status word 0x%x)", st);
+    return TSK_ETIMEOUT;
+  }
+  if (st & kStatusRankDef) {
+    set_err(h, "S A had rank < k for at least one matrix");
+    return TSK_ERANKDEF;
+  }
+  return TSK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// argument checks
+// ---------------------------------------------------------------------------
+static tsk_status check_desc(tsk_handle h, const tsk_mat_desc& d, int64_t i,
+                             tsk_prec prec) {
+  if (!d.A || !d.S) {
+    set_err(h, "matrix %lld: A or S is NULL", (long long)i);
+    return TSK_EINVAL;
+  }
+  if (d.m < 1 || d.n < 1 || d.lda < d.n) {
+    set_err(h, "matrix %lld: need m, n >= 1 and lda >= n (m=%lld n=%lld lda=%lld)",
+            (long long)i, (long long)d.m, (long long)d.n, (long long)d.lda);
+    return TSK_EINVAL;
+  }
+  const int64_t mn = std::min(d.m, d.n);
+  if (d.r < 1 || d.r > d.k || d.k > mn || d.k > TSK_MAX_K) {
+    set_err(h, "matrix %lld: need 1 <= r <= k <= min(m, n) and k <= %d "
+               "(r=%d k=%d m=%lld n=%lld)",
+            (long long)i, TSK_MAX_K, d.r, d.k, (long long)d.m, (long long)d.n);
+    return TSK_EINVAL;
+  }
+  const size_t es = elt_size(prec);
+  if (((uintptr_t)d.A) % es != 0 || ((uintptr_t)d.S) % compute_size(prec) != 0) {
+    set_err(h, "matrix %lld: A or S is not aligned to its element size", (long long)i);
+    return TSK_EINVAL;
+  }
+  return TSK_OK;
+}
+
+static bool tc_eligible(const tsk_mat_desc* mats, int64_t count) {
+  for (int64_t i = 0; i < count; ++i) {
+    if (((uintptr_t)mats[i].A) % 16 != 0) return false;
+    if ((mats[i].lda * 2) % 16 != 0) return false;
+    if (((uintptr_t)mats[i].S) % 16 != 0) return false;
+    if ((mats[i].m * 4) % 16 != 0) return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// plans
+// ---------------------------------------------------------------------------
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    off = align_up(off, 256);
+    size_t o = off;
+    off += bytes;
+    return o;
+  }
+};
+
+// Records one execution of the plan into a CUDA graph.  With events given,
+// event-record nodes bracket the sketch pass (the stage that streams A).
+static cudaError_t capture_plan(tsk_plan p, cudaEvent_t evb, cudaEvent_t eve) {
+  tsk_handle h = p->h;
+  unsigned char* base = p->base;
+  const int kp = p->kp;
+  const int count = p->count;
+  const int in_type = (int)p->prec;
+  const MatDev* d_mats = (const MatDev*)(base + p->o_mats);
+  double* d_norm = p->d_norm;
+  double* d_err = p->d_err;
+  cudaStream_t s = h->cap_stream;
+  if (p->exec) {
+    cudaGraphExecDestroy(p->exec);
+    p->exec = nullptr;
+  }
+  if (p->graph) {
+    cudaGraphDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  p->probe_begin = p->probe_end = nullptr;
+  cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+  if (ce != cudaSuccess) return ce;
+  int launches = 0;
+  ce = cudaMemsetAsync(d_norm, 0, sizeof(double) * count, s);
+  if (ce == cudaSuccess && evb) ce = cudaEventRecordWithFlags(evb, s, cudaEventRecordExternal);
+  if (ce == cudaSuccess) {
+    if (p->use_tc) {
+      ce = tc_launch(p->tc, s);
+      launches += tc_launches(p->tc);
+    } else {
+      ce = launch_sketch_x(in_type, kp, d_mats, (const int2*)(base + p->o_ix),
+                           p->nx, base + p->o_X, d_norm, s);
+      if (ce == cudaSuccess)
+        ce = launch_sketch_y(in_type, kp, d_mats, (const int2*)(base + p->o_iy),
+                             p->ny, base + p->o_X, base + p->o_Y, s);
+      launches += 2;
+    }
+  }
+  if (ce == cudaSuccess && eve) ce = cudaEventRecordWithFlags(eve, s, cudaEventRecordExternal);
+  if (ce == cudaSuccess) {
+    ce = launch_tsqr(p->dbl, kp, (const PanelDev*)(base + p->o_pan), 2 * count,
+                     h->opts.refine_q ? 1 : 0, h->d_status, s);
+    ++launches;
+  }
+  if (ce == cudaSuccess) {
+    const double tau = p->dbl ? 1e-6 : 1e-4;
+    ce = launch_small_svd(p->dbl, kp, d_mats, count, base + p->o_RX,
+                          base + p->o_RY, base + p->o_W, d_norm, d_err,
+                          (int*)(base + p->o_flag), h->opts.err_mode, tau,
+                          h->d_status, s);
+    ++launches;
+  }
+  if (ce == cudaSuccess && h->opts.err_mode != 1) {
+    ce = cudaMemsetAsync(base + p->o_e2, 0, sizeof(double) * count, s);
+    if (ce == cudaSuccess)
+      ce = launch_direct_fallback(in_type, kp, d_mats, count, (const int*)(base + p->o_flag),
+                                  base + p->o_X, base + p->o_Y, base + p->o_W,
+                                  base + p->o_U2, base + p->o_V2, (double*)(base + p->o_e2),
+                                  d_err, s);
+    launches += 3;
+  }
+  if (ce == cudaSuccess && p->any_out) {
+    ce = launch_project_out(p->dbl, kp, d_mats, (const int4*)(base + p->o_io),
+                            p->nio, base + p->o_X, base + p->o_Y, base + p->o_W,
+                            s);
+    ++launches;
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t ce2 = cudaStreamEndCapture(s, &g);
+  if (ce == cudaSuccess) ce = ce2;
+  p->graph = g;
+  if (ce == cudaSuccess) ce = cudaGraphInstantiate(&p->exec, p->graph, 0);
+  if (ce == cudaSuccess && evb && eve) {
+    size_t nn = 0;
+    ce = cudaGraphGetNodes(p->graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (ce == cudaSuccess && nn) ce = cudaGraphGetNodes(p->graph, nodes.data(), &nn);
+    for (size_t i = 0; ce == cudaSuccess && i < nn; ++i) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess) continue;
+      if (t != cudaGraphNodeTypeEventRecord) continue;
+      cudaEvent_t ev = nullptr;
+      if (cudaGraphEventRecordNodeGetEvent(nodes[i], &ev) != cudaSuccess) continue;
+      if (ev == evb) p->probe_begin = nodes[i];
+      if (ev == eve) p->probe_end = nodes[i];
+    }
+  }
+  p->launches = launches;
+  return ce;
+}
+
+static tsk_status build_plan(tsk_handle h, int64_t count,
+                             const tsk_mat_desc* mats, tsk_prec prec,
+                             const tsk_mat_out* outs, double* err,
+                             double* normA2, tsk_plan* out) {
+  *out = nullptr;
+  if (count < 1 || !mats) {
+    set_err(h, "count must be >= 1 and mats non-NULL");
+    return TSK_EINVAL;
+  }
+  if (prec != TSK_FP64 && prec != TSK_FP32 && prec != TSK_BF16) {
+    set_err(h, "unknown precision %d", (int)prec);
+    return TSK_EINVAL;
+  }
+  if (count > (1 << 22)) {
+    set_err(h, "count too large");
+    return TSK_EINVAL;
+  }
+  int kmax = 1;
+  for (int64_t i = 0; i < count; ++i) {
+    tsk_status st = check_desc(h, mats[i], i, prec);
+    if (st != TSK_OK) return st;
+    kmax = std::max(kmax, mats[i].k);
+  }
+  const int req = h->opts.kernel;
+  bool use_tc = false;
+  if (prec == TSK_BF16 && req != TSK_KERNEL_SIMT) {
+    const bool ok = tc_supported() && tc_eligible(mats, count);
+    if (req == TSK_KERNEL_TC && !ok) {
+      set_err(h, "tensor-core kernel requested but unavailable for these "
+                 "arguments (needs a GB300 and 16-byte aligned A, S, lda)");
+      return TSK_EUNSUPPORTED;
+    }
+    use_tc = ok;
+  } else if (req == TSK_KERNEL_TC) {
+    set_err(h, "the tensor-core kernel runs the TSK_BF16 path only");
+    return TSK_EUNSUPPORTED;
+  }
+
+  tsk_plan p = new (std::nothrow) tsk_plan_s();
+  if (!p) return TSK_ENOMEM;
+  p->h = h;
+  p->count = (int)count;
+  p->prec = prec;
+  p->dbl = (prec == TSK_FP64);
+  p->kp = ((kmax + 15) / 16) * 16;
+  p->use_tc = use_tc;
+  const int kp = p->kp;
+  const size_t cs = compute_size(prec);
+
+  std::vector<MatDev> hm(count);
+  std::vector<int2> ix, iy;
+  std::vector<int4> io;
+  long long offX = 0, offY = 0;
+  bool any_out = false;
+  for (int64_t i = 0; i < count; ++i) {
+    MatDev& d = hm[i];
+    d.A = mats[i].A;
+    d.S = mats[i].S;
+    d.m = mats[i].m;
+    d.n = mats[i].n;
+    d.lda = mats[i].lda;
+    d.k = mats[i].k;
+    d.r = mats[i].r;
+    d.offX = offX;
+    d.offY = offY;
+    d.US = outs ? outs[i].US : nullptr;
+    d.Vt = outs ? outs[i].Vt : nullptr;
+    d.sigma = outs ? outs[i].sigma : nullptr;
+    offX += d.n * kp;
+    offY += d.m * kp;
+    for (long long t = 0; t < (d.n + 63) / 64; ++t) ix.push_back(make_int2((int)i, (int)t));
+    for (long long t = 0; t < (d.m + 63) / 64; ++t) iy.push_back(make_int2((int)i, (int)t));
+    if (d.US)
+      for (long long t = 0; t < (d.m + 255) / 256; ++t)
+        io.push_back(make_int4((int)i, (int)t, 0, 0));
+    if (d.Vt)
+      for (long long t = 0; t < (d.n + 255) / 256; ++t)
+        io.push_back(make_int4((int)i, (int)t, 1, 0));
+    any_out |= (d.US || d.Vt);
+  }
+  Carve cv;
+  const size_t o_mats = cv.take(sizeof(MatDev) * count);
+  const size_t o_ix = cv.take(sizeof(int2) * ix.size());
+  const size_t o_iy = cv.take(sizeof(int2) * iy.size());
+  const size_t o_io = cv.take(sizeof(int4) * std::max<size_t>(1, io.size()));
+  const size_t o_pan = cv.take(sizeof(PanelDev) * 2 * count);
+  const size_t o_X = cv.take(cs * offX);
+  const size_t o_Y = cv.take(cs * offY);
+  const size_t o_RX = cv.take(cs * count * kp * kp);
+  const size_t o_RY = cv.take(cs * count * kp * kp);
+  const size_t o_W = cv.take(cs * count * kp * kp);
+  const size_t o_nrm = cv.take(sizeof(double) * count);
+  const size_t o_err = cv.take(sizeof(double) * count);
+  const bool fallback = h->opts.err_mode != 1;
+  const size_t o_flag = cv.take(sizeof(int) * count);
+  const size_t o_U2 = cv.take(fallback ? cs * offY : 0);
+  const size_t o_V2 = cv.take(fallback ? cs * offX : 0);
+  const size_t o_e2 = cv.take(sizeof(double) * count);
+  const size_t host_part = o_X;  // descriptors live before X
+  p->ws_bytes = cv.off;
+  cudaError_t ce = cudaMalloc(&p->ws, p->ws_bytes);
+  if (ce != cudaSuccess) {
+    set_err(h, "plan workspace of %zu bytes: %s", p->ws_bytes, cudaGetErrorString(ce));
+    delete p;
+    return TSK_ENOMEM;
+  }
+  unsigned char* base = (unsigned char*)p->ws;
+  double* d_norm = normA2 ? normA2 : (double*)(base + o_nrm);
+  double* d_err = err ? err : (double*)(base + o_err);
+  std::vector<PanelDev> hp(2 * count);
+  for (int64_t i = 0; i < count; ++i) {
+    PanelDev& px = hp[2 * i];
+    px.P = base + o_X + cs * hm[i].offX;
+    px.rows = hm[i].n;
+    px.k = hm[i].k;
+    px.ld = kp;
+    px.R = base + o_RX + cs * i * kp * kp;
+    PanelDev& py = hp[2 * i + 1];
+    py.P = base + o_Y + cs * hm[i].offY;
+    py.rows = hm[i].m;
+    py.k = hm[i].k;
+    py.ld = kp;
+    py.R = base + o_RY + cs * i * kp * kp;
+  }
+  std::vector<unsigned char> staging(host_part, 0);
+  memcpy(staging.data() + o_mats, hm.data(), sizeof(MatDev) * count);
+  memcpy(staging.data() + o_ix, ix.data(), sizeof(int2) * ix.size());
+  memcpy(staging.data() + o_iy, iy.data(), sizeof(int2) * iy.size());
+  if (!io.empty()) memcpy(staging.data() + o_io, io.data(), sizeof(int4) * io.size());
+  memcpy(staging.data() + o_pan, hp.data(), sizeof(PanelDev) * 2 * count);
+  ce = cudaMemcpy(p->ws, staging.data(), host_part, cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) {
+    set_err(h, "plan upload: %s", cudaGetErrorString(ce));
+    plan_free(p);
+    return TSK_ECUDA;
+  }
+  const MatDev* d_mats = (const MatDev*)(base + o_mats);
+  if (use_tc) {
+    char msg[256] = {0};
+    ce = tc_prepare(&p->tc, hm.data(), d_mats, (int)count, kp, base + o_X, base + o_Y,
+                    d_norm, h->d_status, h->opts.spin_limit, msg, sizeof(msg));
+    if (ce != cudaSuccess) {
+      set_err(h, "tensor-core plan: %s (%s)", msg, cudaGetErrorString(ce));
+      plan_free(p);
+      return TSK_ECUDA;
+    }
+  }
+
+  p->any_out = any_out;
+  p->nx = (int)ix.size();
+  p->ny = (int)iy.size();
+  p->nio = (int)io.size();
+  p->base = base;
+  p->o_mats = o_mats;
+  p->o_ix = o_ix;
+  p->o_iy = o_iy;
+  p->o_io = o_io;
+  p->o_pan = o_pan;
+  p->o_X = o_X;
+  p->o_Y = o_Y;
+  p->o_RX = o_RX;
+  p->o_RY = o_RY;
+  p->o_W = o_W;
+  p->o_flag = o_flag;
+  p->o_U2 = o_U2;
+  p->o_V2 = o_V2;
+  p->o_e2 = o_e2;
+  p->d_norm = d_norm;
+  p->d_err = d_err;
+  ce = capture_plan(p, nullptr, nullptr);
+  if (ce != cudaSuccess) {
+    set_err(h, "plan capture: %s", cudaGetErrorString(ce));
+    cudaGetLastError();
+    plan_free(p);
+    return TSK_ECUDA;
+  }
+  *out = p;
+  return TSK_OK;
+}
+
+extern "C" tsk_status tsk_plan_create(tsk_handle h, int64_t count,
+                                      const tsk_mat_desc* mats, tsk_prec prec,
+                                      const tsk_mat_out* outs, double* err,
+                                      double* normA2, tsk_plan* plan) {
+  if (!h || !plan) return TSK_EINVAL;
+  return build_plan(h, count, mats, prec, outs, err, normA2, plan);
+}
+
+extern "C" tsk_status tsk_plan_execute(tsk_plan p, tsk_stream stream) {
+  if (!p || !p->exec) return TSK_EINVAL;
+  TSK_CUDA(p->h, cudaGraphLaunch(p->exec, (cudaStream_t)stream));
+  return TSK_OK;
+}
+
+extern "C" tsk_status tsk_plan_destroy(tsk_plan p) {
+  if (!p) return TSK_EINVAL;
+  cudaDeviceSynchronize();
+  plan_free(p);
+  return TSK_OK;
+}
+
+extern "C" tsk_status tsk_plan_set_probe(tsk_plan p, void* ev_begin,
+                                         void* ev_end) {
+  if (!p || !ev_begin || !ev_end || ev_begin == ev_end) return TSK_EINVAL;
+  cudaEvent_t b = (cudaEvent_t)ev_begin, e = (cudaEvent_t)ev_end;
+  if (p->probe_begin && p->probe_end) {
+    TSK_CUDA(p->h, cudaGraphExecEventRecordNodeSetEvent(p->exec, p->probe_begin, b));
+    TSK_CUDA(p->h, cudaGraphExecEventRecordNodeSetEvent(p->exec, p->probe_end, e));
+    return TSK_OK;
+  }
+  TSK_CUDA(p->h, cudaDeviceSynchronize());
+  TSK_CUDA(p->h, capture_plan(p, b, e));
+  if (!p->probe_begin || !p->probe_end) {
+    set_err(p->h, "probe nodes not found in the captured graph");
+    return TSK_ECUDA;
+  }
+  return TSK_OK;
+}
+
+extern "C" tsk_status tsk_plan_info(tsk_plan p, int64_t* ws, int32_t* launches) {
+  if (!p) return TSK_EINVAL;
+  if (ws) *ws = (int64_t)p->ws_bytes + (p->tc ? tc_workspace_bytes(p->tc) : 0);
+  if (launches) *launches = p->launches;
+  return TSK_OK;
+}
+
+static std::vector<unsigned char> plan_key(tsk_handle h, int64_t count,
+                                           const tsk_mat_desc* mats,
+                                           tsk_prec prec,
+                                           const tsk_mat_out* outs,
+                                           double* err, double* normA2) {
+  std::vector<unsigned char> k;
+  auto put = [&k](const void* src, size_t n) {
+    const unsigned char* c = (const unsigned char*)src;
+    k.insert(k.end(), c, c + n);
+  };
+  put(&count, sizeof(count));
+  put(&prec, sizeof(prec));
+  put(&err, sizeof(err));
+  put(&normA2, sizeof(normA2));
+  put(&h->opts.kernel, sizeof(h->opts.kernel));
+  put(&h->opts.refine_q, sizeof(h->opts.refine_q));
+  put(&h->opts.err_mode, sizeof(h->opts.err_mode));
+  put(mats, sizeof(tsk_mat_desc) * count);
+  const unsigned char has = outs ? 1 : 0;
+  put(&has, 1);
+  if (outs) put(outs, sizeof(tsk_mat_out) * count);
+  return k;
+}
+
+extern "C" tsk_status tsk_approx_batch(tsk_handle h, int64_t count,
+                                       const tsk_mat_desc* mats, tsk_prec prec,
+                                       const tsk_mat_out* outs, double* err,
+                                       double* normA2, tsk_stream stream) {
+  if (!h) return TSK_EINVAL;
+  if (count < 1 || !mats) {
+    set_err(h, "count must be >= 1 and mats non-NULL");
+    return TSK_EINVAL;
+  }
+  std::vector<unsigned char> key = plan_key(h, count, mats, prec, outs, err, normA2);
+  tsk_plan found = nullptr;
+  for (size_t i = 0; i < h->cache.size(); ++i) {
+    if (h->cache[i]->key == key) {
+      found = h->cache[i];
+      h->cache.erase(h->cache.begin() + i);
+      h->cache.push_back(found);  // most recently used last
+      break;
+    }
+  }
+  if (!found) {
+    tsk_status st = build_plan(h, count, mats, prec, outs, err, normA2, &found);
+    if (st != TSK_OK) return st;
+    found->key = std::move(key);
+    if (h->cache.size() >= 8) {
+      cudaDeviceSynchronize();
+      plan_free(h->cache.front());
+      h->cache.erase(h->cache.begin());
+    }
+    h->cache.push_back(found);
+  }
+  return tsk_plan_execute(found, stream);
+}
+
+// ---------------------------------------------------------------------------
+// direct error (one more pass over A)
+// ---------------------------------------------------------------------------
+extern "C" tsk_status tsk_error(tsk_handle h, int64_t count,
+                                const tsk_mat_desc* mats, tsk_prec prec,
+                                const tsk_mat_out* outs, double* err,
+                                tsk_stream stream) {
+  if (!h) return TSK_EINVAL;
+  if (count < 1 || !mats || !outs || !err) {
+    set_err(h, "tsk_error: count >= 1 and non-NULL mats, outs, err required");
+    return TSK_EINVAL;
+  }
+  std::vector<MatDev> hm(count);
+  std::vector<int2> items;
+  for (int64_t i = 0; i < count; ++i) {
+    tsk_status st = check_desc(h, mats[i], i, prec);
+    if (st != TSK_OK) return st;
+    if (!outs[i].US || !outs[i].Vt) {
+      set_err(h, "tsk_error: matrix %lld has no US/Vt factors", (long long)i);
+      return TSK_EINVAL;
+    }
+    MatDev& d = hm[i];
+    memset(&d, 0, sizeof(d));
+    d.A = mats[i].A;
+    d.S = mats[i].S;
+    d.m = mats[i].m;
+    d.n = mats[i].n;
+    d.lda = mats[i].lda;
+    d.k = mats[i].k;
+    d.r = mats[i].r;
+    d.US = outs[i].US;
+    d.Vt = outs[i].Vt;
+    for (long long t = 0; t < (d.m + 15) / 16; ++t) items.push_back(make_int2((int)i, (int)t));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t b1 = align_up(sizeof(MatDev) * count, 256);
+  const size_t bytes = b1 + sizeof(int2) * items.size();
+  std::vector<unsigned char> staging(bytes);
+  memcpy(staging.data(), hm.data(), sizeof(MatDev) * count);
+  memcpy(staging.data() + b1, items.data(), sizeof(int2) * items.size());
+  void* d = nullptr;
+  TSK_CUDA(h, cudaMallocAsync(&d, bytes, s));
+  TSK_CUDA(h, cudaMemcpyAsync(d, staging.data(), bytes, cudaMemcpyHostToDevice, s));
+  TSK_CUDA(h, cudaMemsetAsync(err, 0, sizeof(double) * count, s));
+  TSK_CUDA(h, launch_direct_error((int)prec, (const MatDev*)d,
+                                  (const int2*)((unsigned char*)d + b1),
+                                  (int)items.size(), err, s));
+  TSK_CUDA(h, launch_sqrt_inplace(err, (int)count, s));
+  TSK_CUDA(h, cudaFreeAsync(d, s));
+  // The pageable staging buffer must outlive the copy.
+  TSK_CUDA(h, cudaStreamSynchronize(s));
+  return TSK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// training side
+// ---------------------------------------------------------------------------
+extern "C" tsk_status tsk_gram(tsk_handle h, const void* const* A, int64_t D,
+                               int64_t m, int64_t n, int64_t lda,
+                               tsk_prec prec, int32_t mode, double* G,
+                               int32_t accumulate, tsk_stream stream) {
+  if (!h) return TSK_EINVAL;
+  if (!A || !G || D < 1 || m < 1 || n < 1 || lda < n || (mode != 1 && mode != 2)) {
+    set_err(h, "tsk_gram: need A, G non-NULL, D, m, n >= 1, lda >= n, mode 1 or 2");
+    return TSK_EINVAL;
+  }
+  if (prec != TSK_FP64 && prec != TSK_FP32 && prec != TSK_BF16) {
+    set_err(h, "tsk_gram: unknown precision");
+    return TSK_EINVAL;
+  }
+  for (int64_t d = 0; d < D; ++d)
+    if (!A[d] || ((uintptr_t)A[d]) % elt_size(prec) != 0) {
+      set_err(h, "tsk_gram: A[%lld] is NULL or misaligned", (long long)d);
+      return TSK_EINVAL;
+    }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t dim = (mode == 1) ? m : n;
+  void* dA = nullptr;
+  TSK_CUDA(h, cudaMallocAsync(&dA, sizeof(void*) * D, s));
+  TSK_CUDA(h, cudaMemcpyAsync(dA, A, sizeof(void*) * D, cudaMemcpyHostToDevice, s));
+  if (!accumulate) TSK_CUDA(h, cudaMemsetAsync(G, 0, sizeof(double) * dim * dim, s));
+  TSK_CUDA(h, launch_gram((int)prec, (const void* const*)dA, D, m, n, lda, mode, G, s));
+  TSK_CUDA(h, cudaFreeAsync(dA, s));
+  TSK_CUDA(h, cudaStreamSynchronize(s));  // A (host array) must outlive the copy
+  return TSK_OK;
+}
+
+extern "C" tsk_status tsk_sketch_from_gram(tsk_handle h, const double* G,
+                                           int64_t dim, int32_t k,
+                                           tsk_prec prec, void* S, double* eig,
+                                           tsk_stream stream) {
+  if (!h) return TSK_EINVAL;
+  if (!G || !S || dim < 1 || k < 1 || k > dim || k > TSK_MAX_K) {
+    set_err(h, "tsk_sketch_from_gram: need G, S non-NULL and 1 <= k <= min(dim, %d)",
+            TSK_MAX_K);
+    return TSK_EINVAL;
+  }
+  const bool dbl = (prec == TSK_FP64);
+  const size_t cs = dbl ? 8 : 4;
+  // Oversampling: the block converges at the rate lambda_{p+1}/lambda_k per
+  // iteration, and streams whose matrices drift have flat spectra there.
+  int p = std::max(2 * k, k + 32);
+  p = std::min<int64_t>(p, 96);
+  p = std::max(p, (int)k);
+  p = (int)std::min<int64_t>(p, dim);
+  double tol = h->opts.eig_tol > 0 ? h->opts.eig_tol : (dbl ? 1e-13 : 2e-6);
+  cudaStream_t s = (cudaStream_t)stream;
+  Carve cv;
+  const size_t o_Gc = dbl ? 0 : cv.take(cs * dim * dim);
+  const size_t o_Z = cv.take(cs * dim * p);
+  const size_t o_W = cv.take(cs * dim * p);
+  const size_t o_U = cv.take(cs * dim * p);
+  const size_t o_GU = cv.take(cs * dim * p);
+  const size_t o_H = cv.take(cs * p * p);
+  const size_t o_V = cv.take(cs * p * p);
+  const size_t o_th = cv.take(cs * p);
+  const size_t o_R = cv.take(cs * p * p);
+  const size_t o_res = cv.take(sizeof(double) * k);
+  const size_t o_pan = cv.take(sizeof(PanelDev));
+  void* ws = nullptr;
+  TSK_CUDA(h, cudaMallocAsync(&ws, cv.off, s));
+  unsigned char* b = (unsigned char*)ws;
+  const void* Gm = dbl ? (const void*)G : (const void*)(b + o_Gc);
+  void *Z = b + o_Z, *W = b + o_W, *U = b + o_U, *GU = b + o_GU, *H = b + o_H,
+       *V = b + o_V, *th = b + o_th, *R = b + o_R;
+  double* res = (double*)(b + o_res);
+  PanelDev* dpan = (PanelDev*)(b + o_pan);
+  tsk_status result = TSK_OK;
+#define TSK_E(call)                                                            \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) {                                                   \
+      set_err(h, "%s failed: %s", #call, cudaGetErrorString(e_));              \
+      cudaFreeAsync(ws, s);                                                    \
+      return TSK_ECUDA;                                                        \
+    }                                                                          \
+  } while (0)
+  if (!dbl) TSK_E(launch_convert_gram(false, G, b + o_Gc, dim * dim, s));
+  // orth(P) in place through the panel descriptor: R = TSQR(P), P <- P R^{-1}
+  auto orth = [&](void* P) -> cudaError_t {
+    PanelDev pd;
+    pd.P = P;
+    pd.rows = dim;
+    pd.k = p;
+    pd.ld = p;
+    pd.R = R;
+    cudaError_t e = cudaMemcpyAsync(dpan, &pd, sizeof(pd), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // pd is on the stack
+    if (e == cudaSuccess) e = launch_tsqr(dbl, p, dpan, 1, 1, h->d_status, s);
+    if (e == cudaSuccess) e = launch_apply_rinv(dbl, P, R, P, dim, p, s);
+    return e;
+  };
+  TSK_E(launch_random_fill(dbl, Z, dim * p, 0x5eed5eedull, s));
+  TSK_E(orth(Z));
+  std::vector<double> hres(k), hth(p);
+  std::vector<float> hthf(p);
+  double best = 1e300;
+  int stall = 0;
+  bool converged = false;
+  for (int it = 0; it < h->opts.max_iter; ++it) {
+    TSK_E(launch_gemm(dbl, 0, 0, dim, p, dim, 1.0, Gm, dim, Z, p, 0.0, W, p, s));
+    TSK_E(launch_gemm(dbl, 1, 0, p, p, dim, 1.0, Z, p, W, p, 0.0, H, p, s));
+    TSK_E(launch_sym_eig(dbl, H, p, th, V, s));
+    TSK_E(launch_gemm(dbl, 0, 0, dim, p, p, 1.0, Z, p, V, p, 0.0, U, p, s));
+    TSK_E(launch_gemm(dbl, 0, 0, dim, p, p, 1.0, W, p, V, p, 0.0, GU, p, s));
+    TSK_E(launch_ritz_residual(dbl, U, GU, th, res, dim, p, k, s));
+    TSK_E(cudaMemcpyAsync(hres.data(), res, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    if (dbl)
+      TSK_E(cudaMemcpyAsync(hth.data(), th, sizeof(double) * p, cudaMemcpyDeviceToHost, s));
+    else
+      TSK_E(cudaMemcpyAsync(hthf.data(), th, sizeof(float) * p, cudaMemcpyDeviceToHost, s));
+    TSK_E(cudaStreamSynchronize(s));
+    if (!dbl)
+      for (int c = 0; c < p; ++c) hth[c] = hthf[c];
+    const double scale = std::max(std::fabs(hth[0]), 1e-300);
+    double worst = 0.0;
+    for (int c = 0; c < k; ++c) worst = std::max(worst, hres[c] / scale);
+    if (worst <= tol) {
+      converged = true;
+      break;
+    }
+    // A residual that stopped improving has reached the rounding floor of
+    // the compute type.
+    if (worst < 0.999 * best) {
+      best = worst;
+      stall = 0;
+    } else if (++stall >= 4 && worst < 1e3 * tol) {
+      converged = true;
+      break;
+    }
+    TSK_E(orth(GU));
+    std::swap(Z, GU);
+  }
+  TSK_E(launch_emit_sketch(dbl, U, dim, p, k, S, s));
+  if (eig) {
+    TSK_E(cudaMemcpyAsync(eig, hth.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+  }
+  TSK_E(cudaFreeAsync(ws, s));
+  TSK_E(cudaStreamSynchronize(s));
+#undef TSK_E
+  if (!converged) {
+    set_err(h, "eigensolver: residual above %g after %d iterations", tol,
+            h->opts.max_iter);
+    result = TSK_ENOCONV;
+  }
+  return result;
+}
+
+extern "C" tsk_status tsk_train_sketch(tsk_handle h, const void* const* A,
+                                       int64_t D, int64_t m, int64_t n,
+                                       int64_t lda, tsk_prec prec, int32_t k,
+                                       int32_t l, void* S, void* W,
+                                       double* eig, tsk_stream stream) {
+  if (!h) return TSK_EINVAL;
+  if (k < 1 || k > std::min(m, n) || k > TSK_MAX_K || l < 0 ||
+      (l > 0 && (l > std::min(m, n) || l > TSK_MAX_K || !W)) || !S) {
+    set_err(h, "tsk_train_sketch: need 1 <= k <= min(m, n, %d), 0 <= l <= "
+               "min(m, n, %d), S (and W when l > 0) non-NULL", TSK_MAX_K, TSK_MAX_K);
+    return TSK_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t dmax = (l > 0) ? std::max(m, n) : m;
+  double* G = nullptr;
+  TSK_CUDA(h, cudaMallocAsync((void**)&G, sizeof(double) * dmax * dmax, s));
+  tsk_status st = tsk_gram(h, A, D, m, n, lda, prec, 1, G, 0, stream);
+  tsk_status st2 = TSK_OK;
+  if (st == TSK_OK) {
+    st = tsk_sketch_from_gram(h, G, m, k, prec, S, eig, stream);
+    if (st == TSK_ENOCONV) st2 = st, st = TSK_OK;
+  }
+  if (st == TSK_OK && l > 0) {
+    st = tsk_gram(h, A, D, m, n, lda, prec, 2, G, 0, stream);
+    if (st == TSK_OK) {
+      st = tsk_sketch_from_gram(h, G, n, l, prec, W, eig ? eig + k : nullptr, stream);
+      if (st == TSK_ENOCONV) st2 = st, st = TSK_OK;
+    }
+  }
+  cudaFreeAsync(G, s);
+  cudaStreamSynchronize(s);
+  return st != TSK_OK ? st : st2;
+}

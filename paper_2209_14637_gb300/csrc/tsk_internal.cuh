@@ -1,0 +1,128 @@
+// Internal declarations shared by the CUDA translation units of libtsk.
+// Nothing here is part of the C ABI (include/tsk.h is).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tsk.h"
+
+namespace tsk {
+
+// Bits of the device status word (most severe wins when reported).
+enum : int {
+  kStatusRankDef = 1,  // |R_jj| of a sketch panel fell below the threshold
+  kStatusTimeout = 2,  // a bounded spin-wait ran out
+};
+
+// One test-side matrix as the kernels see it.  X (n x kp) and Y (m x kp) are
+// per-matrix panels in the plan workspace; kp is the batch-wide padded k.
+struct MatDev {
+  const void* A;
+  const void* S;
+  long long m, n, lda;
+  int k, r;
+  long long offX, offY;  // element offsets of X and Y in the workspace
+  void* US;
+  void* Vt;
+  void* sigma;
+};
+
+// A tall panel (rows x kp, leading dimension kp) whose R factor is wanted.
+struct PanelDev {
+  const void* P;  // rows x ld, row-major; columns [0, k) are used
+  long long rows;
+  int k;
+  int ld;
+  void* R;  // kp x kp row-major, upper triangle holds R
+};
+
+// Element conversions used by the loaders.
+__device__ __forceinline__ float to_float(float x) { return x; }
+__device__ __forceinline__ float to_float(double x) { return (float)x; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+template <typename Tc, typename Tin>
+__device__ __forceinline__ Tc convert_in(Tin x) {
+  return (Tc)to_float(x);
+}
+template <>
+__device__ __forceinline__ double convert_in<double, double>(double x) {
+  return x;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---- launchers (host functions), defined in the .cu files ---------------
+
+// k_simt.cu
+cudaError_t launch_sketch_x(int in_type, int kp, const MatDev* mats,
+                            const int2* items, int nitems, void* X,
+                            double* normA2, cudaStream_t s);
+cudaError_t launch_sketch_y(int in_type, int kp, const MatDev* mats,
+                            const int2* items, int nitems, const void* X,
+                            void* Y, cudaStream_t s);
+cudaError_t launch_gram(int in_type, const void* const* dA, long long D,
+                        long long m, long long n, long long lda, int mode,
+                        double* G, cudaStream_t s);
+cudaError_t launch_gemm(bool dbl, int transA, int transB, long long M,
+                        long long N, long long K, double alpha, const void* A,
+                        long long lda, const void* B, long long ldb,
+                        double beta, void* C, long long ldc, cudaStream_t s);
+cudaError_t launch_project_out(bool dbl, int kp, const MatDev* mats,
+                               const int4* items, int nitems, const void* X,
+                               const void* Y, const void* Wm, cudaStream_t s);
+cudaError_t launch_direct_error(int in_type, const MatDev* mats,
+                                const int2* items, int nitems, double* err2,
+                                cudaStream_t s);
+cudaError_t launch_sqrt_inplace(double* v, int count, cudaStream_t s);
+cudaError_t launch_direct_fallback(int in_type, int kp, const MatDev* mats, int count,
+                                   const int* flags, const void* X, const void* Y,
+                                   const void* Wm, void* U2, void* V2, double* err2,
+                                   double* err, cudaStream_t s);
+cudaError_t launch_convert_gram(bool dbl, const double* G, void* out,
+                                long long count, cudaStream_t s);
+cudaError_t launch_random_fill(bool dbl, void* Z, long long count,
+                               unsigned long long seed, cudaStream_t s);
+cudaError_t launch_apply_rinv(bool dbl, const void* P, const void* R,
+                              void* Q, long long rows, int p, cudaStream_t s);
+cudaError_t launch_ritz_residual(bool dbl, const void* U, const void* GU,
+                                 const void* theta, double* res,
+                                 long long rows, int p, int k, cudaStream_t s);
+cudaError_t launch_emit_sketch(bool dbl, const void* U, long long rows, int p,
+                               int k, void* S, cudaStream_t s);
+
+// k_small.cu
+cudaError_t launch_tsqr(bool dbl, int kp, const PanelDev* panels, int count,
+                        int refine, int* status, cudaStream_t s);
+cudaError_t launch_small_svd(bool dbl, int kp, const MatDev* mats, int count,
+                             const void* RX, const void* RY, void* Wm,
+                             double* normA2, double* err, int* flags,
+                             int err_mode, double tau, int* status,
+                             cudaStream_t s);
+cudaError_t launch_sym_eig(bool dbl, const void* H, int p, void* theta,
+                           void* V, cudaStream_t s);
+
+// k_tc.cu (tcgen05 / TMA kernels; BF16)
+struct TcPlan;
+bool tc_supported();
+cudaError_t tc_prepare(TcPlan** out, const MatDev* host_mats,
+                       const MatDev* dev_mats, int count, int kp, void* dev_X,
+                       void* dev_Y, double* dev_normA2,
+                       int* status, long long spin_limit, char* msg,
+                       int msglen);
+cudaError_t tc_launch(TcPlan* p, cudaStream_t s);
+int tc_launches(const TcPlan* p);
+long long tc_workspace_bytes(const TcPlan* p);
+void tc_destroy(TcPlan* p);
+
+}  // namespace tsk

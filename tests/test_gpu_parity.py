@@ -1,0 +1,222 @@
+"""GPU-vs-oracle parity through the C ABI (needs a GB300).
+
+Tolerances (stated by the method's precision lines):
+  * FP64 path: 1e-10 relative on errors, singular values and factors.
+  * FP32 / BF16 paths: relative Frobenius-error gap |err_gpu - err_oracle| /
+    err_oracle <= 1e-3, the oracle run in float64 on the same stored values
+    (BF16 A promoted exactly to float64, the float32 sketch promoted too).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GAP = 1e-3
+FP64_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def tsk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2209_14637_gb300 as mod
+    from paper_2209_14637_gb300 import build
+    build.build()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def handle(tsk):
+    h = tsk.Handle()
+    yield h
+    h.close()
+
+
+def _np(t):
+    return t.detach().double().cpu().numpy()
+
+
+def _oracle_errs(As_np, S_np, r):
+    return [oracle.scw(A, S_np, r, dense=False) for A in As_np]
+
+
+def _gap(g, o):
+    g = np.asarray(g)
+    o = np.asarray(o)
+    return np.max(np.abs(g - o) / o)
+
+
+# ------------------------------------------------------------- FP64 (C1) ---
+def test_c1_fp64_training_matches_oracle(tsk, handle):
+    spec = synth.C1
+    tr = synth.stream(spec, "train", device="cuda")
+    S, W, eig, st = handle.train_sketch(tr, spec.k, l=6)
+    assert st == 0
+    tr_np = list(_np(tr))
+    S_o, W_o, lam1, lam2 = oracle.train_sketch(tr_np, spec.k, l=6)
+    Sg = _np(S)
+    assert np.linalg.norm(Sg @ Sg.T - np.eye(spec.k)) < 1e-12
+    assert np.linalg.norm(Sg.T @ Sg - S_o.T @ S_o) < 1e-9
+    np.testing.assert_allclose(Sg, S_o, atol=1e-9)          # canonical signs too
+    np.testing.assert_allclose(_np(eig)[:spec.k], lam1[:spec.k], rtol=1e-10)
+    Wg = _np(W)
+    assert np.linalg.norm(Wg.T @ Wg - W_o.T @ W_o) < 1e-9
+    np.testing.assert_allclose(_np(eig)[spec.k:], lam2[:6], rtol=1e-10)
+
+
+def test_c1_fp64_test_pass_matches_oracle(tsk, handle):
+    spec = synth.C1
+    tr = synth.stream(spec, "train", device="cuda")
+    te = synth.stream(spec, "test", device="cuda")
+    S_o, _, _, _ = oracle.train_sketch(list(_np(tr)), spec.k)
+    S = torch.tensor(S_o, device="cuda")
+    out = handle.approx_batch(te, S, spec.r, outputs=True)
+    torch.cuda.synchronize()
+    assert handle.sync_status() == 0
+    ref = _oracle_errs(list(_np(te)), S_o, spec.r)
+    err = _np(out["err"])
+    np.testing.assert_allclose(err, [o["err"] for o in ref], rtol=FP64_TOL)
+    np.testing.assert_allclose(_np(out["normA2"]), [o["normA2"] for o in ref], rtol=1e-12)
+    for i, o in enumerate(ref):
+        np.testing.assert_allclose(_np(out["sigma"][i]), o["sigma"], rtol=FP64_TOL)
+        B = _np(out["US"][i]) @ _np(out["Vt"][i])
+        assert np.linalg.norm(B - o["US"] @ o["Vt"]) <= FP64_TOL * np.sqrt(o["normA2"])
+    direct = _np(handle.error(te, S, spec.r, out["US"], out["Vt"]))
+    np.testing.assert_allclose(direct, [o["err"] for o in ref], rtol=FP64_TOL)
+
+
+def test_fp64_edge_cases(tsk, handle):
+    rng = np.random.default_rng(7)
+    cases = [(16, 16, 1, 1), (8, 8, 8, 8), (70, 33, 33, 33), (65, 129, 12, 12),
+             (200, 100, 64, 3), (129, 65, 17, 9)]
+    for m, n, k, r in cases:
+        A = rng.standard_normal((m, n))
+        S = rng.standard_normal((k, m))
+        out = handle.approx_batch([torch.tensor(A, device="cuda")],
+                                  [torch.tensor(S, device="cuda")], r, outputs=True)
+        o = oracle.scw(A, S, r)
+        scale = np.sqrt(o["normA2"])
+        assert abs(float(out["err"][0]) - o["err"]) <= FP64_TOL * scale, (m, n, k, r)
+        np.testing.assert_allclose(_np(out["sigma"][0]), o["sigma"], rtol=1e-9,
+                                   atol=1e-12 * scale)
+        B = _np(out["US"][0]) @ _np(out["Vt"][0])
+        assert np.linalg.norm(B - o["B"]) <= 1e-9 * scale, (m, n, k, r)
+
+
+def test_fp64_ragged_batch(tsk, handle):
+    rng = np.random.default_rng(11)
+    sizes = [(96, 80, 10, 5), (40, 72, 8, 4), (130, 31, 20, 10), (64, 64, 16, 16)]
+    As = [rng.standard_normal((m, n)) for m, n, _, _ in sizes]
+    Ss = [rng.standard_normal((k, m)) for m, _, k, _ in sizes]
+    rs = [r for *_, r in sizes]
+    out = handle.approx_batch([torch.tensor(a, device="cuda") for a in As],
+                              [torch.tensor(s, device="cuda") for s in Ss], rs)
+    for i in range(len(sizes)):
+        o = oracle.scw(As[i], Ss[i], rs[i], dense=False)
+        assert abs(float(out["err"][i]) - o["err"]) <= FP64_TOL * o["err"]
+
+
+def test_gram_parity(tsk, handle):
+    rng = np.random.default_rng(3)
+    As = [rng.standard_normal((70, 45)) for _ in range(5)]
+    for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5), (torch.bfloat16, 1e-5)):
+        T = [torch.tensor(a, device="cuda").to(dt) for a in As]
+        An = [_np(t) for t in T]
+        G1 = _np(handle.gram(T, mode=1))
+        G2 = _np(handle.gram(T, mode=2))
+        R1, R2 = oracle.gram_mode1(An), oracle.gram_mode2(An)
+        assert np.linalg.norm(G1 - R1) <= tol * np.linalg.norm(R1), dt
+        assert np.linalg.norm(G2 - R2) <= tol * np.linalg.norm(R2), dt
+        # partial Gram matrices of two shards sum to the whole
+        G = handle.gram(T[:2], mode=1)
+        handle.gram(T[2:], mode=1, out=G, accumulate=True)
+        assert np.linalg.norm(_np(G) - R1) <= tol * np.linalg.norm(R1)
+
+
+# ---------------------------------------------------- FP32 / BF16 paths ---
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_reduced_precision_scaled(tsk, handle, storage):
+    base = synth.C2 if storage == "f32" else synth.C3
+    k, r = (20, 10) if storage == "f32" else (40, 20)
+    spec = synth.scaled(base, 320, 264, 24, 6, k=k, r=r, storage=storage)
+    tr = synth.stream(spec, "train", device="cuda")
+    te = synth.stream(spec, "test", device="cuda")
+    S_o, _, _, _ = oracle.train_sketch(list(_np(tr)), k)
+    S = torch.tensor(S_o, device="cuda", dtype=torch.float32)
+    out = handle.approx_batch(te, S, r, outputs=True)
+    ref = _oracle_errs(list(_np(te)), _np(S), r)
+    gap = _gap(_np(out["err"]), [o["err"] for o in ref])
+    assert gap <= GAP, gap
+    # training side in the reduced precision: same leading subspace
+    S_g, _, eig, _ = handle.train_sketch(tr, k)
+    Sg = _np(S_g)
+    assert np.linalg.norm(Sg @ Sg.T - np.eye(k)) < 1e-4
+    # the sketch is only determined where the spectrum has a gap; compare
+    # the errors it gives instead of its entries
+    out2 = handle.approx_batch(te, S_g, r)
+    ref2 = _oracle_errs(list(_np(te)), Sg, r)
+    assert _gap(_np(out2["err"]), [o["err"] for o in ref2]) <= GAP
+    assert _gap(_np(out2["err"]), [o["err"] for o in ref]) <= 1e-2
+
+
+def test_bf16_ragged_batch(tsk, handle):
+    items = synth.ragged_sizes(12, m_range=(64, 600), n_range=(64, 400))
+    As, Ss, rs = [], [], []
+    for it in items:
+        g = torch.Generator(device="cuda").manual_seed(it.spec.seed)
+        A = torch.randn(it.m, it.n, generator=g, device="cuda").to(torch.bfloat16)
+        S = torch.randn(it.k, it.m, generator=g, device="cuda")
+        As.append(A)
+        Ss.append(S)
+        rs.append(it.r)
+    out = handle.approx_batch(As, Ss, rs)
+    for i in range(len(items)):
+        o = oracle.scw(_np(As[i]), _np(Ss[i]), rs[i], dense=False)
+        assert abs(float(out["err"][i]) - o["err"]) <= GAP * o["err"], i
+
+
+def test_rank_deficient_sketch_is_reported(tsk, handle):
+    rng = np.random.default_rng(5)
+    A = torch.tensor(rng.standard_normal((64, 48)), device="cuda")
+    S = rng.standard_normal((6, 64))
+    S[3] = S[1]                                    # rank(SA) = 5 < k = 6
+    handle.approx_batch([A], [torch.tensor(S, device="cuda")], 2)
+    assert handle.sync_status() == 6               # TSK_ERANKDEF
+    assert handle.sync_status() == 0               # cleared after reading
+
+
+def test_invalid_arguments_are_rejected(tsk, handle):
+    A = torch.zeros(32, 16, device="cuda")
+    S = torch.zeros(20, 32, device="cuda")         # k = 20 > n = 16
+    with pytest.raises(tsk.TskError):
+        handle.approx_batch([A], [S], 2)
+    S = torch.zeros(4, 32, device="cuda")
+    with pytest.raises(tsk.TskError):
+        handle.approx_batch([A], [S], 5)           # r > k
+
+
+# -------------------------------------------- full size, sampled outputs ---
+def test_c3_full_size_sampled(tsk):
+    """2048 x 2048 BF16, k=40, r=20: the bench's batch of 500 matrices, in
+    the launch configuration the bench uses; 4 sampled outputs checked."""
+    spec = synth.C3
+    h = tsk.Handle()
+    tr = synth.stream(spec, "train", device="cuda", count=16)
+    S, _, _, _ = h.train_sketch(tr, spec.k)
+    del tr
+    te = synth.stream(spec, "test", device="cuda")
+    err = torch.empty(spec.n_test, dtype=torch.float64, device="cuda")
+    plan = h.plan(te, S, spec.r, err)
+    plan.execute()
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    Sn = _np(S)
+    for i in (0, 137, 311, 499):
+        o = oracle.scw(_np(te[i]), Sn, spec.r, dense=False)
+        assert abs(float(err[i]) - o["err"]) <= GAP * o["err"], (i, float(err[i]), o["err"])
+    plan.close()
+    h.close()
