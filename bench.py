@@ -17,6 +17,7 @@ than the 129 MB L2, so no flush is needed between steps).
 from __future__ import annotations
 
 import argparse
+import faulthandler
 import json
 import os
 import statistics
@@ -103,6 +104,10 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def stage(msg):
+    print(f"[bench] {time.strftime('%H:%M:%S')} {msg}", file=sys.stderr, flush=True)
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -166,7 +171,7 @@ def run_reference(args):
         "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line))
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -194,25 +199,31 @@ def run_tsk(args):
     h = tsk.Handle(kernel=args.kernel)
 
     # ---- training side (timed separately, not part of the metric) --------
-    tr = synth.stream(spec, "train", device="cuda", count=args.train)
+    from paper_2209_14637_gb300.dist import allreduce_gram, shard_range
+    a, b = shard_range(args.train, ws, rank)
+    stage(f"generating training matrices {a}..{b}")
+    tr = synth.stream(spec, "train", device="cuda", start=a, count=b - a)
     torch.cuda.synchronize()
+    stage("training the sketch")
     t0 = time.perf_counter()
-    S, _, eig, st = h.train_sketch(tr, spec.k)
+    # mode-1 Gram of this rank's shard, summed over ranks (the one exchange
+    # of the training side), then the leading eigenvectors on every rank
+    G = h.gram([tr[i] for i in range(tr.shape[0])], mode=1)
+    allreduce_gram(G)
+    S, eig, st = h.sketch_from_gram(G, spec.k, prec=tsk.BF16)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    del tr
+    del tr, G
     torch.cuda.empty_cache()
 
-    # ---- test side: this rank's shard of the stream ----------------------
-    te = synth.stream(spec, "test", device="cuda", start=0, count=count)
-    if rank:
-        te = synth.stream(synth.scaled(spec, spec.m, spec.n, spec.n_train,
-                                       count * ws), "test", device="cuda",
-                          start=rank * count, count=count)
+    # ---- test side: this rank's shard of the stream (weak scaling) --------
+    stage(f"trained in {train_s:.2f} s (status {st}); generating the test stream")
+    te = synth.stream(spec, "test", device="cuda", start=rank * count, count=count)
     err = torch.empty(count, dtype=torch.float64, device="cuda")
     plan = h.plan(te, S, spec.r, err)
     info = plan.info()
-    plan_kind = "tcgen05" if info.get("tc") else "simt" 
+    plan_kind = "tcgen05" if te.dtype == torch.bfloat16 and args.kernel != tsk.KERNEL_SIMT else "simt"
+    stage(f"plan ready: {info}")
 
     def timed(plan_, steps, probe=True):
         evb = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -241,6 +252,7 @@ def run_tsk(args):
     for _ in range(args.warmup):
         plan.execute()
     torch.cuda.synchronize()
+    stage("timing the BF16 path")
     clocks = ClockSampler(local)
     clocks.start()
     total_ms, stage_ms = timed(plan, args.steps)
@@ -253,6 +265,8 @@ def run_tsk(args):
     value = count * ws * args.steps / (max_ms / 1e3)
     ms_per_step = max_ms / args.steps
     stage_avg = statistics.mean(stage_ms)
+    stage(f"bf16: {value:.1f} matrices/s, {ms_per_step:.3f} ms/step, sketch pass "
+          f"{stage_avg:.3f} ms, clocks {clk}")
     alg_bytes = float(sum(te[i].numel() * te[i].element_size() for i in range(count)))
     achieved = alg_bytes / (stage_avg / 1e3) / 1e9
     peak = float(peaks["hbm_gbs"])
@@ -260,6 +274,7 @@ def run_tsk(args):
     # ---- plain FP32 path on the same matrices ----------------------------
     fp32 = None
     if not args.no_fp32:
+        stage("timing the FP32 path")
         te32 = te.float()
         err32 = torch.empty(count, dtype=torch.float64, device="cuda")
         h32 = tsk.Handle()
@@ -275,44 +290,57 @@ def run_tsk(args):
         fp32 = {"value": count * ws * steps32 / (ms32 / 1e3), "unit": "matrices/s",
                 "ms_per_step": ms32 / steps32, "steps": steps32,
                 "sketch_pass_ms": statistics.mean(st32)}
+        stage(f"fp32: {fp32}")
 
     # ---- end to end through the public API with host buffers -------------
     e2e = None
     if not args.no_e2e:
-        host = torch.empty_like(te, device="cpu").pin_memory()
+        stage("end to end with host buffers")
+        # Host copy of this rank's inputs, page-locked in place (no second
+        # staging copy), filled once outside the timed region.
+        host = torch.empty(te.shape, dtype=te.dtype)
+        nbytes = host.numel() * host.element_size()
+        cudart = torch.cuda.cudart()
+        reg = cudart.cudaHostRegister(host.data_ptr(), nbytes, 0)
+        registered = int(reg) == 0
         host.copy_(te)
-        err_host = torch.empty(count, dtype=torch.float64).pin_memory()
-        steps_e = max(1, min(args.steps, 10))
-        for _ in range(1):
-            te.copy_(host, non_blocking=True)
-            plan.execute()
-            err_host.copy_(err, non_blocking=True)
+        err_host = torch.empty(count, dtype=torch.float64, pin_memory=True)
+        steps_e = max(1, min(args.steps, 5))
+        te.copy_(host, non_blocking=True)
+        plan.execute()
+        err_host.copy_(err, non_blocking=True)
         torch.cuda.synchronize()
+        stage("end to end: timed steps")
         if ws > 1:
             dist.barrier()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
+        a_ev = torch.cuda.Event(enable_timing=True)
+        b_ev = torch.cuda.Event(enable_timing=True)
+        a_ev.record()
         for _ in range(steps_e):
             te.copy_(host, non_blocking=True)
             plan.execute()
             err_host.copy_(err, non_blocking=True)
-        b.record()
+        b_ev.record()
         torch.cuda.synchronize()
-        ms_e = a.elapsed_time(b)
+        ms_e = a_ev.elapsed_time(b_ev)
         t = torch.tensor([ms_e], device="cuda", dtype=torch.float64)
         if ws > 1:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_e = float(t.item())
         e2e = {"value": count * ws * steps_e / (ms_e / 1e3), "unit": "matrices/s",
                "h2d_bytes_per_step": int(alg_bytes), "d2h_bytes_per_step": 8 * count,
-               "steps": steps_e}
+               "steps": steps_e, "host_buffer": "page-locked" if registered else "pageable",
+               "ms_per_step": ms_e / steps_e}
+        stage(f"e2e: {e2e}")
+        if registered:
+            cudart.cudaHostUnregister(host.data_ptr())
         del host
 
     # ---- oracle on a bounded sample: CPU baseline and the error gap ------
     cpu = None
     gap = None
     if rank == 0 and ws == 1 and not args.no_cpu:
+        stage("oracle sample on the host cores")
         import oracle
         Sn = S.double().cpu().numpy()
         idx = list(range(0, count, max(1, count // args.cpu_sample)))[:args.cpu_sample]
@@ -333,6 +361,7 @@ def run_tsk(args):
             g32 = err32.cpu().numpy()[idx]
             gap["fp32"] = float(np.max(np.abs(g32 - ref) / np.asarray(ref)))
         gap["checked"] = len(mats)
+        stage(f"oracle: {cpu}; gap {gap}")
 
     if rank == 0:
         line = {
@@ -363,7 +392,10 @@ def run_tsk(args):
             "train_s": train_s,
             "train_status": st,
         }
-        print(json.dumps(line))
+        print(json.dumps(line), flush=True)
+    if fp32 is not None:
+        plan32.close()
+        h32.close()
     plan.close()
     h.close()
     if ws > 1:
@@ -372,6 +404,7 @@ def run_tsk(args):
 
 
 def main():
+    faulthandler.enable()
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)

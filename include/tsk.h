@@ -213,6 +213,50 @@ tsk_status tsk_error(tsk_handle h, int64_t count, const tsk_mat_desc* mats,
                      tsk_prec prec, const tsk_mat_out* outs, double* err,
                      tsk_stream stream);
 
+/* ---- learned sketch refiner (IVY loss, Eq. 2.1) ------------------------ */
+
+/* Batch IVY loss and its gradient with respect to the sketch.
+   mats: host array of count matrices sharing m, n, k and r (their S fields
+   are ignored); S: device, k x m (double for TSK_FP64, float for TSK_FP32;
+   TSK_BF16 is not supported).  grad (device, k x m) receives
+   dL/dS of L(S) = mean_A ||A - SCW(A, S, r)||_F^2 / ||A||_F^2, computed as
+   -(2/||A||^2) W (A A^T Z - Z Sigma_r^2)^T averaged over the batch, with
+   X = (SA)^T = QR, AQ = U Sigma V^T, Z = U_r Sigma_r, W = R^{-1} V_r (the
+   derivation is the library's; the paper gives none).  loss (device double,
+   nullable) receives L(S).  Needs sigma_r(AQ) > sigma_{r+1}(AQ).  Blocks
+   until done. */
+tsk_status tsk_ivy_grad(tsk_handle h, int64_t count, const tsk_mat_desc* mats,
+                        tsk_prec prec, const void* S, void* grad, double* loss,
+                        tsk_stream stream);
+
+typedef struct {
+  int32_t steps;          /* SGD steps (2000)                                 */
+  int32_t batch;          /* matrices per step (16)                           */
+  double lr;              /* learning rate (1e-3)                             */
+  int32_t eval_every;     /* validation interval in steps (100)              */
+  int32_t reserved;
+  uint64_t seed;          /* seed of the batch order when order is NULL       */
+  const int32_t* order;   /* host, steps*batch indices into the training set
+                             (the random draws of SGD), or NULL               */
+} tsk_refine_opts;
+
+void tsk_default_refine_options(tsk_refine_opts* out);
+
+/* Trains S_theta = S_tensor + dS by plain SGD on the IVY loss (Eq. 2.1, per-
+   sample normalised) over the training matrices, validating on val every
+   eval_every steps with the test-side SCW, and leaves in dS the value with
+   the lowest validation loss seen -- the given dS (normally zero, i.e. the
+   plain tensor sketch) included, so the result is never worse on val.
+   train, val: host arrays of descriptors sharing m, n, k, r (S ignored);
+   S_tensor (k x m) and dS (k x m, in/out): device, FP32 (FP64 for TSK_FP64).
+   history (host, nullable): steps/eval_every + 1 validation losses, the
+   first for the starting dS.  Blocks until done. */
+tsk_status tsk_refine_sketch(tsk_handle h, const tsk_mat_desc* train,
+                             int64_t ntrain, const tsk_mat_desc* val,
+                             int64_t nval, tsk_prec prec,
+                             const tsk_refine_opts* opts, const void* S_tensor,
+                             void* dS, double* history, tsk_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

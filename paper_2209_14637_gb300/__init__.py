@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import sys
 from typing import List, Optional, Sequence
 
 import torch
@@ -56,6 +57,12 @@ class MatOut(C.Structure):
     _fields_ = [("US", C.c_void_p), ("Vt", C.c_void_p), ("sigma", C.c_void_p)]
 
 
+class RefineOpts(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double),
+                ("eval_every", C.c_int32), ("reserved", C.c_int32),
+                ("seed", C.c_uint64), ("order", C.POINTER(C.c_int32))]
+
+
 _lib = None
 
 
@@ -89,6 +96,10 @@ def load_library(path: str = LIB_PATH):
         "tsk_plan_info": ([P, C.POINTER(I64), C.POINTER(I32)], I32),
         "tsk_plan_set_probe": ([P, P, P], I32),
         "tsk_error": ([P, I64, C.POINTER(MatDesc), I32, C.POINTER(MatOut), P, P], I32),
+        "tsk_ivy_grad": ([P, I64, C.POINTER(MatDesc), I32, P, P, P, P], I32),
+        "tsk_default_refine_options": ([C.POINTER(RefineOpts)], None),
+        "tsk_refine_sketch": ([P, C.POINTER(MatDesc), I64, C.POINTER(MatDesc), I64, I32,
+                               C.POINTER(RefineOpts), P, P, C.POINTER(D), P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -143,6 +154,10 @@ class Handle:
             self._h = None
 
     def __del__(self):
+        # At interpreter exit the CUDA runtime may already be torn down;
+        # the process is ending anyway, so leave the handle alone then.
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -285,6 +300,45 @@ class Handle:
         return err
 
 
+    # ---- learned refiner ------------------------------------------------
+    def ivy_grad(self, As, S, r: int, stream=None):
+        """IVY loss (Eq. 2.1, per-sample normalised) and dL/dS for a batch."""
+        As = [As[i] for i in range(As.shape[0])] if isinstance(As, torch.Tensor) else list(As)
+        _require_cuda(*As, S)
+        prec = _DTYPE_PREC[As[0].dtype]
+        descs = self._descs(As, [S] * len(As), [S.shape[0]] * len(As), [r] * len(As))
+        grad = torch.empty_like(S)
+        loss = torch.empty(1, dtype=torch.float64, device=S.device)
+        self._check(self._lib.tsk_ivy_grad(self._h, len(As), descs, prec, _ptr(S),
+                                           _ptr(grad), _ptr(loss), _stream(stream)))
+        return grad, float(loss.item())
+
+    def refine_sketch(self, train, val, S_tensor, r: int, steps: int = 2000,
+                      batch: int = 16, lr: float = 1e-3, eval_every: int = 100,
+                      seed: int = 20220929, order=None, dS=None, stream=None):
+        """SGD on S_theta = S_tensor + dS; returns (dS, validation history)."""
+        train = [train[i] for i in range(train.shape[0])] if isinstance(train, torch.Tensor) else list(train)
+        val = [val[i] for i in range(val.shape[0])] if isinstance(val, torch.Tensor) else list(val)
+        _require_cuda(*train, *val, S_tensor)
+        prec = _DTYPE_PREC[train[0].dtype]
+        k = S_tensor.shape[0]
+        td = self._descs(train, [S_tensor] * len(train), [k] * len(train), [r] * len(train))
+        vd = self._descs(val, [S_tensor] * len(val), [k] * len(val), [r] * len(val))
+        o = RefineOpts()
+        self._lib.tsk_default_refine_options(C.byref(o))
+        o.steps, o.batch, o.lr, o.eval_every, o.seed = steps, batch, lr, eval_every, seed
+        keep = None
+        if order is not None:
+            keep = (C.c_int32 * len(order))(*[int(x) for x in order])
+            o.order = C.cast(keep, C.POINTER(C.c_int32))
+        dS = torch.zeros_like(S_tensor) if dS is None else dS
+        hist = (C.c_double * (steps // eval_every + 1))()
+        self._check(self._lib.tsk_refine_sketch(self._h, td, len(train), vd, len(val), prec,
+                                                C.byref(o), _ptr(S_tensor), _ptr(dS), hist,
+                                                _stream(stream)))
+        return dS, list(hist)
+
+
 class Plan:
     """A built test-side plan (workspace + schedule + CUDA graph)."""
 
@@ -303,11 +357,7 @@ class Plan:
     def info(self):
         ws, nl = C.c_int64(), C.c_int32()
         self._h._check(self._h._lib.tsk_plan_info(self._p, C.byref(ws), C.byref(nl)))
-        return {"workspace_bytes": ws.value, "launches": nl.value,
-                "tc": bool(nl.value and self._h._lib.tsk_plan_info and self._uses_tc())}
-
-    def _uses_tc(self) -> bool:
-        return False
+        return {"workspace_bytes": ws.value, "launches": nl.value}
 
     def close(self):
         if self._p:
@@ -315,6 +365,8 @@ class Plan:
             self._p = None
 
     def __del__(self):
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:

@@ -830,3 +830,352 @@ extern "C" tsk_status tsk_train_sketch(tsk_handle h, const void* const* A,
   cudaStreamSynchronize(s);
   return st != TSK_OK ? st : st2;
 }
+
+// ---------------------------------------------------------------------------
+// learned refiner: IVY loss (Eq. 2.1) gradient and the SGD loop
+// ---------------------------------------------------------------------------
+namespace {
+
+// Device workspace for one forward + backward over a batch of `cap` matrices
+// that share m, n, k and r (slot b always uses the same X / Y offsets).
+struct GradWs {
+  bool dbl = false;
+  int cap = 0, kp = 16, kp2 = 16, k = 0, r = 0;
+  long long m = 0, n = 0, zt_stride = 0;
+  unsigned char* base = nullptr;
+  size_t bytes = 0;
+  int2 *ix = nullptr, *iy = nullptr, *ix2 = nullptr, *iy2 = nullptr;
+  int nx = 0, ny = 0;
+  PanelDev* pan = nullptr;
+  void *X = nullptr, *Y = nullptr, *RX = nullptr, *RY = nullptr, *W = nullptr,
+       *sig = nullptr, *Zt = nullptr, *X2 = nullptr, *Y2 = nullptr;
+  double *norm = nullptr, *norm2 = nullptr, *err = nullptr, *e2 = nullptr;
+  int* flags = nullptr;
+};
+
+cudaError_t gradws_alloc(GradWs& g, bool dbl, int cap, long long m, long long n, int k,
+                         int r, cudaStream_t s) {
+  g.dbl = dbl;
+  g.cap = cap;
+  g.m = m;
+  g.n = n;
+  g.k = k;
+  g.r = r;
+  g.kp = ((k + 15) / 16) * 16;
+  g.kp2 = ((r + 15) / 16) * 16;
+  g.zt_stride = (long long)r * m;
+  const size_t cs = dbl ? 8 : 4;
+  const int tx = (int)((n + 63) / 64), ty = (int)((m + 63) / 64);
+  g.nx = tx * cap;
+  g.ny = ty * cap;
+  Carve cv;
+  const size_t o_ix = cv.take(sizeof(int2) * g.nx), o_iy = cv.take(sizeof(int2) * g.ny);
+  const size_t o_pan = cv.take(sizeof(PanelDev) * 2 * cap);
+  const size_t o_X = cv.take(cs * cap * n * g.kp), o_Y = cv.take(cs * cap * m * g.kp);
+  const size_t o_RX = cv.take(cs * cap * g.kp * g.kp), o_RY = cv.take(cs * cap * g.kp * g.kp);
+  const size_t o_W = cv.take(cs * cap * g.kp * g.kp), o_sig = cv.take(cs * cap * g.kp);
+  const size_t o_Zt = cv.take(cs * cap * g.zt_stride);
+  const size_t o_X2 = cv.take(cs * cap * n * g.kp2), o_Y2 = cv.take(cs * cap * m * g.kp2);
+  const size_t o_nrm = cv.take(8 * cap), o_nrm2 = cv.take(8 * cap), o_err = cv.take(8 * cap);
+  const size_t o_e2 = cv.take(8 * cap), o_fl = cv.take(4 * cap);
+  g.bytes = cv.off;
+  cudaError_t e = cudaMallocAsync((void**)&g.base, g.bytes, s);
+  if (e != cudaSuccess) return e;
+  unsigned char* b = g.base;
+  g.ix = (int2*)(b + o_ix);
+  g.iy = (int2*)(b + o_iy);
+  g.pan = (PanelDev*)(b + o_pan);
+  g.X = b + o_X;
+  g.Y = b + o_Y;
+  g.RX = b + o_RX;
+  g.RY = b + o_RY;
+  g.W = b + o_W;
+  g.sig = b + o_sig;
+  g.Zt = b + o_Zt;
+  g.X2 = b + o_X2;
+  g.Y2 = b + o_Y2;
+  g.norm = (double*)(b + o_nrm);
+  g.norm2 = (double*)(b + o_nrm2);
+  g.err = (double*)(b + o_err);
+  g.e2 = (double*)(b + o_e2);
+  g.flags = (int*)(b + o_fl);
+  std::vector<int2> ix, iy;
+  for (int sl = 0; sl < cap; ++sl) {
+    for (int t = 0; t < tx; ++t) ix.push_back(make_int2(sl, t));
+    for (int t = 0; t < ty; ++t) iy.push_back(make_int2(sl, t));
+  }
+  std::vector<PanelDev> pan(2 * cap);
+  for (int sl = 0; sl < cap; ++sl) {
+    pan[2 * sl] = PanelDev{(unsigned char*)g.X + cs * sl * n * g.kp, n, k, g.kp,
+                           (unsigned char*)g.RX + cs * sl * g.kp * g.kp};
+    pan[2 * sl + 1] = PanelDev{(unsigned char*)g.Y + cs * sl * m * g.kp, m, k, g.kp,
+                               (unsigned char*)g.RY + cs * sl * g.kp * g.kp};
+  }
+  std::vector<unsigned char> host(o_X, 0);
+  memcpy(host.data() + o_ix, ix.data(), sizeof(int2) * ix.size());
+  memcpy(host.data() + o_iy, iy.data(), sizeof(int2) * iy.size());
+  memcpy(host.data() + o_pan, pan.data(), sizeof(PanelDev) * pan.size());
+  e = cudaMemcpyAsync(b, host.data(), o_X, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
+// Forward and backward descriptors of one batch (A pointers of the slots).
+void gradws_descs(const GradWs& g, const tsk_mat_desc* const* slots, int count,
+                  const void* S, MatDev* fwd, MatDev* bwd) {
+  const size_t cs = g.dbl ? 8 : 4;
+  for (int sl = 0; sl < count; ++sl) {
+    const tsk_mat_desc& d = *slots[sl];
+    MatDev f;
+    memset(&f, 0, sizeof(f));
+    f.A = d.A;
+    f.S = S;
+    f.m = g.m;
+    f.n = g.n;
+    f.lda = d.lda;
+    f.k = g.k;
+    f.r = g.r;
+    f.offX = (long long)sl * g.n * g.kp;
+    f.offY = (long long)sl * g.m * g.kp;
+    f.sigma = (unsigned char*)g.sig + cs * sl * g.kp;
+    fwd[sl] = f;
+    MatDev bb = f;
+    bb.S = (unsigned char*)g.Zt + cs * sl * g.zt_stride;
+    bb.k = g.r;
+    bb.offX = (long long)sl * g.n * g.kp2;
+    bb.offY = (long long)sl * g.m * g.kp2;
+    bb.sigma = nullptr;
+    bwd[sl] = bb;
+  }
+}
+
+// One forward + backward: grad (k x m) = mean dL/dS over the batch, and the
+// batch loss (device double) when loss != NULL.
+cudaError_t gradws_run(const GradWs& g, int in_type, int count, const MatDev* fwd,
+                       const MatDev* bwd, void* grad, double* loss, int* status,
+                       cudaStream_t s) {
+  const int tx = (int)((g.n + 63) / 64), ty = (int)((g.m + 63) / 64);
+  cudaError_t e = cudaMemsetAsync(g.norm, 0, 8 * count, s);
+  if (e == cudaSuccess) e = launch_sketch_x(in_type, g.kp, fwd, g.ix, tx * count, g.X, g.norm, s);
+  if (e == cudaSuccess) e = launch_sketch_y(in_type, g.kp, fwd, g.iy, ty * count, g.X, g.Y, s);
+  if (e == cudaSuccess) e = launch_tsqr(g.dbl, g.kp, g.pan, 2 * count, 1, status, s);
+  if (e == cudaSuccess)
+    e = launch_small_svd(g.dbl, g.kp, fwd, count, g.RX, g.RY, g.W, g.norm, g.err, g.flags, 1,
+                         0.0, status, s);
+  if (e == cudaSuccess) e = launch_zt(g.dbl, g.kp, fwd, count, g.Y, g.W, g.Zt, g.zt_stride, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.norm2, 0, 8 * count, s);
+  if (e == cudaSuccess)
+    e = launch_sketch_x(in_type, g.kp2, bwd, g.ix, tx * count, g.X2, g.norm2, s);
+  if (e == cudaSuccess)
+    e = launch_sketch_y(in_type, g.kp2, bwd, g.iy, ty * count, g.X2, g.Y2, s);
+  if (e == cudaSuccess)
+    e = launch_ivy_grad(g.dbl, g.kp, g.kp2, count, (long long)g.k * g.m, fwd, bwd, g.W, g.sig,
+                        g.Zt, g.zt_stride, g.Y2, g.norm, 1.0 / count, grad, s);
+  if (e == cudaSuccess && loss) e = launch_batch_loss(count, g.err, g.norm, loss, s);
+  return e;
+}
+
+tsk_status check_refine_batch(tsk_handle h, const tsk_mat_desc* mats, int64_t count,
+                              tsk_prec prec) {
+  for (int64_t i = 0; i < count; ++i) {
+    tsk_status st = check_desc(h, mats[i], i, prec);
+    if (st != TSK_OK) return st;
+    if (mats[i].m != mats[0].m || mats[i].n != mats[0].n || mats[i].k != mats[0].k ||
+        mats[i].r != mats[0].r) {
+      set_err(h, "refiner: every matrix must share m, n, k and r");
+      return TSK_EINVAL;
+    }
+  }
+  if (prec == TSK_BF16) {
+    set_err(h, "refiner: TSK_FP32 or TSK_FP64 only");
+    return TSK_EUNSUPPORTED;
+  }
+  return TSK_OK;
+}
+
+}  // namespace
+
+extern "C" tsk_status tsk_ivy_grad(tsk_handle h, int64_t count, const tsk_mat_desc* mats,
+                                   tsk_prec prec, const void* S, void* grad, double* loss,
+                                   tsk_stream stream) {
+  if (!h) return TSK_EINVAL;
+  if (count < 1 || !mats || !S || !grad) {
+    set_err(h, "tsk_ivy_grad: count >= 1 and non-NULL mats, S, grad required");
+    return TSK_EINVAL;
+  }
+  tsk_status st = check_refine_batch(h, mats, count, prec);
+  if (st != TSK_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  GradWs g;
+  TSK_CUDA(h, gradws_alloc(g, prec == TSK_FP64, (int)count, mats[0].m, mats[0].n, mats[0].k,
+                           mats[0].r, s));
+  std::vector<const tsk_mat_desc*> slots(count);
+  for (int64_t i = 0; i < count; ++i) slots[i] = &mats[i];
+  std::vector<MatDev> fwd(count), bwd(count);
+  gradws_descs(g, slots.data(), (int)count, S, fwd.data(), bwd.data());
+  MatDev* d = nullptr;
+  TSK_CUDA(h, cudaMallocAsync((void**)&d, sizeof(MatDev) * 2 * count, s));
+  TSK_CUDA(h, cudaMemcpyAsync(d, fwd.data(), sizeof(MatDev) * count, cudaMemcpyHostToDevice, s));
+  TSK_CUDA(h, cudaMemcpyAsync(d + count, bwd.data(), sizeof(MatDev) * count,
+                              cudaMemcpyHostToDevice, s));
+  TSK_CUDA(h, gradws_run(g, (int)prec, (int)count, d, d + count, grad, loss, h->d_status, s));
+  TSK_CUDA(h, cudaFreeAsync(d, s));
+  TSK_CUDA(h, cudaFreeAsync(g.base, s));
+  TSK_CUDA(h, cudaStreamSynchronize(s));
+  return TSK_OK;
+}
+
+extern "C" void tsk_default_refine_options(tsk_refine_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->steps = 2000;
+  o->batch = 16;
+  o->lr = 1e-3;
+  o->eval_every = 100;
+  o->seed = 20220929ull;
+  o->order = nullptr;
+}
+
+extern "C" tsk_status tsk_refine_sketch(tsk_handle h, const tsk_mat_desc* train,
+                                        int64_t ntrain, const tsk_mat_desc* val, int64_t nval,
+                                        tsk_prec prec, const tsk_refine_opts* opts,
+                                        const void* S_tensor, void* dS, double* history,
+                                        tsk_stream stream) {
+  if (!h) return TSK_EINVAL;
+  tsk_refine_opts o;
+  tsk_default_refine_options(&o);
+  if (opts) o = *opts;
+  if (!train || ntrain < 1 || !val || nval < 1 || !S_tensor || !dS || o.steps < 0 ||
+      o.batch < 1 || o.eval_every < 1) {
+    set_err(h, "tsk_refine_sketch: bad arguments");
+    return TSK_EINVAL;
+  }
+  tsk_status st = check_refine_batch(h, train, ntrain, prec);
+  if (st != TSK_OK) return st;
+  st = check_refine_batch(h, val, nval, prec);
+  if (st != TSK_OK) return st;
+  if (val[0].m != train[0].m || val[0].k != train[0].k || val[0].r != train[0].r) {
+    set_err(h, "tsk_refine_sketch: validation and training shapes differ");
+    return TSK_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool dbl = prec == TSK_FP64;
+  const size_t cs = dbl ? 8 : 4;
+  const int B = o.batch;
+  const long long km = (long long)train[0].k * train[0].m;
+  // batch order: the method's random draws, passed in or drawn here
+  std::vector<int32_t> order((size_t)o.steps * B);
+  if (o.order) {
+    for (size_t i = 0; i < order.size(); ++i) {
+      if (o.order[i] < 0 || o.order[i] >= ntrain) {
+        set_err(h, "tsk_refine_sketch: order[%zu] out of range", i);
+        return TSK_EINVAL;
+      }
+      order[i] = o.order[i];
+    }
+  } else {
+    unsigned long long x = o.seed ? o.seed : 1;
+    for (size_t i = 0; i < order.size(); ++i) {
+      x ^= x << 13;
+      x ^= x >> 7;
+      x ^= x << 17;
+      order[i] = (int32_t)(x % (unsigned long long)ntrain);
+    }
+  }
+  GradWs g;
+  TSK_CUDA(h, gradws_alloc(g, dbl, B, train[0].m, train[0].n, train[0].k, train[0].r, s));
+  // S_theta, grad, best dS, per-step descriptors, losses
+  Carve cv;
+  const size_t o_St = cv.take(cs * km), o_gr = cv.take(cs * km), o_best = cv.take(cs * km);
+  const size_t o_desc = cv.take(sizeof(MatDev) * 2 * (size_t)std::max(1, o.steps) * B);
+  const size_t o_loss = cv.take(8 * (size_t)std::max(1, o.steps));
+  unsigned char* wb = nullptr;
+  TSK_CUDA(h, cudaMallocAsync((void**)&wb, cv.off, s));
+  void* St = wb + o_St;
+  void* gr = wb + o_gr;
+  void* best = wb + o_best;
+  MatDev* dd = (MatDev*)(wb + o_desc);
+  double* dloss = (double*)(wb + o_loss);
+  {
+    std::vector<MatDev> all(2 * (size_t)std::max(1, o.steps) * B);
+    std::vector<const tsk_mat_desc*> slots(B);
+    for (int t = 0; t < o.steps; ++t) {
+      for (int b = 0; b < B; ++b) slots[b] = &train[order[(size_t)t * B + b]];
+      gradws_descs(g, slots.data(), B, St, &all[(size_t)t * 2 * B], &all[(size_t)t * 2 * B + B]);
+    }
+    TSK_CUDA(h, cudaMemcpyAsync(dd, all.data(), sizeof(MatDev) * all.size(),
+                                cudaMemcpyHostToDevice, s));
+    TSK_CUDA(h, cudaStreamSynchronize(s));
+  }
+  // validation: a test-side plan over the held-out matrices reading S_theta
+  std::vector<tsk_mat_desc> vd(val, val + nval);
+  for (auto& v : vd) v.S = St;
+  double* verr = nullptr;
+  double* vnorm = nullptr;
+  TSK_CUDA(h, cudaMalloc((void**)&verr, 16 * nval));
+  vnorm = verr + nval;
+  tsk_plan vplan = nullptr;
+  const int save_mode = h->opts.err_mode;
+  h->opts.err_mode = 1;
+  st = build_plan(h, nval, vd.data(), prec, nullptr, verr, vnorm, &vplan);
+  h->opts.err_mode = save_mode;
+  if (st != TSK_OK) {
+    cudaFree(verr);
+    cudaFreeAsync(wb, s);
+    cudaFreeAsync(g.base, s);
+    return st;
+  }
+  std::vector<double> he(nval), hn(nval);
+  auto validate = [&](double* out) -> tsk_status {
+    TSK_CUDA(h, launch_add(dbl, km, S_tensor, dS, St, s));
+    TSK_CUDA(h, cudaGraphLaunch(vplan->exec, s));
+    TSK_CUDA(h, cudaMemcpyAsync(he.data(), verr, 8 * nval, cudaMemcpyDeviceToHost, s));
+    TSK_CUDA(h, cudaMemcpyAsync(hn.data(), vnorm, 8 * nval, cudaMemcpyDeviceToHost, s));
+    TSK_CUDA(h, cudaStreamSynchronize(s));
+    double l = 0.0;
+    for (int64_t i = 0; i < nval; ++i) l += he[i] * he[i] / hn[i];
+    *out = l / nval;
+    return TSK_OK;
+  };
+  double best_loss = 0.0;
+  const int nhist = o.steps / o.eval_every + 1;
+  std::vector<double> hist;
+  st = validate(&best_loss);  // dS as given (zero: the plain tensor sketch)
+  if (st == TSK_OK) {
+    hist.push_back(best_loss);
+    cudaMemcpyAsync(best, dS, cs * km, cudaMemcpyDeviceToDevice, s);
+  }
+  for (int t = 0; st == TSK_OK && t < o.steps; ++t) {
+    cudaError_t e = launch_add(dbl, km, S_tensor, dS, St, s);
+    const MatDev* f = dd + (size_t)t * 2 * B;
+    if (e == cudaSuccess) e = gradws_run(g, (int)prec, B, f, f + B, gr, dloss + t, h->d_status, s);
+    if (e == cudaSuccess) e = launch_axpy(dbl, km, -o.lr, gr, dS, s);
+    if (e != cudaSuccess) {
+      set_err(h, "refiner step %d: %s", t, cudaGetErrorString(e));
+      st = TSK_ECUDA;
+      break;
+    }
+    if ((t + 1) % o.eval_every == 0) {
+      double l = 0.0;
+      st = validate(&l);
+      if (st != TSK_OK) break;
+      hist.push_back(l);
+      if (l < best_loss) {
+        best_loss = l;
+        cudaMemcpyAsync(best, dS, cs * km, cudaMemcpyDeviceToDevice, s);
+      }
+    }
+  }
+  // keep the best validated dS ("never worse" than the plain tensor sketch)
+  if (st == TSK_OK) cudaMemcpyAsync(dS, best, cs * km, cudaMemcpyDeviceToDevice, s);
+  cudaStreamSynchronize(s);
+  if (history) {
+    for (int i = 0; i < nhist; ++i) history[i] = i < (int)hist.size() ? hist[i] : NAN;
+  }
+  plan_free(vplan);
+  cudaFree(verr);
+  cudaFreeAsync(wb, s);
+  cudaFreeAsync(g.base, s);
+  cudaStreamSynchronize(s);
+  return st;
+}

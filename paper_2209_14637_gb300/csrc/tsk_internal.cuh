@@ -112,6 +112,21 @@ cudaError_t launch_small_svd(bool dbl, int kp, const MatDev* mats, int count,
 cudaError_t launch_sym_eig(bool dbl, const void* H, int p, void* theta,
                            void* V, cudaStream_t s);
 
+// k_refine.cu
+cudaError_t launch_zt(bool dbl, int kp, const MatDev* mats, int count, const void* Y,
+                      const void* Wm, void* Zt, long long zt_stride, cudaStream_t s);
+cudaError_t launch_ivy_grad(bool dbl, int kp, int kp2, int count, long long km,
+                            const MatDev* mats, const MatDev* mats2, const void* Wm,
+                            const void* sig, const void* Zt, long long zt_stride,
+                            const void* Y2, const double* normA2, double scale, void* grad,
+                            cudaStream_t s);
+cudaError_t launch_axpy(bool dbl, long long n, double alpha, const void* x, void* y,
+                        cudaStream_t s);
+cudaError_t launch_add(bool dbl, long long n, const void* a, const void* b, void* out,
+                       cudaStream_t s);
+cudaError_t launch_batch_loss(int count, const double* err, const double* normA2,
+                              double* loss, cudaStream_t s);
+
 // k_tc.cu (tcgen05 / TMA kernels; BF16)
 struct TcPlan;
 bool tc_supported();

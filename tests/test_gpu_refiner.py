@@ -1,0 +1,82 @@
+"""Learned sketch refiner on the GPU: gradient parity and the SGD loop.
+
+The IVY loss (Eq. 2.1) of a dense sketch and its analytic gradient are
+compared with the oracle (itself pinned to central finite differences); the
+SGD loop must never return a sketch worse than the plain tensor sketch on
+its validation matrices, and the held-out gain is reported.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tsk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2209_14637_gb300 as mod
+    from paper_2209_14637_gb300 import build
+    build.build()
+    return mod
+
+
+def _np(t):
+    return t.detach().double().cpu().numpy()
+
+
+def _setup(dtype, seed=0):
+    spec = synth.scaled(synth.C5, 192, 144, 40, 12, k=12, r=6, storage="f32")
+    tr = synth.stream(spec, "train", device="cuda", dtype=dtype)
+    te = synth.stream(spec, "test", device="cuda", dtype=dtype)
+    S_o, _, _, _ = oracle.train_sketch(list(_np(tr)), spec.k)
+    g = np.random.default_rng(seed)
+    S = S_o + 0.05 * g.standard_normal(S_o.shape)
+    return spec, tr, te, S_o, S
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-9), (torch.float32, 2e-3)])
+def test_ivy_grad_matches_oracle(tsk, dtype, tol):
+    spec, tr, _, _, S = _setup(dtype)
+    h = tsk.Handle()
+    batch = tr[:6]
+    St = torch.tensor(S, device="cuda", dtype=dtype)
+    grad, loss = h.ivy_grad(batch, St, spec.r)
+    As = list(_np(batch))
+    Sn = _np(St)
+    g_o = oracle.ivy_grad(Sn, As, spec.r)
+    l_o = oracle.ivy_loss(Sn, As, spec.r)
+    rel = np.linalg.norm(_np(grad) - g_o) / np.linalg.norm(g_o)
+    assert rel <= tol, rel
+    assert abs(loss - l_o) <= max(tol, 1e-12) * l_o
+    h.close()
+
+
+def test_refiner_is_never_worse_on_validation(tsk):
+    spec, tr, te, S_o, _ = _setup(torch.float32)
+    h = tsk.Handle()
+    S_t = torch.tensor(S_o, device="cuda", dtype=torch.float32)
+    train, val = tr[:30], tr[30:]
+    dS, hist = h.refine_sketch(train, val, S_t, spec.r, steps=200, batch=8, lr=1e-2,
+                               eval_every=20)
+    assert np.isfinite(hist).all()
+    assert min(hist) <= hist[0]
+    S_ref = S_t + dS
+    # held-out test error (Eq. 4.1): refined vs plain tensor sketch
+    plain = h.approx_batch(te, S_t, spec.r)["err"]
+    ref = h.approx_batch(te, S_ref, spec.r)["err"]
+    opt = [oracle.optimal_error(a, spec.r) for a in _np(te)]
+    e_plain = oracle.test_error(_np(plain), opt)
+    e_ref = oracle.test_error(_np(ref), opt)
+    print(f"\nrefiner: validation loss {hist[0]:.6f} -> {min(hist):.6f}; "
+          f"held-out test error plain {e_plain:.5f}, refined {e_ref:.5f}")
+    # the selected dS is the best on validation, so its loss is not above
+    # the plain sketch's there
+    vloss = np.mean(_np(h.approx_batch(val, S_ref, spec.r)["err"]) ** 2
+                    / np.sum(_np(val) ** 2, axis=(1, 2)))
+    assert vloss <= hist[0] * (1 + 1e-6)
+    h.close()

@@ -67,8 +67,8 @@ def test_tc_small_single_cta(tsk):
     (512, 200, 20, 10),     # C = 1, ragged n
     (1000, 448, 40, 20),    # C = 2, ragged m
     (2048, 576, 40, 20),    # C = 4
-    (3000, 130, 10, 5),     # C = 8, ragged m and n
-    (300, 70, 48, 24),      # k = 48 (largest the kernel takes)
+    (3000, 136, 10, 5),     # C = 8, ragged m and n
+    (300, 72, 48, 24),      # k = 48 (largest the kernel takes)
 ])
 def test_tc_matches_oracle(tsk, m, n, k, r):
     A, S = _case(m, n, k, m + n)
@@ -103,6 +103,22 @@ def test_tc_ragged_batch_matches_simt(tsk):
     np.testing.assert_allclose(_np(tc["normA2"]), _np(simt["normA2"]), rtol=1e-5)
     h1.close()
     h2.close()
+
+
+def test_tc_rejects_unaligned_rows(tsk):
+    # a row of 70 BF16 values is 140 bytes: not a multiple of 16, so TMA
+    # cannot tile it; asking for the tensor-core kernel explicitly fails
+    A, S = _case(128, 70, 8, 3)
+    h = tsk.Handle(kernel=tsk.KERNEL_TC)
+    with pytest.raises(tsk.TskError) as e:
+        h.approx_batch([A], [S], 4)
+    assert e.value.status == 7  # TSK_EUNSUPPORTED
+    h.close()
+    # the automatic choice falls back to the CUDA-core kernels
+    out, st, h = _run(tsk, tsk.KERNEL_AUTO, [A], [S], [4])
+    o = oracle.scw(_np(A), _np(S), 4, dense=False)
+    assert st == 0 and abs(float(out["err"][0]) - o["err"]) <= GAP * o["err"]
+    h.close()
 
 
 def test_tc_repeated_plan_is_deterministic(tsk):
