@@ -195,7 +195,7 @@ def run_tsk(args):
         dist.barrier()
     peaks, peak_src = load_peaks()
     spec = synth.C3
-    count = spec.n_test
+    count = args.matrices if args.matrices > 0 else spec.n_test
     h = tsk.Handle(kernel=args.kernel)
 
     # ---- training side (timed separately, not part of the metric) --------
@@ -246,8 +246,10 @@ def run_tsk(args):
         if ws > 1:
             dist.barrier()
         total_ms = t_start.elapsed_time(t_end)
-        stage = [b.elapsed_time(e) for b, e in zip(evb, eve)] if probe else []
-        return total_ms, stage
+        stage_ms = [b.elapsed_time(e) for b, e in zip(evb, eve)] if probe else []
+        if probe:
+            plan_.set_probe(None, None)
+        return total_ms, stage_ms
 
     for _ in range(args.warmup):
         plan.execute()
@@ -370,12 +372,13 @@ def run_tsk(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "C3 test pass: 500 stream matrices 2048x2048 BF16 "
+            "config": {"workload": f"C3 test pass: {count} stream matrices 2048x2048 BF16 "
                                    "per GPU, k=40, r=20, sketch trained on "
                                    f"{args.train} matrices of the stream",
                        "m": spec.m, "n": spec.n, "k": spec.k, "r": spec.r,
                        "matrices_per_step_per_gpu": count,
-                       "l2": "inputs (4.2 GB per step) larger than L2; no flush",
+                       "l2": f"inputs ({alg_bytes / 1e9:.2f} GB per step) larger than "
+                             "L2 (129 MB); no flush",
                        "sketch_kernel": plan_kind},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
@@ -405,6 +408,7 @@ def run_tsk(args):
 
 def main():
     faulthandler.enable()
+    faulthandler.dump_traceback_later(600, repeat=True)
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -412,6 +416,9 @@ def main():
     ap.add_argument("--impl", default="tsk", choices=["tsk", "reference"])
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 simt, 2 tcgen05")
     ap.add_argument("--train", type=int, default=1000)
+    ap.add_argument("--matrices", type=int, default=0,
+                    help="stream matrices per step and GPU (default: the 500 of the "
+                         "workload; smaller values are for profiling captures)")
     ap.add_argument("--cpu-sample", type=int, default=24)
     ap.add_argument("--ref-sample", type=int, default=4)
     ap.add_argument("--no-fp32", action="store_true")

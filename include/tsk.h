@@ -198,7 +198,9 @@ tsk_status tsk_plan_destroy(tsk_plan plan);
    A_d from HBM: X = A^T S^T and Y = A X), so that cudaEventElapsedTime on the
    two caller-owned events (created with timing enabled) gives that stage's
    device time on every later execution.  Later calls only swap the events
-   (no re-recording).  Must not be called while the plan is executing. */
+   (no re-recording).  The events must stay alive while the plan can still
+   execute with them; ev_begin = ev_end = NULL removes the probe (the graph is
+   re-recorded without it).  Must not be called while the plan is executing. */
 tsk_status tsk_plan_set_probe(tsk_plan plan, void* ev_begin, void* ev_end);
 
 /* Bytes of device workspace a plan holds, and the number of kernel launches

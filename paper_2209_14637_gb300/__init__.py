@@ -350,9 +350,15 @@ class Plan:
 
     def set_probe(self, ev_begin, ev_end):
         """Record ev_begin/ev_end (torch.cuda.Event with timing) around the
-        sketch pass on every later execute()."""
+        sketch pass on every later execute(); (None, None) removes the probe.
+        The plan keeps the events alive while its graph refers to them."""
+        if ev_begin is None and ev_end is None:
+            self._h._check(self._h._lib.tsk_plan_set_probe(self._p, None, None))
+            self._probe = None
+            return
         self._h._check(self._h._lib.tsk_plan_set_probe(
             self._p, C.c_void_p(ev_begin.cuda_event), C.c_void_p(ev_end.cuda_event)))
+        self._probe = (ev_begin, ev_end)
 
     def info(self):
         ws, nl = C.c_int64(), C.c_int32()

@@ -419,4 +419,295 @@ cudaError_t launch_sym_eig(bool dbl, const void* H, int p, void* theta,
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Gram route of the FP32 / BF16 paths (E2 + E4 without Householder).
+//
+//   R_X  = chol(X^T X)                       (X = Q R_X; kappa(X) is modest)
+//   R_X <- chol(Q1^T Q1) R_X,  Q1 = X R_X^-1 (one refinement step on Q)
+//   M    = Y R_X^-1 = A Q                    (m x k, well conditioned)
+//   sigma_i(AQ)^2 = lambda_i(M^T M),  V = eigenvectors,  W = R_X^-1 V_r
+//
+// Y itself is not factored: its columns grow like sigma_i^2 and Y^T Y would
+// lose everything in FP32.  Partial Gram matrices are summed in FP32 over
+// chunks of 256 rows and in FP64 across chunks; the k x k Cholesky and
+// inverse run in FP64; the captured energy sum_{i<=r} v_i^T (M^T M) v_i is
+// formed in FP64 from the FP32 eigenvectors.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int GCHUNK = 256;  // rows per partial Gram
+constexpr int GSUB = 32;     // rows staged in shared memory at a time
+}  // namespace
+
+// One CTA per (panel, chunk): partial G = P_c^T P_c over the chunk's rows,
+// where P_c = P or P R^{-1} (Rinv: kp x kp FP32, upper, per panel).
+__global__ void __launch_bounds__(256)
+panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __restrict__ chunks,
+                  const float* __restrict__ rinv, float* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 ch = chunks[blockIdx.x];
+  const PanelDev pd = panels[ch.x];
+  const int k = pd.k, ld = pd.ld;
+  float* Ps = (float*)smem_raw;        // GSUB x (kp + 1)
+  float* Ts = Ps + GSUB * (kp + 1);    // GSUB x (kp + 1) transformed rows
+  float* Rs = Ts + GSUB * (kp + 1);    // kp x kp
+  const float* P = (const float*)pd.P;
+  const bool tr = (rinv != nullptr);
+  if (tr) {
+    const float* R = rinv + (long long)ch.x * kp * kp;
+    for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) Rs[e] = R[e];
+  }
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  const long long r0 = (long long)ch.y * GCHUNK;
+  const long long r1 = min(pd.rows, r0 + GCHUNK);
+  const int ldp = kp + 1;
+  for (long long s0 = r0; s0 < r1; s0 += GSUB) {
+    __syncthreads();
+    for (int e = tid; e < GSUB * kp; e += blockDim.x) {
+      const int ii = e / kp, c = e % kp;
+      const long long i = s0 + ii;
+      Ps[ii * ldp + c] = (i < r1 && c < k) ? P[i * ld + c] : 0.f;
+    }
+    __syncthreads();
+    const float* src = Ps;
+    if (tr) {
+      for (int e = tid; e < GSUB * kp; e += blockDim.x) {
+        const int ii = e / kp, c = e % kp;
+        float t = 0.f;
+        for (int cc = 0; cc <= c && cc < k; ++cc) t += Ps[ii * ldp + cc] * Rs[cc * kp + c];
+        Ts[ii * ldp + c] = (c < k) ? t : 0.f;
+      }
+      __syncthreads();
+      src = Ts;
+    }
+    if (ty * 4 < kp && tx * 4 < kp) {
+#pragma unroll 4
+      for (int ii = 0; ii < GSUB; ++ii) {
+        float x[4], y[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) x[a] = src[ii * ldp + ty * 4 + a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) y[b] = src[ii * ldp + tx * 4 + b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(x[a], y[b], acc[a][b]);
+      }
+    }
+  }
+  if (ty * 4 < kp && tx * 4 < kp) {
+    float* out = partial + (long long)blockIdx.x * kp * kp;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) out[(ty * 4 + a) * kp + tx * 4 + b] = acc[a][b];
+  }
+}
+
+// One CTA per matrix: G (FP64) = sum of its partials; R = chol(G) (upper);
+// with prev != NULL the result is R prev (the refinement step), and
+// rinv64 / rinv32 receive (R prev)^{-1}.  Rank deficiency raises the status.
+__global__ void __launch_bounds__(256)
+chol_kernel(int kp, const MatDev* __restrict__ mats, const int* __restrict__ chunk_off,
+            const float* __restrict__ partial, const double* __restrict__ prev,
+            double* __restrict__ rfac, double* __restrict__ rinv64,
+            float* __restrict__ rinv32, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* G = (double*)smem_raw;   // kp x kp
+  double* R = G + kp * kp;         // kp x kp
+  double* Ri = R + kp * kp;        // kp x kp
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const int k = mats[b].k;
+  const int c0 = chunk_off[b], c1 = chunk_off[b + 1];
+  for (int e = tid; e < kp * kp; e += blockDim.x) {
+    double s = 0.0;
+    for (int c = c0; c < c1; ++c) s += (double)partial[(long long)c * kp * kp + e];
+    G[e] = s;
+    R[e] = 0.0;
+    Ri[e] = 0.0;
+  }
+  __syncthreads();
+  // right-looking Cholesky, one column of R per step
+  __shared__ double dj;
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  for (int j = 0; j < k; ++j) {
+    if (tid == 0) {
+      double d = G[j * kp + j];
+      for (int p = 0; p < j; ++p) d -= R[p * kp + j] * R[p * kp + j];
+      if (!(d > 0.0)) {
+        bad = 1;
+        d = 0.0;
+      }
+      dj = sqrt(d);
+      R[j * kp + j] = dj;
+    }
+    __syncthreads();
+    for (int c = j + 1 + tid; c < k; c += blockDim.x) {
+      double t = G[j * kp + c];
+      for (int p = 0; p < j; ++p) t -= R[p * kp + j] * R[p * kp + c];
+      R[j * kp + c] = (dj > 0.0) ? t / dj : 0.0;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int c = 0; c < k; ++c) mx = fmax(mx, fabs(R[c * kp + c]));
+    for (int c = 0; c < k; ++c) bad |= !(fabs(R[c * kp + c]) > 1e-6 * mx);
+    if (bad) atomicOr(status, kStatusRankDef);
+  }
+  __syncthreads();
+  // R <- R prev (both upper triangular)
+  if (prev != nullptr) {
+    const double* Pv = prev + (long long)b * kp * kp;
+    for (int e = tid; e < kp * kp; e += blockDim.x) {
+      const int a = e / kp, c = e % kp;
+      double t = 0.0;
+      if (a <= c && c < k)
+        for (int p = a; p <= c; ++p) t += R[a * kp + p] * Pv[p * kp + c];
+      G[e] = t;  // reuse G as scratch
+    }
+    __syncthreads();
+    for (int e = tid; e < kp * kp; e += blockDim.x) R[e] = G[e];
+    __syncthreads();
+  }
+  // Ri = R^{-1}: column c solves R x = e_c by back substitution
+  for (int c = tid; c < k; c += blockDim.x) {
+    for (int i = c; i >= 0; --i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int p = i + 1; p <= c; ++p) t -= R[i * kp + p] * Ri[p * kp + c];
+      const double d = R[i * kp + i];
+      Ri[i * kp + c] = (d != 0.0) ? t / d : 0.0;
+    }
+  }
+  __syncthreads();
+  double* ro = rfac + (long long)b * kp * kp;
+  double* ri = rinv64 + (long long)b * kp * kp;
+  float* rf = rinv32 + (long long)b * kp * kp;
+  for (int e = tid; e < kp * kp; e += blockDim.x) {
+    ro[e] = R[e];
+    ri[e] = Ri[e];
+    rf[e] = (float)Ri[e];
+  }
+}
+
+// One CTA per matrix: G_M (FP64) from its partials; eigenvectors by one-sided
+// Jacobi in FP32; captured energy in FP64; err, sigma, W = R_X^{-1} V_r.
+__global__ void __launch_bounds__(256)
+eig_finish_kernel(int kp, const MatDev* __restrict__ mats, const int* __restrict__ chunk_off,
+                  const float* __restrict__ partial, const double* __restrict__ rinv64,
+                  float* __restrict__ Wm, const double* __restrict__ normA2,
+                  double* __restrict__ err, int* __restrict__ flags, int err_mode, double tau) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ld = kp + 1;
+  double* G = (double*)smem_raw;     // kp x kp
+  float* Mf = (float*)(G + kp * kp); // kp x ld
+  float* V = Mf + kp * ld;           // kp x ld
+  float* sig = V + kp * ld;          // kp
+  int* order = (int*)(sig + kp);     // kp
+  __shared__ int rotated;
+  __shared__ double cap_part[8];
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const MatDev md = mats[b];
+  const int k = md.k, r = md.r;
+  const int c0 = chunk_off[b], c1 = chunk_off[b + 1];
+  for (int e = tid; e < kp * kp; e += blockDim.x) {
+    double s = 0.0;
+    for (int c = c0; c < c1; ++c) s += (double)partial[(long long)c * kp * kp + e];
+    G[e] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < kp * kp; e += blockDim.x) {
+    const int i = e / kp, c = e % kp;
+    const bool in = (i < k && c < k);
+    Mf[i * ld + c] = in ? (float)(0.5 * (G[i * kp + c] + G[c * kp + i])) : 0.f;
+    V[i * ld + c] = (i == c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  jacobi_columns<float>(Mf, V, k, k, ld, 60, &rotated);
+  __syncthreads();
+  column_norms_sorted<float>(Mf, k, k, ld, sig, order);
+  // captured energy: sum_{c<r} v_c^T G v_c in FP64 (Ky Fan), one warp per c
+  const int warp = tid >> 5, lane = tid & 31;
+  double mine = 0.0;
+  for (int c = warp; c < r; c += (int)(blockDim.x >> 5)) {
+    const int col = order[c];
+    double part = 0.0;
+    for (int i = lane; i < k; i += 32) {
+      double gi = 0.0;
+      for (int j = 0; j < k; ++j) gi += G[i * kp + j] * (double)V[j * ld + col];
+      part += (double)V[i * ld + col] * gi;
+    }
+    mine += warp_sum(part);
+  }
+  if (lane == 0) cap_part[warp] = mine;
+  __syncthreads();
+  if (tid == 0) {
+    double cap = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) cap += cap_part[w];
+    const double tot = normA2[b];
+    const double e2 = tot - cap;
+    err[b] = sqrt(e2 > 0.0 ? e2 : 0.0);
+    flags[b] = (err_mode == 2) || (err_mode == 0 && e2 < tau * tot);
+  }
+  if (md.sigma != nullptr)
+    for (int c = tid; c < k; c += blockDim.x) ((float*)md.sigma)[c] = sqrtf(sig[order[c]]);
+  // W = R_X^{-1} V_r
+  const double* Ri = rinv64 + (long long)b * kp * kp;
+  float* Wout = Wm + (long long)b * kp * kp;
+  for (int e = tid; e < kp * kp; e += blockDim.x) {
+    const int i = e / kp, c = e % kp;
+    double t = 0.0;
+    if (i < k && c < r) {
+      const int col = order[c];
+      for (int p = i; p < k; ++p) t += Ri[i * kp + p] * (double)V[p * ld + col];
+    }
+    Wout[e] = (float)t;
+  }
+}
+
+cudaError_t launch_gram_route(int kp, const MatDev* mats, int count, const PanelDev* xpanels,
+                              const PanelDev* ypanels, const int2* xchunks, int nxc,
+                              const int* xoff, const int2* ychunks, int nyc, const int* yoff,
+                              float* partial_x, float* partial_y, double* r1, double* r2,
+                              double* rinv64, float* rinv32, float* Wm, double* normA2,
+                              double* err, int* flags, int err_mode, double tau, int refine,
+                              int* status, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const size_t gsm = (size_t)(2 * GSUB * (kp + 1) + kp * kp) * sizeof(float);
+  const size_t csm = (size_t)3 * kp * kp * sizeof(double);
+  const size_t esm = (size_t)kp * kp * sizeof(double) + (size_t)2 * kp * (kp + 1) * sizeof(float) +
+                     kp * sizeof(float) + kp * sizeof(int) + 16;
+  cudaError_t e = cudaFuncSetAttribute(eig_finish_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(panel_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gsm);
+  if (e != cudaSuccess) return e;
+  // R1 = chol(X^T X)
+  panel_gram_kernel<<<nxc, 256, gsm, s>>>(kp, xpanels, xchunks, nullptr, partial_x);
+  chol_kernel<<<count, 256, csm, s>>>(kp, mats, xoff, partial_x, nullptr, r1, rinv64, rinv32,
+                                      status);
+  if (refine) {
+    // R = chol(Q1^T Q1) R1 with Q1 = X R1^{-1}
+    panel_gram_kernel<<<nxc, 256, gsm, s>>>(kp, xpanels, xchunks, rinv32, partial_x);
+    chol_kernel<<<count, 256, csm, s>>>(kp, mats, xoff, partial_x, r1, r2, rinv64, rinv32,
+                                        status);
+  }
+  // G_M = (Y R^{-1})^T (Y R^{-1})
+  panel_gram_kernel<<<nyc, 256, gsm, s>>>(kp, ypanels, ychunks, rinv32, partial_y);
+  eig_finish_kernel<<<count, 256, esm, s>>>(kp, mats, yoff, partial_y, rinv64, Wm, normA2, err,
+                                            flags, err_mode, tau);
+  return cudaGetLastError();
+}
+
+int gram_route_chunks(long long rows) { return (int)((rows + GCHUNK - 1) / GCHUNK); }
+
 }  // namespace tsk

@@ -60,19 +60,26 @@ constexpr int OFF_A = 0;
 constexpr int OFF_S = OFF_A + NST * STAGE_BYTES;
 constexpr int S_BYTES = (MC / 64) * KPAD_MAX * 128;
 constexpr int P_ROW = 272;  // 64 floats + 16 bytes of padding per row
-constexpr int P_BYTES = ((KPAD_MAX * P_ROW + 1023) / 1024) * 1024;
-constexpr int OFF_P = OFF_S + S_BYTES;
-constexpr int OFF_XB = OFF_P + 2 * P_BYTES;
-constexpr int XB_BYTES = KPAD_MAX * 128;
-constexpr int OFF_BAR = OFF_XB + 2 * XB_BYTES;
-constexpr int BAR_BYTES = 512;
-constexpr int SMEM_BYTES = OFF_BAR + BAR_BYTES + 1024;
+constexpr int P_BYTES = KPAD_MAX * P_ROW;
+constexpr int XB_BYTES = 2 * KPAD_MAX * 128;  // X_hi rows, then X_lo rows
+constexpr int OFF_XB = OFF_S + S_BYTES;
+constexpr int OFF_P = OFF_XB + 2 * XB_BYTES;
+constexpr int OFF_BAR = OFF_P + 2 * P_BYTES;
+constexpr int BAR_BYTES = 256;
+// The kernel declares no static shared variables, so its dynamic shared
+// memory starts on a 1024-byte boundary; the kernel checks this and reports
+// misalignment instead of reserving slack.
+constexpr int SMEM_BYTES = OFF_BAR + BAR_BYTES;
 // MMA-X reads 128 rows of S per 64-row chunk although only kpad rows are
 // real; the extra rows (whose results are never used) must stay inside the
 // allocation: from the last chunk they reach at most 16 KB past its start.
 static_assert(OFF_S + (MC / 64 - 1) * KPAD_MAX * 128 + 128 * 128 <= OFF_BAR,
               "S over-read leaves the shared-memory allocation");
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
+static_assert(OFF_S % 1024 == 0 && OFF_XB % 1024 == 0 && XB_BYTES % 1024 == 0 &&
+                  STAGE_BYTES % 1024 == 0,
+              "swizzled operands need 1024-byte aligned atoms");
+static_assert(OFF_P % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 
 // barrier slots
 enum {
@@ -322,9 +329,12 @@ template <int C>
 __global__ void __launch_bounds__(NTHREADS, 1)
 sketch_tc_kernel(const __grid_constant__ TcParams P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  const uint32_t raw_s = smem_u32(smem_raw);
-  unsigned char* sm = smem_raw + ((1024 - (raw_s & 1023)) & 1023);
+  unsigned char* sm = smem_raw;
   const uint32_t sb = smem_u32(sm);  // 1024-aligned shared address
+  if (sb & 1023) {  // every CTA of the launch sees the same layout
+    if (threadIdx.x == 0) atomicOr(P.status, kStatusTimeout);
+    return;
+  }
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t rank = (C > 1) ? cluster_rank() : 0;
   const uint32_t cid = (C > 1) ? cluster_id() : blockIdx.x;
@@ -334,7 +344,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
   uint32_t* tmem_slot = (uint32_t*)(sm + OFF_BAR + 8 * B_COUNT + 8);
 
   const int w0 = P.work_off[cid], w1 = P.work_off[cid + 1];
-  const uint32_t tmem_cols_needed = 2 * NB + (MC / 128) * kpad;
+  const uint32_t tmem_cols_needed = 2 * NB + (MC / 128) * 2 * kpad;
   const uint32_t tmem_cols = tmem_cols_needed <= 256 ? 256 : 512;
 
   if (tid == 0) {
@@ -375,7 +385,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc_x = idesc_bf16(128, NB, 0, 1);
-  const uint32_t idesc_y = idesc_bf16(128, kpad, 0, 0);
+  const uint32_t idesc_y = idesc_bf16(128, 2 * kpad, 0, 0);
   const uint16_t cmask = (uint16_t)((1u << C) - 1);
 
   if (warp == 0) {
@@ -449,7 +459,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
             const uint64_t a = sdesc(sb + OFF_A + sy * STAGE_BYTES + t * 128 * 128 + kk * 32,
                                      16, 1024);
             const uint64_t b = sdesc(sb + OFF_XB + h * XB_BYTES + kk * 32, 16, 1024);
-            tc_mma(tmem + 2 * NB + t * kpad, a, b, idesc_y, (qy > 0 || kk > 0) ? 1u : 0u);
+            tc_mma(tmem + 2 * NB + t * 2 * kpad, a, b, idesc_y, (qy > 0 || kk > 0) ? 1u : 0u);
           }
         }
         tc_commit(bar(B_AEMPTY + sy));
@@ -576,11 +586,28 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
             }
           }
         }
-        // X~ = BF16(X): the values Y is built from; X keeps them in FP32.
-        uint32_t packed[WC / 2];
+        // Two-term BF16 split X = X_hi + X_lo (X_hi = BF16(X), X_lo =
+        // BF16(X - X_hi)); MMA-Y multiplies A by both, so Y = A (X_hi + X_lo)
+        // carries about 16 significant bits of X instead of 8.  X in HBM
+        // holds X_hi + X_lo, the values Y is built from.
+        uint32_t phi[WC / 2], plo[WC / 2];
+        float xs[WC];
 #pragma unroll
         for (int j = 0; j < WC; j += 2) {
-          packed[j / 2] = pack_bf16x2(acc[j], acc[j + 1]);
+          const __nv_bfloat16 h0 = __float2bfloat16_rn(acc[j]);
+          const __nv_bfloat16 h1 = __float2bfloat16_rn(acc[j + 1]);
+          const float f0 = __bfloat162float(h0), f1 = __bfloat162float(h1);
+          const __nv_bfloat16 l0 = __float2bfloat16_rn(acc[j] - f0);
+          const __nv_bfloat16 l1 = __float2bfloat16_rn(acc[j + 1] - f1);
+          xs[j] = f0 + __bfloat162float(l0);
+          xs[j + 1] = f1 + __bfloat162float(l1);
+          __nv_bfloat162 hh, ll;
+          hh.x = h0;
+          hh.y = h1;
+          ll.x = l0;
+          ll.y = l1;
+          phi[j / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+          plo[j / 2] = *reinterpret_cast<const uint32_t*>(&ll);
         }
         if (c < k) {
           float* Xm = P.X + md.offX;
@@ -588,21 +615,26 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
 #pragma unroll
           for (int j = 0; j < WC; ++j) {
             const long long jj = jb + j;
-            const __nv_bfloat16 hv = __float2bfloat16_rn(acc[j]);
-            if (jj < n) Xm[jj * P.kp + c] = __bfloat162float(hv);
+            if (jj < n) Xm[jj * P.kp + c] = xs[j];
           }
         }
         bwait(bar(B_XBEMPTY + h), (v & 1) ^ 1, ctl, P);
         if (c < k) {
-          const uint32_t xrow = sb + OFF_XB + h * XB_BYTES + (c >> 3) * 1024 + (c & 7) * 128;
 #pragma unroll
-          for (int u = 0; u < WC / 8; ++u) {
-            const int unit = (int)(rank * WC / 8) + u;
-            const uint32_t off = xrow + (uint32_t)(((unit ^ (c & 7)) & 7) << 4);
+          for (int half = 0; half < 2; ++half) {
+            const int row = c + half * kpad;
+            const uint32_t* src = half ? plo : phi;
+            const uint32_t xrow =
+                sb + OFF_XB + h * XB_BYTES + (row >> 3) * 1024 + (row & 7) * 128;
 #pragma unroll
-            for (int r = 0; r < C; ++r)
-              st_cluster_v4(mapa(off, r), packed[u * 4], packed[u * 4 + 1], packed[u * 4 + 2],
-                            packed[u * 4 + 3]);
+            for (int u = 0; u < WC / 8; ++u) {
+              const int unit = (int)(rank * WC / 8) + u;
+              const uint32_t off = xrow + (uint32_t)(((unit ^ (row & 7)) & 7) << 4);
+#pragma unroll
+              for (int r = 0; r < C; ++r)
+                st_cluster_v4(mapa(off, r), src[u * 4], src[u * 4 + 1], src[u * 4 + 2],
+                              src[u * 4 + 3]);
+            }
           }
         }
         fence_proxy_async_cluster();
@@ -626,14 +658,17 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
           const long long row = (long long)rank * MC + t * 128 + lane_base + lane;
 #pragma unroll 1
           for (int j = 0; j < kpad; j += 16) {
-            float yv[16];
-            tmem_ld16(tmem + ((uint32_t)lane_base << 16) + 2 * NB + t * kpad + j, yv);
+            float yv[16], yl[16];
+            const uint32_t col = tmem + ((uint32_t)lane_base << 16) + 2 * NB + t * 2 * kpad + j;
+            tmem_ld16(col, yv);
+            tmem_ld16(col + kpad, yl);
             tmem_wait_ld();
             if (row < m) {
               float4* dst = reinterpret_cast<float4*>(Ym + row * P.kp + j);
 #pragma unroll
               for (int e = 0; e < 4; ++e)
-                dst[e] = make_float4(yv[4 * e], yv[4 * e + 1], yv[4 * e + 2], yv[4 * e + 3]);
+                dst[e] = make_float4(yv[4 * e] + yl[4 * e], yv[4 * e + 1] + yl[4 * e + 1],
+                                     yv[4 * e + 2] + yl[4 * e + 2], yv[4 * e + 3] + yl[4 * e + 3]);
             }
           }
         }
@@ -895,11 +930,25 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
     const int C = kv.first;
     std::vector<int> ids = kv.second;
     int ncl = 1;
+    cudaError_t ae = cudaSuccess;
     switch (C) {
-      case 1: set_attrs<1>(); ncl = max_clusters<1>(); break;
-      case 2: set_attrs<2>(); ncl = max_clusters<2>(); break;
-      case 4: set_attrs<4>(); ncl = max_clusters<4>(); break;
-      default: set_attrs<8>(); ncl = max_clusters<8>(); break;
+      case 1: ae = set_attrs<1>(); if (ae == cudaSuccess) ncl = max_clusters<1>(); break;
+      case 2: ae = set_attrs<2>(); if (ae == cudaSuccess) ncl = max_clusters<2>(); break;
+      case 4: ae = set_attrs<4>(); if (ae == cudaSuccess) ncl = max_clusters<4>(); break;
+      default: ae = set_attrs<8>(); if (ae == cudaSuccess) ncl = max_clusters<8>(); break;
+    }
+    if (ae != cudaSuccess) {
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if (msg)
+        snprintf(msg, msglen,
+                 "cudaFuncSetAttribute(%d bytes of shared memory) failed: %s (device opt-in "
+                 "limit %d bytes)",
+                 SMEM_BYTES, cudaGetErrorString(ae), optin);
+      cudaGetLastError();
+      delete p;
+      return ae;
     }
     ncl = std::min<int>(ncl, (int)ids.size());
     std::sort(ids.begin(), ids.end(), [&](int a, int b) {

@@ -35,6 +35,10 @@ struct tsk_plan_s {
   unsigned char* base = nullptr;
   size_t o_mats = 0, o_ix = 0, o_iy = 0, o_io = 0, o_pan = 0, o_X = 0, o_Y = 0,
          o_RX = 0, o_RY = 0, o_W = 0, o_flag = 0, o_U2 = 0, o_V2 = 0, o_e2 = 0;
+  // Gram route (FP32 / BF16)
+  int nxc = 0, nyc = 0;
+  size_t o_xch = 0, o_ych = 0, o_xoff = 0, o_yoff = 0, o_px = 0, o_py = 0, o_r1 = 0,
+         o_r2 = 0, o_ri64 = 0, o_ri32 = 0;
   double* d_norm = nullptr;
   double* d_err = nullptr;
   cudaGraphNode_t probe_begin = nullptr, probe_end = nullptr;
@@ -254,18 +258,31 @@ static cudaError_t capture_plan(tsk_plan p, cudaEvent_t evb, cudaEvent_t eve) {
     }
   }
   if (ce == cudaSuccess && eve) ce = cudaEventRecordWithFlags(eve, s, cudaEventRecordExternal);
-  if (ce == cudaSuccess) {
+  const double tau = p->dbl ? 1e-6 : 1e-4;
+  if (ce == cudaSuccess && p->dbl) {
+    // FP64: blockwise Householder R factors of X and Y, SVD of R_Y R_X^{-1}
     ce = launch_tsqr(p->dbl, kp, (const PanelDev*)(base + p->o_pan), 2 * count,
                      h->opts.refine_q ? 1 : 0, h->d_status, s);
     ++launches;
-  }
-  if (ce == cudaSuccess) {
-    const double tau = p->dbl ? 1e-6 : 1e-4;
-    ce = launch_small_svd(p->dbl, kp, d_mats, count, base + p->o_RX,
-                          base + p->o_RY, base + p->o_W, d_norm, d_err,
-                          (int*)(base + p->o_flag), h->opts.err_mode, tau,
-                          h->d_status, s);
+    if (ce == cudaSuccess)
+      ce = launch_small_svd(p->dbl, kp, d_mats, count, base + p->o_RX,
+                            base + p->o_RY, base + p->o_W, d_norm, d_err,
+                            (int*)(base + p->o_flag), h->opts.err_mode, tau,
+                            h->d_status, s);
     ++launches;
+  } else if (ce == cudaSuccess) {
+    // FP32 / BF16: Cholesky of X^T X (+ one refinement), eigenpairs of M^T M
+    const PanelDev* pan = (const PanelDev*)(base + p->o_pan);
+    ce = launch_gram_route(kp, d_mats, count, pan, pan + count,
+                           (const int2*)(base + p->o_xch), p->nxc,
+                           (const int*)(base + p->o_xoff), (const int2*)(base + p->o_ych),
+                           p->nyc, (const int*)(base + p->o_yoff), (float*)(base + p->o_px),
+                           (float*)(base + p->o_py), (double*)(base + p->o_r1),
+                           (double*)(base + p->o_r2), (double*)(base + p->o_ri64),
+                           (float*)(base + p->o_ri32), (float*)(base + p->o_W), d_norm, d_err,
+                           (int*)(base + p->o_flag), h->opts.err_mode, tau,
+                           h->opts.refine_q ? 1 : 0, h->d_status, s);
+    launches += h->opts.refine_q ? 6 : 4;
   }
   if (ce == cudaSuccess && h->opts.err_mode != 1) {
     ce = cudaMemsetAsync(base + p->o_e2, 0, sizeof(double) * count, s);
@@ -392,6 +409,22 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   const size_t o_iy = cv.take(sizeof(int2) * iy.size());
   const size_t o_io = cv.take(sizeof(int4) * std::max<size_t>(1, io.size()));
   const size_t o_pan = cv.take(sizeof(PanelDev) * 2 * count);
+  // Gram route: row chunks of the X and Y panels and their partial Grams
+  std::vector<int2> xch, ych;
+  std::vector<int> xoff(count + 1, 0), yoff(count + 1, 0);
+  for (int64_t i = 0; i < count; ++i) {
+    xoff[i] = (int)xch.size();
+    for (int c = 0; c < gram_route_chunks(hm[i].n); ++c) xch.push_back(make_int2((int)i, c));
+    yoff[i] = (int)ych.size();
+    for (int c = 0; c < gram_route_chunks(hm[i].m); ++c) ych.push_back(make_int2((int)i, c));
+  }
+  xoff[count] = (int)xch.size();
+  yoff[count] = (int)ych.size();
+  const bool gram = (prec != TSK_FP64);
+  const size_t o_xch = cv.take(gram ? sizeof(int2) * xch.size() : 0);
+  const size_t o_ych = cv.take(gram ? sizeof(int2) * ych.size() : 0);
+  const size_t o_xoff = cv.take(gram ? sizeof(int) * (count + 1) : 0);
+  const size_t o_yoff = cv.take(gram ? sizeof(int) * (count + 1) : 0);
   const size_t o_X = cv.take(cs * offX);
   const size_t o_Y = cv.take(cs * offY);
   const size_t o_RX = cv.take(cs * count * kp * kp);
@@ -405,6 +438,13 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   const size_t o_V2 = cv.take(fallback ? cs * offX : 0);
   const size_t o_e2 = cv.take(sizeof(double) * count);
   const size_t host_part = o_X;  // descriptors live before X
+  const size_t kk2 = (size_t)kp * kp;
+  const size_t o_px = cv.take(gram ? sizeof(float) * kk2 * xch.size() : 0);
+  const size_t o_py = cv.take(gram ? sizeof(float) * kk2 * ych.size() : 0);
+  const size_t o_r1 = cv.take(gram ? sizeof(double) * kk2 * count : 0);
+  const size_t o_r2 = cv.take(gram ? sizeof(double) * kk2 * count : 0);
+  const size_t o_ri64 = cv.take(gram ? sizeof(double) * kk2 * count : 0);
+  const size_t o_ri32 = cv.take(gram ? sizeof(float) * kk2 * count : 0);
   p->ws_bytes = cv.off;
   cudaError_t ce = cudaMalloc(&p->ws, p->ws_bytes);
   if (ce != cudaSuccess) {
@@ -417,13 +457,13 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   double* d_err = err ? err : (double*)(base + o_err);
   std::vector<PanelDev> hp(2 * count);
   for (int64_t i = 0; i < count; ++i) {
-    PanelDev& px = hp[2 * i];
+    PanelDev& px = hp[i];
     px.P = base + o_X + cs * hm[i].offX;
     px.rows = hm[i].n;
     px.k = hm[i].k;
     px.ld = kp;
     px.R = base + o_RX + cs * i * kp * kp;
-    PanelDev& py = hp[2 * i + 1];
+    PanelDev& py = hp[count + i];
     py.P = base + o_Y + cs * hm[i].offY;
     py.rows = hm[i].m;
     py.k = hm[i].k;
@@ -436,6 +476,12 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   memcpy(staging.data() + o_iy, iy.data(), sizeof(int2) * iy.size());
   if (!io.empty()) memcpy(staging.data() + o_io, io.data(), sizeof(int4) * io.size());
   memcpy(staging.data() + o_pan, hp.data(), sizeof(PanelDev) * 2 * count);
+  if (gram) {
+    memcpy(staging.data() + o_xch, xch.data(), sizeof(int2) * xch.size());
+    memcpy(staging.data() + o_ych, ych.data(), sizeof(int2) * ych.size());
+    memcpy(staging.data() + o_xoff, xoff.data(), sizeof(int) * (count + 1));
+    memcpy(staging.data() + o_yoff, yoff.data(), sizeof(int) * (count + 1));
+  }
   ce = cudaMemcpy(p->ws, staging.data(), host_part, cudaMemcpyHostToDevice);
   if (ce != cudaSuccess) {
     set_err(h, "plan upload: %s", cudaGetErrorString(ce));
@@ -473,6 +519,18 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   p->o_U2 = o_U2;
   p->o_V2 = o_V2;
   p->o_e2 = o_e2;
+  p->nxc = (int)xch.size();
+  p->nyc = (int)ych.size();
+  p->o_xch = o_xch;
+  p->o_ych = o_ych;
+  p->o_xoff = o_xoff;
+  p->o_yoff = o_yoff;
+  p->o_px = o_px;
+  p->o_py = o_py;
+  p->o_r1 = o_r1;
+  p->o_r2 = o_r2;
+  p->o_ri64 = o_ri64;
+  p->o_ri32 = o_ri32;
   p->d_norm = d_norm;
   p->d_err = d_err;
   ce = capture_plan(p, nullptr, nullptr);
@@ -509,7 +567,14 @@ extern "C" tsk_status tsk_plan_destroy(tsk_plan p) {
 
 extern "C" tsk_status tsk_plan_set_probe(tsk_plan p, void* ev_begin,
                                          void* ev_end) {
-  if (!p || !ev_begin || !ev_end || ev_begin == ev_end) return TSK_EINVAL;
+  if (!p) return TSK_EINVAL;
+  if (!ev_begin && !ev_end) {  // remove the probe
+    if (!p->probe_begin && !p->probe_end) return TSK_OK;
+    TSK_CUDA(p->h, cudaDeviceSynchronize());
+    TSK_CUDA(p->h, capture_plan(p, nullptr, nullptr));
+    return TSK_OK;
+  }
+  if (!ev_begin || !ev_end || ev_begin == ev_end) return TSK_EINVAL;
   cudaEvent_t b = (cudaEvent_t)ev_begin, e = (cudaEvent_t)ev_end;
   if (p->probe_begin && p->probe_end) {
     TSK_CUDA(p->h, cudaGraphExecEventRecordNodeSetEvent(p->exec, p->probe_begin, b));
