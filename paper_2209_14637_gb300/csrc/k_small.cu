@@ -24,12 +24,14 @@ template <typename T>
 struct Eps;
 template <>
 struct Eps<float> {
-  static constexpr float jacobi = 4.0e-7f;
+  // above the rounding noise of a k-term FP32 dot product (about
+  // sqrt(k) * 6e-8), so that converged columns stop rotating
+  static constexpr float jacobi = 4.0e-6f;
   static constexpr float tiny = 1.0e-30f;
 };
 template <>
 struct Eps<double> {
-  static constexpr double jacobi = 1.0e-15;
+  static constexpr double jacobi = 1.0e-14;
   static constexpr double tiny = 1.0e-280;
 };
 
@@ -440,7 +442,11 @@ constexpr int GSUB = 32;     // rows staged in shared memory at a time
 }  // namespace
 
 // One CTA per (panel, chunk): partial G = P_c^T P_c over the chunk's rows,
-// where P_c = P or P R^{-1} (Rinv: kp x kp FP32, upper, per panel).
+// where P_c = P or P R^{-1} (Rinv: kp x kp FP32, upper, per panel).  Only the
+// upper triangle is formed: the 4x4 tiles with tile-row <= tile-column are
+// spread over the threads, and when there are fewer tiles than threads,
+// several row groups share the rows of each staged block and are summed at
+// the end.  Entries below the diagonal of the partial are left unwritten.
 __global__ void __launch_bounds__(256)
 panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __restrict__ chunks,
                   const float* __restrict__ rinv, float* __restrict__ partial) {
@@ -448,16 +454,30 @@ panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __res
   const int2 ch = chunks[blockIdx.x];
   const PanelDev pd = panels[ch.x];
   const int k = pd.k, ld = pd.ld;
-  float* Ps = (float*)smem_raw;        // GSUB x (kp + 1)
-  float* Ts = Ps + GSUB * (kp + 1);    // GSUB x (kp + 1) transformed rows
-  float* Rs = Ts + GSUB * (kp + 1);    // kp x kp
+  const int ldp = kp + 1;
+  float* Ps = (float*)smem_raw;        // GSUB x ldp
+  float* Ts = Ps + GSUB * ldp;         // GSUB x ldp transformed rows
+  float* Rs = Ts + GSUB * ldp;         // kp x kp
+  float* Red = Rs + kp * kp;           // 256 x 16 partial tiles of the row groups
   const float* P = (const float*)pd.P;
   const bool tr = (rinv != nullptr);
   if (tr) {
     const float* R = rinv + (long long)ch.x * kp * kp;
     for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) Rs[e] = R[e];
   }
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int nt = kp / 4;
+  const int ntiles = nt * (nt + 1) / 2;
+  const int groups = max(1, (int)blockDim.x / ntiles);
+  const int tid = threadIdx.x;
+  const bool active = tid < groups * ntiles;
+  const int tile = tid % ntiles, grp = tid / ntiles;
+  // tile -> (ty, tx) with ty <= tx
+  int ty = 0, rem = tile;
+  while (rem >= nt - ty) {
+    rem -= nt - ty;
+    ++ty;
+  }
+  const int tx = ty + rem;
   float acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -465,7 +485,6 @@ panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __res
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
   const long long r0 = (long long)ch.y * GCHUNK;
   const long long r1 = min(pd.rows, r0 + GCHUNK);
-  const int ldp = kp + 1;
   for (long long s0 = r0; s0 < r1; s0 += GSUB) {
     __syncthreads();
     for (int e = tid; e < GSUB * kp; e += blockDim.x) {
@@ -479,15 +498,14 @@ panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __res
       for (int e = tid; e < GSUB * kp; e += blockDim.x) {
         const int ii = e / kp, c = e % kp;
         float t = 0.f;
-        for (int cc = 0; cc <= c && cc < k; ++cc) t += Ps[ii * ldp + cc] * Rs[cc * kp + c];
+        for (int cc = 0; cc <= c && cc < k; ++cc) t = fmaf(Ps[ii * ldp + cc], Rs[cc * kp + c], t);
         Ts[ii * ldp + c] = (c < k) ? t : 0.f;
       }
       __syncthreads();
       src = Ts;
     }
-    if (ty * 4 < kp && tx * 4 < kp) {
-#pragma unroll 4
-      for (int ii = 0; ii < GSUB; ++ii) {
+    if (active) {
+      for (int ii = grp; ii < GSUB; ii += groups) {
         float x[4], y[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) x[a] = src[ii * ldp + ty * 4 + a];
@@ -500,7 +518,22 @@ panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __res
       }
     }
   }
-  if (ty * 4 < kp && tx * 4 < kp) {
+  // sum the row groups
+  if (active && grp > 0) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) Red[tid * 16 + a * 4 + b] = acc[a][b];
+  }
+  __syncthreads();
+  if (active && grp == 0) {
+    for (int g2 = 1; g2 < groups; ++g2) {
+      const int t2 = g2 * ntiles + tile;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += Red[t2 * 16 + a * 4 + b];
+    }
     float* out = partial + (long long)blockIdx.x * kp * kp;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -509,90 +542,95 @@ panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __res
   }
 }
 
-// One CTA per matrix: G (FP64) = sum of its partials; R = chol(G) (upper);
-// with prev != NULL the result is R prev (the refinement step), and
-// rinv64 / rinv32 receive (R prev)^{-1}.  Rank deficiency raises the status.
+// Entry (i, c) of a symmetric matrix whose partials hold the upper triangle.
+__device__ __forceinline__ double gram_entry(const float* partial, int c0, int c1, int kp,
+                                             int i, int c) {
+  const int a = min(i, c), b = max(i, c);
+  double s = 0.0;
+  for (int q = c0; q < c1; ++q) s += (double)partial[(long long)q * kp * kp + a * kp + b];
+  return s;
+}
+
+// One CTA per matrix: G = sum of its partials (added in FP64), R = chol(G)
+// (upper, FP32, right-looking: each step scales a row and updates the
+// trailing triangle in parallel); with prev != NULL the result is R prev
+// (the refinement step).  rinv receives (R prev)^{-1}.  A pivot that is not
+// positive, or tiny next to the largest, raises the rank-deficiency status.
 __global__ void __launch_bounds__(256)
 chol_kernel(int kp, const MatDev* __restrict__ mats, const int* __restrict__ chunk_off,
-            const float* __restrict__ partial, const double* __restrict__ prev,
-            double* __restrict__ rfac, double* __restrict__ rinv64,
-            float* __restrict__ rinv32, int* __restrict__ status) {
+            const float* __restrict__ partial, const float* __restrict__ prev,
+            float* __restrict__ rfac, float* __restrict__ rinv, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* G = (double*)smem_raw;   // kp x kp
-  double* R = G + kp * kp;         // kp x kp
-  double* Ri = R + kp * kp;        // kp x kp
+  const int ld = kp + 1;
+  float* G = (float*)smem_raw;  // kp x ld, becomes R in place
+  float* T = G + kp * ld;       // kp x ld scratch
+  float* Ri = T + kp * ld;      // kp x ld
+  __shared__ float inv_d;
+  __shared__ int bad;
   const int b = blockIdx.x, tid = threadIdx.x;
   const int k = mats[b].k;
   const int c0 = chunk_off[b], c1 = chunk_off[b + 1];
   for (int e = tid; e < kp * kp; e += blockDim.x) {
-    double s = 0.0;
-    for (int c = c0; c < c1; ++c) s += (double)partial[(long long)c * kp * kp + e];
-    G[e] = s;
-    R[e] = 0.0;
-    Ri[e] = 0.0;
+    const int i = e / kp, c = e % kp;
+    G[i * ld + c] = (i < k && c < k && i <= c) ? (float)gram_entry(partial, c0, c1, kp, i, c) : 0.f;
+    Ri[i * ld + c] = 0.f;
   }
-  __syncthreads();
-  // right-looking Cholesky, one column of R per step
-  __shared__ double dj;
-  __shared__ int bad;
   if (tid == 0) bad = 0;
+  __syncthreads();
   for (int j = 0; j < k; ++j) {
     if (tid == 0) {
-      double d = G[j * kp + j];
-      for (int p = 0; p < j; ++p) d -= R[p * kp + j] * R[p * kp + j];
-      if (!(d > 0.0)) {
-        bad = 1;
-        d = 0.0;
-      }
-      dj = sqrt(d);
-      R[j * kp + j] = dj;
+      const float d = G[j * ld + j];
+      if (!(d > 0.f)) bad = 1;
+      const float r = d > 0.f ? sqrtf(d) : 0.f;
+      G[j * ld + j] = r;
+      inv_d = r > 0.f ? 1.f / r : 0.f;
     }
     __syncthreads();
-    for (int c = j + 1 + tid; c < k; c += blockDim.x) {
-      double t = G[j * kp + c];
-      for (int p = 0; p < j; ++p) t -= R[p * kp + j] * R[p * kp + c];
-      R[j * kp + c] = (dj > 0.0) ? t / dj : 0.0;
+    for (int c = j + 1 + tid; c < k; c += blockDim.x) G[j * ld + c] *= inv_d;
+    __syncthreads();
+    const int w = k - j - 1;
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int a = j + 1 + e / w, c = j + 1 + e % w;
+      if (a <= c) G[a * ld + c] = fmaf(-G[j * ld + a], G[j * ld + c], G[a * ld + c]);
     }
     __syncthreads();
   }
   if (tid == 0) {
-    double mx = 0.0;
-    for (int c = 0; c < k; ++c) mx = fmax(mx, fabs(R[c * kp + c]));
-    for (int c = 0; c < k; ++c) bad |= !(fabs(R[c * kp + c]) > 1e-6 * mx);
+    float mx = 0.f;
+    for (int c = 0; c < k; ++c) mx = fmaxf(mx, fabsf(G[c * ld + c]));
+    for (int c = 0; c < k; ++c) bad |= !(fabsf(G[c * ld + c]) > 1e-6f * mx);
     if (bad) atomicOr(status, kStatusRankDef);
   }
   __syncthreads();
-  // R <- R prev (both upper triangular)
-  if (prev != nullptr) {
-    const double* Pv = prev + (long long)b * kp * kp;
+  if (prev != nullptr) {  // R <- R prev, both upper triangular
+    const float* Pv = prev + (long long)b * kp * kp;
     for (int e = tid; e < kp * kp; e += blockDim.x) {
       const int a = e / kp, c = e % kp;
-      double t = 0.0;
+      float t = 0.f;
       if (a <= c && c < k)
-        for (int p = a; p <= c; ++p) t += R[a * kp + p] * Pv[p * kp + c];
-      G[e] = t;  // reuse G as scratch
+        for (int q = a; q <= c; ++q) t = fmaf(G[a * ld + q], Pv[q * kp + c], t);
+      T[a * ld + c] = t;
     }
     __syncthreads();
-    for (int e = tid; e < kp * kp; e += blockDim.x) R[e] = G[e];
+    for (int e = tid; e < kp * kp; e += blockDim.x) G[(e / kp) * ld + e % kp] = T[(e / kp) * ld + e % kp];
     __syncthreads();
   }
-  // Ri = R^{-1}: column c solves R x = e_c by back substitution
+  // Ri = R^{-1}: column c by back substitution
   for (int c = tid; c < k; c += blockDim.x) {
     for (int i = c; i >= 0; --i) {
-      double t = (i == c) ? 1.0 : 0.0;
-      for (int p = i + 1; p <= c; ++p) t -= R[i * kp + p] * Ri[p * kp + c];
-      const double d = R[i * kp + i];
-      Ri[i * kp + c] = (d != 0.0) ? t / d : 0.0;
+      float t = (i == c) ? 1.f : 0.f;
+      for (int q = i + 1; q <= c; ++q) t = fmaf(-G[i * ld + q], Ri[q * ld + c], t);
+      const float d = G[i * ld + i];
+      Ri[i * ld + c] = (d != 0.f) ? t / d : 0.f;
     }
   }
   __syncthreads();
-  double* ro = rfac + (long long)b * kp * kp;
-  double* ri = rinv64 + (long long)b * kp * kp;
-  float* rf = rinv32 + (long long)b * kp * kp;
+  float* ro = rfac + (long long)b * kp * kp;
+  float* ri = rinv + (long long)b * kp * kp;
   for (int e = tid; e < kp * kp; e += blockDim.x) {
-    ro[e] = R[e];
-    ri[e] = Ri[e];
-    rf[e] = (float)Ri[e];
+    const int i = e / kp, c = e % kp;
+    ro[e] = (i <= c) ? G[i * ld + c] : 0.f;
+    ri[e] = Ri[i * ld + c];
   }
 }
 
@@ -600,7 +638,7 @@ chol_kernel(int kp, const MatDev* __restrict__ mats, const int* __restrict__ chu
 // Jacobi in FP32; captured energy in FP64; err, sigma, W = R_X^{-1} V_r.
 __global__ void __launch_bounds__(256)
 eig_finish_kernel(int kp, const MatDev* __restrict__ mats, const int* __restrict__ chunk_off,
-                  const float* __restrict__ partial, const double* __restrict__ rinv64,
+                  const float* __restrict__ partial, const float* __restrict__ rinv,
                   float* __restrict__ Wm, const double* __restrict__ normA2,
                   double* __restrict__ err, int* __restrict__ flags, int err_mode, double tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -617,19 +655,23 @@ eig_finish_kernel(int kp, const MatDev* __restrict__ mats, const int* __restrict
   const int k = md.k, r = md.r;
   const int c0 = chunk_off[b], c1 = chunk_off[b + 1];
   for (int e = tid; e < kp * kp; e += blockDim.x) {
-    double s = 0.0;
-    for (int c = c0; c < c1; ++c) s += (double)partial[(long long)c * kp * kp + e];
-    G[e] = s;
+    const int i = e / kp, c = e % kp;
+    G[e] = (i < k && c < k) ? gram_entry(partial, c0, c1, kp, i, c) : 0.0;
   }
   __syncthreads();
   for (int e = tid; e < kp * kp; e += blockDim.x) {
     const int i = e / kp, c = e % kp;
-    const bool in = (i < k && c < k);
-    Mf[i * ld + c] = in ? (float)(0.5 * (G[i * kp + c] + G[c * kp + i])) : 0.f;
+    Mf[i * ld + c] = (float)G[i * kp + c];
     V[i * ld + c] = (i == c) ? 1.f : 0.f;
   }
   __syncthreads();
-  jacobi_columns<float>(Mf, V, k, k, ld, 60, &rotated);
+  // G_M is the square of a matrix with condition number ~1e2, so in FP32
+  // the off-diagonal noise of the rotated columns stays near eps * kappa(G_M)
+  // and a relative threshold is never met.  The eigenvalues converge
+  // quadratically and are at FP32 accuracy after a handful of sweeps; the
+  // captured energy below is insensitive (second order) to the remaining
+  // eigenvector error, so the sweeps are capped.
+  jacobi_columns<float>(Mf, V, k, k, ld, 10, &rotated);
   __syncthreads();
   column_norms_sorted<float>(Mf, k, k, ld, sig, order);
   // captured energy: sum_{c<r} v_c^T G v_c in FP64 (Ky Fan), one warp per c
@@ -658,29 +700,29 @@ eig_finish_kernel(int kp, const MatDev* __restrict__ mats, const int* __restrict
   if (md.sigma != nullptr)
     for (int c = tid; c < k; c += blockDim.x) ((float*)md.sigma)[c] = sqrtf(sig[order[c]]);
   // W = R_X^{-1} V_r
-  const double* Ri = rinv64 + (long long)b * kp * kp;
+  const float* Ri = rinv + (long long)b * kp * kp;
   float* Wout = Wm + (long long)b * kp * kp;
   for (int e = tid; e < kp * kp; e += blockDim.x) {
     const int i = e / kp, c = e % kp;
-    double t = 0.0;
+    float t = 0.f;
     if (i < k && c < r) {
       const int col = order[c];
-      for (int p = i; p < k; ++p) t += Ri[i * kp + p] * (double)V[p * ld + col];
+      for (int p = i; p < k; ++p) t = fmaf(Ri[i * kp + p], V[p * ld + col], t);
     }
-    Wout[e] = (float)t;
+    Wout[e] = t;
   }
 }
 
 cudaError_t launch_gram_route(int kp, const MatDev* mats, int count, const PanelDev* xpanels,
                               const PanelDev* ypanels, const int2* xchunks, int nxc,
                               const int* xoff, const int2* ychunks, int nyc, const int* yoff,
-                              float* partial_x, float* partial_y, double* r1, double* r2,
-                              double* rinv64, float* rinv32, float* Wm, double* normA2,
-                              double* err, int* flags, int err_mode, double tau, int refine,
-                              int* status, cudaStream_t s) {
+                              float* partial_x, float* partial_y, float* r1, float* r2,
+                              float* rinv, float* Wm, double* normA2, double* err, int* flags,
+                              int err_mode, double tau, int refine, int* status,
+                              cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  const size_t gsm = (size_t)(2 * GSUB * (kp + 1) + kp * kp) * sizeof(float);
-  const size_t csm = (size_t)3 * kp * kp * sizeof(double);
+  const size_t gsm = (size_t)(2 * GSUB * (kp + 1) + kp * kp + 256 * 16) * sizeof(float);
+  const size_t csm = (size_t)3 * kp * (kp + 1) * sizeof(float);
   const size_t esm = (size_t)kp * kp * sizeof(double) + (size_t)2 * kp * (kp + 1) * sizeof(float) +
                      kp * sizeof(float) + kp * sizeof(int) + 16;
   cudaError_t e = cudaFuncSetAttribute(eig_finish_kernel,
@@ -693,17 +735,15 @@ cudaError_t launch_gram_route(int kp, const MatDev* mats, int count, const Panel
   if (e != cudaSuccess) return e;
   // R1 = chol(X^T X)
   panel_gram_kernel<<<nxc, 256, gsm, s>>>(kp, xpanels, xchunks, nullptr, partial_x);
-  chol_kernel<<<count, 256, csm, s>>>(kp, mats, xoff, partial_x, nullptr, r1, rinv64, rinv32,
-                                      status);
+  chol_kernel<<<count, 256, csm, s>>>(kp, mats, xoff, partial_x, nullptr, r1, rinv, status);
   if (refine) {
     // R = chol(Q1^T Q1) R1 with Q1 = X R1^{-1}
-    panel_gram_kernel<<<nxc, 256, gsm, s>>>(kp, xpanels, xchunks, rinv32, partial_x);
-    chol_kernel<<<count, 256, csm, s>>>(kp, mats, xoff, partial_x, r1, r2, rinv64, rinv32,
-                                        status);
+    panel_gram_kernel<<<nxc, 256, gsm, s>>>(kp, xpanels, xchunks, rinv, partial_x);
+    chol_kernel<<<count, 256, csm, s>>>(kp, mats, xoff, partial_x, r1, r2, rinv, status);
   }
   // G_M = (Y R^{-1})^T (Y R^{-1})
-  panel_gram_kernel<<<nyc, 256, gsm, s>>>(kp, ypanels, ychunks, rinv32, partial_y);
-  eig_finish_kernel<<<count, 256, esm, s>>>(kp, mats, yoff, partial_y, rinv64, Wm, normA2, err,
+  panel_gram_kernel<<<nyc, 256, gsm, s>>>(kp, ypanels, ychunks, rinv, partial_y);
+  eig_finish_kernel<<<count, 256, esm, s>>>(kp, mats, yoff, partial_y, rinv, Wm, normA2, err,
                                             flags, err_mode, tau);
   return cudaGetLastError();
 }

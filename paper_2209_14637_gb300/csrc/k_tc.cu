@@ -96,7 +96,8 @@ enum {
   B_SFULL = B_YFREE + 1,
   B_SEMPTY = B_SFULL + 1,
   B_DRAIN = B_SEMPTY + 1,
-  B_COUNT = B_DRAIN + 1
+  B_DRAIN2 = B_DRAIN + 1,
+  B_COUNT = B_DRAIN2 + 1
 };
 static_assert(B_COUNT * 8 + 16 <= BAR_BYTES, "barrier area");
 
@@ -170,14 +171,8 @@ __device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
   return r;
 }
-__device__ __forceinline__ void fence_cluster() {
-  asm volatile("fence.acq_rel.cluster;" ::: "memory");
-}
 // Orders generic-proxy shared-memory writes before later async-proxy
 // (tensor-core) reads of the same memory.
-__device__ __forceinline__ void fence_proxy_async_cluster() {
-  asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
-}
 __device__ __forceinline__ void fence_proxy_async_cta() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -210,12 +205,6 @@ __device__ __forceinline__ void ld_cluster_v4(uint32_t addr, float& a, float& b,
                : "r"(addr)
                : "memory");
 }
-__device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint32_t a, uint32_t b,
-                                              uint32_t c, uint32_t d) {
-  asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr),
-               "r"(a), "r"(b), "r"(c), "r"(d)
-               : "memory");
-}
 // tcgen05
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -235,13 +224,6 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           bar)
-      : "memory");
-}
-__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::"
-      "cluster.b64 [%0], %1;" ::"r"(bar),
-      "h"(mask)
       : "memory");
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
@@ -320,6 +302,30 @@ __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity,
   }
 }
 
+// Sum of squares of one A stage (MC x 64 BF16), shared by 128 threads
+// (t = 0..127).  Eight independent FP32 accumulators per thread, each summing
+// 32 squares per stage, keep the dependent chains short; stages are summed
+// in FP64.
+__device__ __forceinline__ double stage_sumsq(const unsigned char* stage, int t) {
+  const uint4* st = reinterpret_cast<const uint4*>(stage);
+  float a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = 0.f;
+#pragma unroll 4
+  for (int e = t; e < STAGE_BYTES / 16; e += 128) {
+    const uint4 w = st[e];
+    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float lo = __uint_as_float(ww[i] << 16);
+      const float hi = __uint_as_float(ww[i] & 0xFFFF0000u);
+      a[2 * i] = fmaf(lo, lo, a[2 * i]);
+      a[2 * i + 1] = fmaf(hi, hi, a[2 * i + 1]);
+    }
+  }
+  return (double)((a[0] + a[1]) + (a[2] + a[3])) + (double)((a[4] + a[5]) + (a[6] + a[7]));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&v);
@@ -350,21 +356,22 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(bar(B_AFULL + s), 1);
-      mbar_init(bar(B_AEMPTY + s), 3);  // MMA-Y commit + two norm warps
+      mbar_init(bar(B_AEMPTY + s), 5);  // MMA-Y commit + four norm warps
     }
     for (int h = 0; h < 2; ++h) {
       mbar_init(bar(B_XFULL + h), 1);
       mbar_init(bar(B_XTEMPTY + h), 2);
       mbar_init(bar(B_PFULL + h), C);
       mbar_init(bar(B_PEMPTY + h), C);
-      mbar_init(bar(B_XBFULL + h), C);
-      mbar_init(bar(B_XBEMPTY + h), C);
+      mbar_init(bar(B_XBFULL + h), 1);   // own epilogue built X~ locally
+      mbar_init(bar(B_XBEMPTY + h), 1);  // own MMA-Y finished reading it
     }
     mbar_init(bar(B_YFULL), 1);
     mbar_init(bar(B_YFREE), 4);
     mbar_init(bar(B_SFULL), 1);
     mbar_init(bar(B_SEMPTY), 1);
     mbar_init(bar(B_DRAIN), 1);
+    mbar_init(bar(B_DRAIN2), 1);
     ctl->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -386,7 +393,6 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc_x = idesc_bf16(128, NB, 0, 1);
   const uint32_t idesc_y = idesc_bf16(128, 2 * kpad, 0, 0);
-  const uint16_t cmask = (uint16_t)((1u << C) - 1);
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -435,41 +441,16 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
       if (sloads > 0) drain_wait(bar(B_SFULL), (sloads - 1) & 1, P);
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
+    // ---------------------------------------- MMA issuers: lane 0 X, lane 1 Y
+    // MMA-X of block g+1 must not wait for the exchange of block g, so the
+    // two contractions are issued by different threads; each commits and
+    // drains only its own tcgen05 operations.
     if (lane == 0) {
       long long g = 0;
-      int swaits = 0, mi = 0;
+      int swaits = 0;
       const unsigned char* cur_img = nullptr;
-      // the block whose MMA-Y is still to be issued
-      long long pg = -1;
-      int ps = 0, pq = 0, pn = 0, pmi = 0;
       bool ok = true;
-      auto issue_y = [&](long long gy, int sy, int qy, int ny, int miy) {
-        const int h = (int)(gy & 1);
-        const uint32_t v = (uint32_t)(gy >> 1);
-        if (!bwait(bar(B_XBFULL + h), v & 1, ctl, P)) ok = false;
-        if (ok && qy == 0 && miy > 0 && !bwait(bar(B_YFREE), (miy - 1) & 1, ctl, P)) ok = false;
-        if (!ok) return;
-        fence_proxy_async_cta();
-        tc_fence_after();
-#pragma unroll 1
-        for (int t = 0; t < MC / 128; ++t) {
-#pragma unroll
-          for (int kk = 0; kk < NB / 16; ++kk) {
-            const uint64_t a = sdesc(sb + OFF_A + sy * STAGE_BYTES + t * 128 * 128 + kk * 32,
-                                     16, 1024);
-            const uint64_t b = sdesc(sb + OFF_XB + h * XB_BYTES + kk * 32, 16, 1024);
-            tc_mma(tmem + 2 * NB + t * 2 * kpad, a, b, idesc_y, (qy > 0 || kk > 0) ? 1u : 0u);
-          }
-        }
-        tc_commit(bar(B_AEMPTY + sy));
-        if (C > 1)
-          tc_commit_mc(bar(B_XBEMPTY + h), cmask);
-        else
-          tc_commit(bar(B_XBEMPTY + h));
-        if (qy == ny - 1) tc_commit(bar(B_YFULL));
-      };
-      for (int wi = w0; wi < w1 && ok; ++wi, ++mi) {
+      for (int wi = w0; wi < w1 && ok; ++wi) {
         const int d = P.work[wi];
         const MatDev& md = P.mats[d];
         const unsigned char* img = P.simg + P.simg_off[d] + (long long)rank * P.img_rank_bytes;
@@ -491,11 +472,8 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
           const uint32_t u = (uint32_t)(g / NST);
           const int h = (int)(g & 1);
           const uint32_t v = (uint32_t)(g >> 1);
-          if (!bwait(bar(B_AFULL + s), u & 1, ctl, P)) {
-            ok = false;
-            break;
-          }
-          if (!bwait(bar(B_XTEMPTY + h), (v & 1) ^ 1, ctl, P)) {
+          if (!bwait(bar(B_AFULL + s), u & 1, ctl, P) ||
+              !bwait(bar(B_XTEMPTY + h), (v & 1) ^ 1, ctl, P)) {
             ok = false;
             break;
           }
@@ -510,27 +488,57 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
           }
           tc_commit(bar(B_XFULL + h));
           if (q == nblk - 1 && next_img != img) tc_commit(bar(B_SEMPTY));
-          if (pg >= 0) issue_y(pg, ps, pq, pn, pmi);
-          pg = g;
-          ps = s;
-          pq = q;
-          pn = nblk;
-          pmi = mi;
         }
       }
-      if (ok && pg >= 0) issue_y(pg, ps, pq, pn, pmi);
-      // Drain: all MMAs issued by this thread complete before TMEM is freed.
       tc_commit(bar(B_DRAIN));
       drain_wait(bar(B_DRAIN), 0, P);
+    } else if (lane == 1) {
+      long long g = 0;
+      int mi = 0;
+      bool ok = true;
+      for (int wi = w0; wi < w1 && ok; ++wi, ++mi) {
+        const MatDev& md = P.mats[P.work[wi]];
+        const int nblk = (int)((md.n + NB - 1) / NB);
+        for (int q = 0; q < nblk && ok; ++q, ++g) {
+          const int s = (int)(g % NST);
+          const uint32_t u = (uint32_t)(g / NST);
+          const int h = (int)(g & 1);
+          const uint32_t v = (uint32_t)(g >> 1);
+          if (!bwait(bar(B_AFULL + s), u & 1, ctl, P) ||
+              !bwait(bar(B_XBFULL + h), v & 1, ctl, P) ||
+              (q == 0 && mi > 0 && !bwait(bar(B_YFREE), (mi - 1) & 1, ctl, P))) {
+            ok = false;
+            break;
+          }
+          fence_proxy_async_cta();
+          tc_fence_after();
+#pragma unroll 1
+          for (int t = 0; t < MC / 128; ++t) {
+#pragma unroll
+            for (int kk = 0; kk < NB / 16; ++kk) {
+              const uint64_t a =
+                  sdesc(sb + OFF_A + s * STAGE_BYTES + t * 128 * 128 + kk * 32, 16, 1024);
+              const uint64_t b = sdesc(sb + OFF_XB + h * XB_BYTES + kk * 32, 16, 1024);
+              tc_mma(tmem + 2 * NB + t * 2 * kpad, a, b, idesc_y, (q > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          tc_commit(bar(B_AEMPTY + s));
+          tc_commit(bar(B_XBEMPTY + h));
+          if (q == nblk - 1) tc_commit(bar(B_YFULL));
+        }
+      }
+      tc_commit(bar(B_DRAIN2));
+      drain_wait(bar(B_DRAIN2), 0, P);
     }
   } else if (warp >= 2 && warp <= 5) {
-    // ----------------------------------------- X exchange (warps 4, 5) and Y out
+    // ------- X exchange (warps 4, 5) or ||A||^2 (warps 2, 3), then Y out (all four)
     const int lane_base = (warp & 3) * 32;
     const bool xwarp = (warp >= 4);
+    double tot = 0.0;
     const int c = lane_base + lane;  // TMEM lane = row c of D_x / row of D_y tile
     long long g = 0;
     int mi = 0;
-    constexpr int WC = NB / C;  // columns this CTA reduces
+    constexpr int WC = NB / C;  // columns of X this CTA writes to HBM
     for (int wi = w0; wi < w1; ++wi, ++mi) {
       const int d = P.work[wi];
       const MatDev& md = P.mats[d];
@@ -538,7 +546,15 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
       const long long n = md.n, m = md.m;
       const int nblk = (int)((n + NB - 1) / NB);
       for (int q = 0; q < nblk; ++q, ++g) {
-        if (!xwarp) continue;
+        if (!xwarp) {
+          const int s = (int)(g % NST);
+          const uint32_t u = (uint32_t)(g / NST);
+          if (bwait_warp(bar(B_AFULL + s), u & 1, ctl, P))
+            tot += stage_sumsq(sm + OFF_A + s * STAGE_BYTES, tid - 64);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(B_AEMPTY + s));
+          continue;
+        }
         const int h = (int)(g & 1);
         const uint32_t v = (uint32_t)(g >> 1);
         float xr[NB];
@@ -552,6 +568,8 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_XTEMPTY + h));
+        // publish this CTA's partial D_x rows (peers read them once they
+        // have all arrived on this CTA's PFULL)
         bwait(bar(B_PEMPTY + h), (v & 1) ^ 1, ctl, P);
         float* prow = (float*)(sm + OFF_P + h * P_BYTES + c * P_ROW);
         if (c < k) {
@@ -559,7 +577,8 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
           for (int j = 0; j < NB; j += 4)
             *reinterpret_cast<float4*>(prow + j) = make_float4(xr[j], xr[j + 1], xr[j + 2], xr[j + 3]);
         }
-        fence_cluster();
+        // The CTA barrier orders both warps' writes before one thread's
+        // cluster-scope release arrive, which publishes them to the peers.
         named_bar(1, 64);
         if (warp == 4 && lane == 0) {
           const uint32_t pf = bar(B_PFULL + h);
@@ -567,87 +586,88 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
           for (int r = 0; r < C; ++r) mbar_arrive_cluster(mapa(pf, r));
         }
         bwait(bar(B_PFULL + h), v & 1, ctl, P);
-        float acc[WC];
-#pragma unroll
-        for (int j = 0; j < WC; ++j) acc[j] = 0.f;
-        if (c < k) {
-          const uint32_t src = smem_u32(prow) + rank * WC * 4;
-#pragma unroll
-          for (int r = 0; r < C; ++r) {
-            const uint32_t ra = mapa(src, r);
-#pragma unroll
-            for (int j = 0; j < WC; j += 4) {
-              float a0, a1, a2, a3;
-              ld_cluster_v4(ra + j * 4, a0, a1, a2, a3);
-              acc[j] += a0;
-              acc[j + 1] += a1;
-              acc[j + 2] += a2;
-              acc[j + 3] += a3;
-            }
-          }
-        }
+        // X row c of this block = sum of the C partials (every CTA forms the
+        // whole block itself: one round trip instead of reduce + gather).
         // Two-term BF16 split X = X_hi + X_lo (X_hi = BF16(X), X_lo =
         // BF16(X - X_hi)); MMA-Y multiplies A by both, so Y = A (X_hi + X_lo)
         // carries about 16 significant bits of X instead of 8.  X in HBM
-        // holds X_hi + X_lo, the values Y is built from.
-        uint32_t phi[WC / 2], plo[WC / 2];
-        float xs[WC];
-#pragma unroll
-        for (int j = 0; j < WC; j += 2) {
-          const __nv_bfloat16 h0 = __float2bfloat16_rn(acc[j]);
-          const __nv_bfloat16 h1 = __float2bfloat16_rn(acc[j + 1]);
-          const float f0 = __bfloat162float(h0), f1 = __bfloat162float(h1);
-          const __nv_bfloat16 l0 = __float2bfloat16_rn(acc[j] - f0);
-          const __nv_bfloat16 l1 = __float2bfloat16_rn(acc[j + 1] - f1);
-          xs[j] = f0 + __bfloat162float(l0);
-          xs[j + 1] = f1 + __bfloat162float(l1);
-          __nv_bfloat162 hh, ll;
-          hh.x = h0;
-          hh.y = h1;
-          ll.x = l0;
-          ll.y = l1;
-          phi[j / 2] = *reinterpret_cast<const uint32_t*>(&hh);
-          plo[j / 2] = *reinterpret_cast<const uint32_t*>(&ll);
-        }
-        if (c < k) {
-          float* Xm = P.X + md.offX;
-          const long long jb = (long long)q * NB + rank * WC;
-#pragma unroll
-          for (int j = 0; j < WC; ++j) {
-            const long long jj = jb + j;
-            if (jj < n) Xm[jj * P.kp + c] = xs[j];
-          }
-        }
+        // holds X_hi + X_lo, the values Y is built from.  Done in two halves
+        // of 32 columns to bound register use.
         bwait(bar(B_XBEMPTY + h), (v & 1) ^ 1, ctl, P);
         if (c < k) {
+          const uint32_t src = smem_u32(prow);
+          float* Xm = P.X + md.offX;
 #pragma unroll
-          for (int half = 0; half < 2; ++half) {
-            const int row = c + half * kpad;
-            const uint32_t* src = half ? plo : phi;
-            const uint32_t xrow =
-                sb + OFF_XB + h * XB_BYTES + (row >> 3) * 1024 + (row & 7) * 128;
+          for (int hb = 0; hb < 2; ++hb) {
+            float acc[32];
 #pragma unroll
-            for (int u = 0; u < WC / 8; ++u) {
-              const int unit = (int)(rank * WC / 8) + u;
-              const uint32_t off = xrow + (uint32_t)(((unit ^ (row & 7)) & 7) << 4);
+            for (int j = 0; j < 32; ++j) acc[j] = 0.f;
 #pragma unroll
-              for (int r = 0; r < C; ++r)
-                st_cluster_v4(mapa(off, r), src[u * 4], src[u * 4 + 1], src[u * 4 + 2],
-                              src[u * 4 + 3]);
+            for (int r = 0; r < C; ++r) {
+              const uint32_t ra = mapa(src + hb * 128, r);
+#pragma unroll
+              for (int j = 0; j < 32; j += 4) {
+                float a0, a1, a2, a3;
+                ld_cluster_v4(ra + j * 4, a0, a1, a2, a3);
+                acc[j] += a0;
+                acc[j + 1] += a1;
+                acc[j + 2] += a2;
+                acc[j + 3] += a3;
+              }
+            }
+            uint32_t phi[16], plo[16];
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              const __nv_bfloat16 h0 = __float2bfloat16_rn(acc[j]);
+              const __nv_bfloat16 h1 = __float2bfloat16_rn(acc[j + 1]);
+              const float f0 = __bfloat162float(h0), f1 = __bfloat162float(h1);
+              const __nv_bfloat16 l0 = __float2bfloat16_rn(acc[j] - f0);
+              const __nv_bfloat16 l1 = __float2bfloat16_rn(acc[j + 1] - f1);
+              acc[j] = f0 + __bfloat162float(l0);
+              acc[j + 1] = f1 + __bfloat162float(l1);
+              __nv_bfloat162 hh, ll;
+              hh.x = h0;
+              hh.y = h1;
+              ll.x = l0;
+              ll.y = l1;
+              phi[j / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+              plo[j / 2] = *reinterpret_cast<const uint32_t*>(&ll);
+            }
+            const long long jb = (long long)q * NB + hb * 32;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {  // this CTA's 64/C columns go to HBM
+              const long long jj = jb + j;
+              if ((hb * 32 + j) / WC == (int)rank && jj < n) Xm[jj * P.kp + c] = acc[j];
+            }
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+              const int row = c + half * kpad;
+              const uint32_t* w = half ? plo : phi;
+              unsigned char* xrow =
+                  sm + OFF_XB + h * XB_BYTES + (row >> 3) * 1024 + (row & 7) * 128;
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int unit = hb * 4 + u;
+                *reinterpret_cast<uint4*>(xrow + (((unit ^ (row & 7)) & 7) << 4)) =
+                    make_uint4(w[u * 4], w[u * 4 + 1], w[u * 4 + 2], w[u * 4 + 3]);
+              }
             }
           }
         }
-        fence_proxy_async_cluster();
-        fence_cluster();
+        fence_proxy_async_cta();
         named_bar(1, 64);
         if (warp == 4 && lane == 0) {
-          const uint32_t xf = bar(B_XBFULL + h), pe = bar(B_PEMPTY + h);
+          // peers' partials are consumed: they may reuse their P buffers
+          const uint32_t pe = bar(B_PEMPTY + h);
 #pragma unroll
-          for (int r = 0; r < C; ++r) {
-            mbar_arrive_cluster(mapa(xf, r));
-            mbar_arrive_cluster(mapa(pe, r));
-          }
+          for (int r = 0; r < C; ++r) mbar_arrive_cluster(mapa(pe, r));
         }
+        if (warp == 4 && lane == 0) mbar_arrive(bar(B_XBFULL + h));
+      }
+      if (!xwarp) {
+        tot = warp_sum(tot);
+        if (lane == 0) atomicAdd(P.normA2 + d, tot);
+        tot = 0.0;
       }
       // ---- Y epilogue for this matrix: the CTA's MC rows of Y = A X~
       if (bwait_warp(bar(B_YFULL), mi & 1, ctl, P)) {
@@ -684,13 +704,11 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
         if (g > h) {
           const long long last = ((g - 1 - h) / 2) * 2 + h;
           drain_wait(bar(B_PEMPTY + h), (uint32_t)((last >> 1) & 1), P);
-          drain_wait(bar(B_XBEMPTY + h), (uint32_t)((last >> 1) & 1), P);
         }
       }
     }
   } else {
     // ------------------------------------------------ ||A||_F^2 (warps 6, 7)
-    const int t2 = tid - 6 * 32;  // 0..63
     long long g = 0;
     for (int wi = w0; wi < w1; ++wi) {
       const int d = P.work[wi];
@@ -700,28 +718,8 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
       for (int q = 0; q < nblk; ++q, ++g) {
         const int s = (int)(g % NST);
         const uint32_t u = (uint32_t)(g / NST);
-        if (bwait_warp(bar(B_AFULL + s), u & 1, ctl, P)) {
-          const uint4* st = reinterpret_cast<const uint4*>(sm + OFF_A + s * STAGE_BYTES);
-          float sum = 0.f, comp = 0.f;
-#pragma unroll 4
-          for (int e = t2; e < STAGE_BYTES / 16; e += 64) {
-            const uint4 w = st[e];
-            const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
-            float part = 0.f;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const float lo = __uint_as_float(ww[i] << 16);
-              const float hi = __uint_as_float(ww[i] & 0xFFFF0000u);
-              part = fmaf(lo, lo, part);
-              part = fmaf(hi, hi, part);
-            }
-            const float y = part - comp;
-            const float t = sum + y;
-            comp = (t - sum) - y;
-            sum = t;
-          }
-          tot += (double)sum - (double)comp;
-        }
+        if (bwait_warp(bar(B_AFULL + s), u & 1, ctl, P))
+          tot += stage_sumsq(sm + OFF_A + s * STAGE_BYTES, tid - 128);
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_AEMPTY + s));
       }

@@ -277,9 +277,9 @@ static cudaError_t capture_plan(tsk_plan p, cudaEvent_t evb, cudaEvent_t eve) {
                            (const int2*)(base + p->o_xch), p->nxc,
                            (const int*)(base + p->o_xoff), (const int2*)(base + p->o_ych),
                            p->nyc, (const int*)(base + p->o_yoff), (float*)(base + p->o_px),
-                           (float*)(base + p->o_py), (double*)(base + p->o_r1),
-                           (double*)(base + p->o_r2), (double*)(base + p->o_ri64),
-                           (float*)(base + p->o_ri32), (float*)(base + p->o_W), d_norm, d_err,
+                           (float*)(base + p->o_py), (float*)(base + p->o_r1),
+                           (float*)(base + p->o_r2), (float*)(base + p->o_ri32),
+                           (float*)(base + p->o_W), d_norm, d_err,
                            (int*)(base + p->o_flag), h->opts.err_mode, tau,
                            h->opts.refine_q ? 1 : 0, h->d_status, s);
     launches += h->opts.refine_q ? 6 : 4;

@@ -114,10 +114,10 @@ cudaError_t launch_sym_eig(bool dbl, const void* H, int p, void* theta,
 cudaError_t launch_gram_route(int kp, const MatDev* mats, int count, const PanelDev* xpanels,
                               const PanelDev* ypanels, const int2* xchunks, int nxc,
                               const int* xoff, const int2* ychunks, int nyc, const int* yoff,
-                              float* partial_x, float* partial_y, double* r1, double* r2,
-                              double* rinv64, float* rinv32, float* Wm, double* normA2,
-                              double* err, int* flags, int err_mode, double tau, int refine,
-                              int* status, cudaStream_t s);
+                              float* partial_x, float* partial_y, float* r1, float* r2,
+                              float* rinv, float* Wm, double* normA2, double* err, int* flags,
+                              int err_mode, double tau, int refine, int* status,
+                              cudaStream_t s);
 int gram_route_chunks(long long rows);
 
 // k_refine.cu
