@@ -259,6 +259,35 @@ tsk_status tsk_refine_sketch(tsk_handle h, const tsk_mat_desc* train,
                              const tsk_refine_opts* opts, const void* S_tensor,
                              void* dS, double* history, tsk_stream stream);
 
+/* ---- allocation-free SCW (no counterpart in the paper) ------------------ */
+
+/* Bytes of the static device array that tsk_approx_noalloc works in. */
+#define TSK_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* SCW with errors (as tsk_approx_batch) for ONE matrix, for callers that must
+   not allocate device memory at the point of the call: code that runs inside
+   a memory pool owned by another framework, latency-critical paths where
+   cudaMalloc (which may synchronise the device and has unbounded latency) is
+   not allowed, and deployments that budget every byte of GPU memory in
+   advance.  No handle is needed and nothing is allocated: every intermediate
+   lives in a file-scope __device__ array of TSK_NOALLOC_SCRATCH_BYTES (8 MiB)
+   that each GPU which loads the library holds until the process exits.
+   Matrices needing more than that ((m + n) * k_pad * element size plus a few
+   KB of descriptors, k_pad = k rounded up to 16) are rejected with
+   TSK_EINVAL and a message in tsk_last_error(NULL).
+   mat: host pointer to the descriptor (device A and S as for
+   tsk_approx_batch; any of the three precisions, always the CUDA-core
+   kernels).  err: device, one double; normA2: device, one double, nullable.
+   The first call on each device looks up the array's device address with
+   cudaGetSymbolAddress while that device is current, so make that first call
+   before any stream capture.  All calls share the one array and it keeps the
+   previous call's contents (the call clears what it accumulates into): calls
+   that overlap on the GPU -- on two streams, or from two host threads --
+   race and corrupt each other's results.  Asynchronous on stream; other
+   errors as in the rest of this header (tsk_last_error(NULL) has the text). */
+tsk_status tsk_approx_noalloc(const tsk_mat_desc* mat, tsk_prec prec,
+                              double* err, double* normA2, tsk_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -97,6 +97,7 @@ def load_library(path: str = LIB_PATH):
         "tsk_plan_set_probe": ([P, P, P], I32),
         "tsk_error": ([P, I64, C.POINTER(MatDesc), I32, C.POINTER(MatOut), P, P], I32),
         "tsk_ivy_grad": ([P, I64, C.POINTER(MatDesc), I32, P, P, P, P], I32),
+        "tsk_approx_noalloc": ([C.POINTER(MatDesc), I32, P, P, P], I32),
         "tsk_default_refine_options": ([C.POINTER(RefineOpts)], None),
         "tsk_refine_sketch": ([P, C.POINTER(MatDesc), I64, C.POINTER(MatDesc), I64, I32,
                                C.POINTER(RefineOpts), P, P, C.POINTER(D), P], I32),

@@ -63,6 +63,13 @@ static void set_err(tsk_handle h, const char* fmt, ...) {
   va_end(ap);
 }
 
+void tsk::set_thread_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_create_error, sizeof(g_create_error), fmt, ap);
+  va_end(ap);
+}
+
 #define TSK_CUDA(h, call)                                                   \
   do {                                                                      \
     cudaError_t e_ = (call);                                                \

@@ -62,6 +62,9 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Sets the calling thread's error text (what tsk_last_error(NULL) returns).
+void set_thread_error(const char* fmt, ...);
+
 // ---- launchers (host functions), defined in the .cu files ---------------
 
 // k_simt.cu
