@@ -438,7 +438,7 @@ cudaError_t launch_sym_eig(bool dbl, const void* H, int p, void* theta,
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int GCHUNK = 256;  // rows per partial Gram
-constexpr int GSUB = 32;     // rows staged in shared memory at a time
+constexpr int GSUB = 64;     // rows staged in shared memory at a time
 }  // namespace
 
 // One CTA per (panel, chunk): partial G = P_c^T P_c over the chunk's rows,
@@ -454,7 +454,7 @@ panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __res
   const int2 ch = chunks[blockIdx.x];
   const PanelDev pd = panels[ch.x];
   const int k = pd.k, ld = pd.ld;
-  const int ldp = kp + 1;
+  const int ldp = kp + 4;              // 16-byte aligned rows
   float* Ps = (float*)smem_raw;        // GSUB x ldp
   float* Ts = Ps + GSUB * ldp;         // GSUB x ldp transformed rows
   float* Rs = Ts + GSUB * ldp;         // kp x kp
@@ -485,32 +485,50 @@ panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __res
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
   const long long r0 = (long long)ch.y * GCHUNK;
   const long long r1 = min(pd.rows, r0 + GCHUNK);
+  const int q4 = kp / 4;  // float4 per row
   for (long long s0 = r0; s0 < r1; s0 += GSUB) {
     __syncthreads();
-    for (int e = tid; e < GSUB * kp; e += blockDim.x) {
-      const int ii = e / kp, c = e % kp;
+    for (int e = tid; e < GSUB * q4; e += blockDim.x) {
+      const int ii = e / q4, c4 = (e % q4) * 4;
       const long long i = s0 + ii;
-      Ps[ii * ldp + c] = (i < r1 && c < k) ? P[i * ld + c] : 0.f;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < r1) {
+        v = *reinterpret_cast<const float4*>(P + i * ld + c4);
+        if (c4 + 0 >= k) v.x = 0.f;
+        if (c4 + 1 >= k) v.y = 0.f;
+        if (c4 + 2 >= k) v.z = 0.f;
+        if (c4 + 3 >= k) v.w = 0.f;
+      }
+      *reinterpret_cast<float4*>(Ps + ii * ldp + c4) = v;
     }
     __syncthreads();
     const float* src = Ps;
     if (tr) {
-      for (int e = tid; e < GSUB * kp; e += blockDim.x) {
-        const int ii = e / kp, c = e % kp;
-        float t = 0.f;
-        for (int cc = 0; cc <= c && cc < k; ++cc) t = fmaf(Ps[ii * ldp + cc], Rs[cc * kp + c], t);
-        Ts[ii * ldp + c] = (c < k) ? t : 0.f;
+      // Ts = Ps Rinv (Rinv upper triangular), four columns per work item
+      for (int e = tid; e < GSUB * q4; e += blockDim.x) {
+        const int ii = e / q4, c4 = (e % q4) * 4;
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int top = min(k, c4 + 4);
+        for (int cc = 0; cc < top; ++cc) {
+          const float p = Ps[ii * ldp + cc];
+          const float4 r = *reinterpret_cast<const float4*>(Rs + cc * kp + c4);
+          t.x = fmaf(p, r.x, t.x);
+          t.y = fmaf(p, r.y, t.y);
+          t.z = fmaf(p, r.z, t.z);
+          t.w = fmaf(p, r.w, t.w);
+        }
+        *reinterpret_cast<float4*>(Ts + ii * ldp + c4) = t;
       }
       __syncthreads();
       src = Ts;
     }
     if (active) {
+#pragma unroll 4
       for (int ii = grp; ii < GSUB; ii += groups) {
-        float x[4], y[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) x[a] = src[ii * ldp + ty * 4 + a];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) y[b] = src[ii * ldp + tx * 4 + b];
+        const float4 x4 = *reinterpret_cast<const float4*>(src + ii * ldp + ty * 4);
+        const float4 y4 = *reinterpret_cast<const float4*>(src + ii * ldp + tx * 4);
+        const float x[4] = {x4.x, x4.y, x4.z, x4.w};
+        const float y[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -537,8 +555,8 @@ panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __res
     float* out = partial + (long long)blockIdx.x * kp * kp;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) out[(ty * 4 + a) * kp + tx * 4 + b] = acc[a][b];
+      *reinterpret_cast<float4*>(out + (ty * 4 + a) * kp + tx * 4) =
+          make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
   }
 }
 
@@ -634,8 +652,76 @@ chol_kernel(int kp, const MatDev* __restrict__ mats, const int* __restrict__ chu
   }
 }
 
-// One CTA per matrix: G_M (FP64) from its partials; eigenvectors by one-sided
-// Jacobi in FP32; captured energy in FP64; err, sigma, W = R_X^{-1} V_r.
+// Two-sided cyclic Jacobi on the symmetric A (k x k, leading dimension ld) in
+// the parallel round-robin order: each round computes the rotations of its
+// disjoint pairs from (A_pp, A_qq, A_pq), then applies them to the columns
+// of A and V, then to the rows of A.  Whole-block cooperative.  On return
+// diag(A) holds the eigenvalues and the columns of V the eigenvectors.
+template <typename T>
+__device__ void jacobi_sym(T* A, T* V, int k, int ld, int max_sweeps, T tol, T* cs,
+                           int* pq, int* rotated) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int kk = k + (k & 1), np = kk / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) *rotated = 0;
+    __syncthreads();
+    for (int round = 0; round < kk - 1; ++round) {
+      for (int i = tid; i < np; i += nt) {
+        int p, q;
+        rr_pair(round, i, kk, p, q);
+        T c = T(1), sn = T(0);
+        if (p < k && q < k) {
+          const T apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
+          if (fabs(apq) > tol * sqrt(fabs(app * aqq)) && fabs(apq) > Eps<T>::tiny) {
+            const T tau = (aqq - app) / (T(2) * apq);
+            const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+            c = T(1) / sqrt(T(1) + t * t);
+            sn = t * c;
+            *rotated = 1;
+          }
+        } else {
+          p = -1;
+        }
+        cs[2 * i] = c;
+        cs[2 * i + 1] = sn;
+        pq[2 * i] = p;
+        pq[2 * i + 1] = q;
+      }
+      __syncthreads();
+      for (int e = tid; e < np * k; e += nt) {  // columns of A and V
+        const int i = e / k, r = e % k;
+        const int p = pq[2 * i], q = pq[2 * i + 1];
+        if (p < 0) continue;
+        const T c = cs[2 * i], sn = cs[2 * i + 1];
+        const T x = A[r * ld + p], y = A[r * ld + q];
+        A[r * ld + p] = c * x - sn * y;
+        A[r * ld + q] = sn * x + c * y;
+        const T vx = V[r * ld + p], vy = V[r * ld + q];
+        V[r * ld + p] = c * vx - sn * vy;
+        V[r * ld + q] = sn * vx + c * vy;
+      }
+      __syncthreads();
+      for (int e = tid; e < np * k; e += nt) {  // rows of A
+        const int i = e / k, r = e % k;
+        const int p = pq[2 * i], q = pq[2 * i + 1];
+        if (p < 0) continue;
+        const T c = cs[2 * i], sn = cs[2 * i + 1];
+        const T x = A[p * ld + r], y = A[q * ld + r];
+        A[p * ld + r] = c * x - sn * y;
+        A[q * ld + r] = sn * x + c * y;
+      }
+      __syncthreads();
+    }
+    if (*rotated == 0) break;
+  }
+}
+
+// One CTA per matrix: G_M (FP64) from its partials; eigenpairs of G_M by
+// two-sided Jacobi in FP32; V_r brought back to orthonormal in FP64 with one
+// step V <- V (I - (V^T V - I) / 2) (its error is quadratic in the FP32
+// orthogonality error); captured energy tr(V_r^T G_M V_r) in FP64 (Ky Fan:
+// equal to sum_{i<=r} lambda_i up to second-order terms); err, sigma and
+// W = R_X^{-1} V_r.
 __global__ void __launch_bounds__(256)
 eig_finish_kernel(int kp, const MatDev* __restrict__ mats, const int* __restrict__ chunk_off,
                   const float* __restrict__ partial, const float* __restrict__ rinv,
@@ -643,72 +729,87 @@ eig_finish_kernel(int kp, const MatDev* __restrict__ mats, const int* __restrict
                   double* __restrict__ err, int* __restrict__ flags, int err_mode, double tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ld = kp + 1;
-  double* G = (double*)smem_raw;     // kp x kp
-  float* Mf = (float*)(G + kp * kp); // kp x ld
-  float* V = Mf + kp * ld;           // kp x ld
-  float* sig = V + kp * ld;          // kp
-  int* order = (int*)(sig + kp);     // kp
+  double* G = (double*)smem_raw;      // kp x kp
+  double* Vd = G + kp * kp;           // kp x kp : V_r (FP64 copy of the FP32 result)
+  double* Ed = Vd + kp * kp;          // kp x kp : V_r^T V_r - I
+  double* Vc = Ed + kp * kp;          // kp x kp : corrected V_r
+  float* Af = (float*)(Vc + kp * kp); // kp x ld
+  float* V = Af + kp * ld;            // kp x ld
+  float* cs = V + kp * ld;            // 2 * kp
+  float* lam = cs + 2 * kp;           // kp
+  int* pq = (int*)(lam + kp);         // 2 * kp
+  int* order = pq + 2 * kp;           // kp
   __shared__ int rotated;
-  __shared__ double cap_part[8];
+  __shared__ double red[8];
   const int b = blockIdx.x, tid = threadIdx.x;
   const MatDev md = mats[b];
   const int k = md.k, r = md.r;
   const int c0 = chunk_off[b], c1 = chunk_off[b + 1];
   for (int e = tid; e < kp * kp; e += blockDim.x) {
     const int i = e / kp, c = e % kp;
-    G[e] = (i < k && c < k) ? gram_entry(partial, c0, c1, kp, i, c) : 0.0;
-  }
-  __syncthreads();
-  for (int e = tid; e < kp * kp; e += blockDim.x) {
-    const int i = e / kp, c = e % kp;
-    Mf[i * ld + c] = (float)G[i * kp + c];
+    const double g = (i < k && c < k) ? gram_entry(partial, c0, c1, kp, i, c) : 0.0;
+    G[e] = g;
+    Af[i * ld + c] = (float)g;
     V[i * ld + c] = (i == c) ? 1.f : 0.f;
   }
   __syncthreads();
-  // G_M is the square of a matrix with condition number ~1e2, so in FP32
-  // the off-diagonal noise of the rotated columns stays near eps * kappa(G_M)
-  // and a relative threshold is never met.  The eigenvalues converge
-  // quadratically and are at FP32 accuracy after a handful of sweeps; the
-  // captured energy below is insensitive (second order) to the remaining
-  // eigenvector error, so the sweeps are capped.
-  jacobi_columns<float>(Mf, V, k, k, ld, 10, &rotated);
+  jacobi_sym<float>(Af, V, k, ld, 12, 4.0e-6f, cs, pq, &rotated);
+  for (int c = tid; c < k; c += blockDim.x) lam[c] = Af[c * ld + c];
   __syncthreads();
-  column_norms_sorted<float>(Mf, k, k, ld, sig, order);
-  // captured energy: sum_{c<r} v_c^T G v_c in FP64 (Ky Fan), one warp per c
-  const int warp = tid >> 5, lane = tid & 31;
-  double mine = 0.0;
-  for (int c = warp; c < r; c += (int)(blockDim.x >> 5)) {
-    const int col = order[c];
-    double part = 0.0;
-    for (int i = lane; i < k; i += 32) {
-      double gi = 0.0;
-      for (int j = 0; j < k; ++j) gi += G[i * kp + j] * (double)V[j * ld + col];
-      part += (double)V[i * ld + col] * gi;
-    }
-    mine += warp_sum(part);
+  for (int c = tid; c < k; c += blockDim.x) {  // descending eigenvalues
+    int rank = 0;
+    for (int c2 = 0; c2 < k; ++c2) rank += (lam[c2] > lam[c]) || (lam[c2] == lam[c] && c2 < c);
+    order[rank] = c;
   }
-  if (lane == 0) cap_part[warp] = mine;
+  __syncthreads();
+  for (int e = tid; e < k * r; e += blockDim.x) {
+    const int i = e / r, c = e % r;
+    Vd[i * kp + c] = (double)V[i * ld + order[c]];
+  }
+  __syncthreads();
+  for (int e = tid; e < r * r; e += blockDim.x) {  // E = V_r^T V_r - I
+    const int a = e / r, c = e % r;
+    double t = (a == c) ? -1.0 : 0.0;
+    for (int i = 0; i < k; ++i) t += Vd[i * kp + a] * Vd[i * kp + c];
+    Ed[a * kp + c] = t;
+  }
+  __syncthreads();
+  for (int e = tid; e < k * r; e += blockDim.x) {  // V_r <- V_r - V_r E / 2
+    const int i = e / r, c = e % r;
+    double t = 0.0;
+    for (int a = 0; a < r; ++a) t += Vd[i * kp + a] * Ed[a * kp + c];
+    Vc[i * kp + c] = Vd[i * kp + c] - 0.5 * t;
+  }
+  __syncthreads();
+  double part = 0.0;  // tr(V_r^T G V_r)
+  for (int e = tid; e < k * r; e += blockDim.x) {
+    const int i = e / r, c = e % r;
+    double gv = 0.0;
+    for (int j = 0; j < k; ++j) gv += G[i * kp + j] * Vc[j * kp + c];
+    part += Vc[i * kp + c] * gv;
+  }
+  part = warp_sum(part);
+  if ((tid & 31) == 0) red[tid >> 5] = part;
   __syncthreads();
   if (tid == 0) {
     double cap = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) cap += cap_part[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) cap += red[w];
     const double tot = normA2[b];
     const double e2 = tot - cap;
     err[b] = sqrt(e2 > 0.0 ? e2 : 0.0);
     flags[b] = (err_mode == 2) || (err_mode == 0 && e2 < tau * tot);
   }
   if (md.sigma != nullptr)
-    for (int c = tid; c < k; c += blockDim.x) ((float*)md.sigma)[c] = sqrtf(sig[order[c]]);
+    for (int c = tid; c < k; c += blockDim.x)
+      ((float*)md.sigma)[c] = sqrtf(fmaxf(lam[order[c]], 0.f));
   // W = R_X^{-1} V_r
   const float* Ri = rinv + (long long)b * kp * kp;
   float* Wout = Wm + (long long)b * kp * kp;
   for (int e = tid; e < kp * kp; e += blockDim.x) {
     const int i = e / kp, c = e % kp;
     float t = 0.f;
-    if (i < k && c < r) {
-      const int col = order[c];
-      for (int p = i; p < k; ++p) t = fmaf(Ri[i * kp + p], V[p * ld + col], t);
-    }
+    if (i < k && c < r)
+      for (int q = i; q < k; ++q) t = fmaf(Ri[i * kp + q], (float)Vc[q * kp + c], t);
     Wout[e] = t;
   }
 }
@@ -721,10 +822,11 @@ cudaError_t launch_gram_route(int kp, const MatDev* mats, int count, const Panel
                               int err_mode, double tau, int refine, int* status,
                               cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  const size_t gsm = (size_t)(2 * GSUB * (kp + 1) + kp * kp + 256 * 16) * sizeof(float);
+  const size_t gsm = (size_t)(2 * GSUB * (kp + 4) + kp * kp + 256 * 16) * sizeof(float);
   const size_t csm = (size_t)3 * kp * (kp + 1) * sizeof(float);
-  const size_t esm = (size_t)kp * kp * sizeof(double) + (size_t)2 * kp * (kp + 1) * sizeof(float) +
-                     kp * sizeof(float) + kp * sizeof(int) + 16;
+  const size_t esm = (size_t)4 * kp * kp * sizeof(double) +
+                     (size_t)2 * kp * (kp + 1) * sizeof(float) + 3 * kp * sizeof(float) +
+                     3 * kp * sizeof(int) + 16;
   cudaError_t e = cudaFuncSetAttribute(eig_finish_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm);
   if (e == cudaSuccess)

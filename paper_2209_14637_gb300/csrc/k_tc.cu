@@ -52,7 +52,7 @@ constexpr int NB = 64;         // columns of A per block (one 128-byte row)
 constexpr int MC = 512;        // rows of A per CTA
 constexpr int NST = 2;         // A stages
 constexpr int KPAD_MAX = 48;   // largest padded k this kernel takes
-constexpr int NTHREADS = 256;  // 8 warps
+constexpr int NTHREADS = 288;  // 9 warps
 constexpr int BOX_ROWS = 256;  // TMA box height (hardware limit 256)
 
 constexpr int STAGE_BYTES = MC * 128;
@@ -440,12 +440,13 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
       }
       if (sloads > 0) drain_wait(bar(B_SFULL), (sloads - 1) & 1, P);
     }
-  } else if (warp == 1) {
-    // ---------------------------------------- MMA issuers: lane 0 X, lane 1 Y
+  } else if (warp == 1 || warp == 8) {
+    // ------------------------------- MMA issuers: warp 1 -> MMA-X, warp 8 -> MMA-Y
     // MMA-X of block g+1 must not wait for the exchange of block g, so the
-    // two contractions are issued by different threads; each commits and
-    // drains only its own tcgen05 operations.
-    if (lane == 0) {
+    // two contractions are issued from different warps (a thread suspended in
+    // an mbarrier wait would also hold up a sibling lane of its own warp);
+    // each issuer commits and drains only its own tcgen05 operations.
+    if (warp == 1 && lane == 0) {
       long long g = 0;
       int swaits = 0;
       const unsigned char* cur_img = nullptr;
@@ -492,7 +493,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
       }
       tc_commit(bar(B_DRAIN));
       drain_wait(bar(B_DRAIN), 0, P);
-    } else if (lane == 1) {
+    } else if (warp == 8 && lane == 0) {
       long long g = 0;
       int mi = 0;
       bool ok = true;
@@ -557,26 +558,28 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
         }
         const int h = (int)(g & 1);
         const uint32_t v = (uint32_t)(g >> 1);
-        float xr[NB];
+        // publish this CTA's partial D_x rows, 16 columns at a time (peers
+        // read them once they have all arrived on this CTA's PFULL)
+        bwait(bar(B_PEMPTY + h), (v & 1) ^ 1, ctl, P);
+        float* prow = (float*)(sm + OFF_P + h * P_BYTES + c * P_ROW);
         if (bwait_warp(bar(B_XFULL + h), v & 1, ctl, P)) {
           tc_fence_after();
+#pragma unroll 1
+          for (int j = 0; j < NB; j += 16) {
+            float xr[16];
+            tmem_ld16(tmem + ((uint32_t)lane_base << 16) + h * NB + j, xr);
+            tmem_wait_ld();
+            if (c < k) {
 #pragma unroll
-          for (int j = 0; j < NB; j += 16)
-            tmem_ld16(tmem + ((uint32_t)lane_base << 16) + h * NB + j, xr + j);
-          tmem_wait_ld();
+              for (int e = 0; e < 16; e += 4)
+                *reinterpret_cast<float4*>(prow + j + e) =
+                    make_float4(xr[e], xr[e + 1], xr[e + 2], xr[e + 3]);
+            }
+          }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_XTEMPTY + h));
-        // publish this CTA's partial D_x rows (peers read them once they
-        // have all arrived on this CTA's PFULL)
-        bwait(bar(B_PEMPTY + h), (v & 1) ^ 1, ctl, P);
-        float* prow = (float*)(sm + OFF_P + h * P_BYTES + c * P_ROW);
-        if (c < k) {
-#pragma unroll
-          for (int j = 0; j < NB; j += 4)
-            *reinterpret_cast<float4*>(prow + j) = make_float4(xr[j], xr[j + 1], xr[j + 2], xr[j + 3]);
-        }
         // The CTA barrier orders both warps' writes before one thread's
         // cluster-scope release arrive, which publishes them to the peers.
         named_bar(1, 64);
@@ -591,22 +594,22 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
         // Two-term BF16 split X = X_hi + X_lo (X_hi = BF16(X), X_lo =
         // BF16(X - X_hi)); MMA-Y multiplies A by both, so Y = A (X_hi + X_lo)
         // carries about 16 significant bits of X instead of 8.  X in HBM
-        // holds X_hi + X_lo, the values Y is built from.  Done in two halves
-        // of 32 columns to bound register use.
+        // holds X_hi + X_lo, the values Y is built from.  Done 16 columns at
+        // a time to bound register use.
         bwait(bar(B_XBEMPTY + h), (v & 1) ^ 1, ctl, P);
         if (c < k) {
           const uint32_t src = smem_u32(prow);
           float* Xm = P.X + md.offX;
+#pragma unroll 1
+          for (int qb = 0; qb < 4; ++qb) {
+            float acc[16];
 #pragma unroll
-          for (int hb = 0; hb < 2; ++hb) {
-            float acc[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+            for (int j = 0; j < 16; ++j) acc[j] = 0.f;
 #pragma unroll
             for (int r = 0; r < C; ++r) {
-              const uint32_t ra = mapa(src + hb * 128, r);
+              const uint32_t ra = mapa(src + qb * 64, r);
 #pragma unroll
-              for (int j = 0; j < 32; j += 4) {
+              for (int j = 0; j < 16; j += 4) {
                 float a0, a1, a2, a3;
                 ld_cluster_v4(ra + j * 4, a0, a1, a2, a3);
                 acc[j] += a0;
@@ -615,9 +618,9 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
                 acc[j + 3] += a3;
               }
             }
-            uint32_t phi[16], plo[16];
+            uint32_t phi[8], plo[8];
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
+            for (int j = 0; j < 16; j += 2) {
               const __nv_bfloat16 h0 = __float2bfloat16_rn(acc[j]);
               const __nv_bfloat16 h1 = __float2bfloat16_rn(acc[j + 1]);
               const float f0 = __bfloat162float(h0), f1 = __bfloat162float(h1);
@@ -633,11 +636,11 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
               phi[j / 2] = *reinterpret_cast<const uint32_t*>(&hh);
               plo[j / 2] = *reinterpret_cast<const uint32_t*>(&ll);
             }
-            const long long jb = (long long)q * NB + hb * 32;
+            const long long jb = (long long)q * NB + qb * 16;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {  // this CTA's 64/C columns go to HBM
+            for (int j = 0; j < 16; ++j) {  // this CTA's 64/C columns go to HBM
               const long long jj = jb + j;
-              if ((hb * 32 + j) / WC == (int)rank && jj < n) Xm[jj * P.kp + c] = acc[j];
+              if ((qb * 16 + j) / WC == (int)rank && jj < n) Xm[jj * P.kp + c] = acc[j];
             }
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
@@ -646,8 +649,8 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
               unsigned char* xrow =
                   sm + OFF_XB + h * XB_BYTES + (row >> 3) * 1024 + (row & 7) * 128;
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const int unit = hb * 4 + u;
+              for (int u = 0; u < 2; ++u) {
+                const int unit = qb * 2 + u;
                 *reinterpret_cast<uint4*>(xrow + (((unit ^ (row & 7)) & 7) << 4)) =
                     make_uint4(w[u * 4], w[u * 4 + 1], w[u * 4 + 2], w[u * 4 + 3]);
               }
