@@ -49,49 +49,62 @@ namespace tsk {
 namespace {
 
 constexpr int NB = 64;         // columns of A per block (one 128-byte row)
-constexpr int MC = 512;        // rows of A per CTA
-constexpr int NST = 2;         // A stages
 constexpr int KPAD_MAX = 48;   // largest padded k this kernel takes
-constexpr int NTHREADS = 288;  // 9 warps
+constexpr int NTHREADS = 352;  // 11 warps
 constexpr int BOX_ROWS = 256;  // TMA box height (hardware limit 256)
+constexpr int NST_MAX = 4;     // barrier slots reserved for A stages
 
-constexpr int STAGE_BYTES = MC * 128;
-constexpr int OFF_A = 0;
-constexpr int OFF_S = OFF_A + NST * STAGE_BYTES;
-constexpr int S_BYTES = (MC / 64) * KPAD_MAX * 128;
-constexpr int P_ROW = 272;  // 64 floats + 16 bytes of padding per row
-constexpr int P_BYTES = KPAD_MAX * P_ROW;
+// Receive buffer of the X reduction: the owner of rows [rho*R, rho*R + R) of
+// D_x gets them from every CTA of the cluster, slot by slot (C slots of R
+// rows, C*R = kq <= KPAD_MAX rows in all).
+constexpr int RECV_ROW = 272;  // 64 floats + 16 bytes of padding per row
+constexpr int RECV_BYTES = KPAD_MAX * RECV_ROW;
 constexpr int XB_BYTES = 2 * KPAD_MAX * 128;  // X_hi rows, then X_lo rows
-constexpr int OFF_XB = OFF_S + S_BYTES;
-constexpr int OFF_P = OFF_XB + 2 * XB_BYTES;
-constexpr int OFF_BAR = OFF_P + 2 * P_BYTES;
 constexpr int BAR_BYTES = 256;
-// The kernel declares no static shared variables, so its dynamic shared
-// memory starts on a 1024-byte boundary; the kernel checks this and reports
-// misalignment instead of reserving slack.
-constexpr int SMEM_BYTES = OFF_BAR + BAR_BYTES;
-// MMA-X reads 128 rows of S per 64-row chunk although only kpad rows are
-// real; the extra rows (whose results are never used) must stay inside the
-// allocation: from the last chunk they reach at most 16 KB past its start.
-static_assert(OFF_S + (MC / 64 - 1) * KPAD_MAX * 128 + 128 * 128 <= OFF_BAR,
-              "S over-read leaves the shared-memory allocation");
-static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
-static_assert(OFF_S % 1024 == 0 && OFF_XB % 1024 == 0 && XB_BYTES % 1024 == 0 &&
-                  STAGE_BYTES % 1024 == 0,
-              "swizzled operands need 1024-byte aligned atoms");
-static_assert(OFF_P % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+
+// Shared-memory layout for MC rows of A per CTA.  With MC = 256 a stage is
+// 32 KB and four of them are in flight; with MC = 512 two stages of 64 KB.  The kernel declares no static shared
+// variables, so its dynamic shared memory starts on a 1024-byte boundary; the
+// kernel checks this and reports misalignment instead of reserving slack.
+template <int MC>
+struct Lay {
+  static constexpr int NST = MC == 256 ? 4 : 2;
+  static constexpr int STAGE_BYTES = MC * 128;
+  static constexpr int OFF_A = 0;
+  static constexpr int OFF_S = OFF_A + NST * STAGE_BYTES;
+  static constexpr int S_BYTES = (MC / 64) * KPAD_MAX * 128;
+  static constexpr int OFF_XB = OFF_S + S_BYTES;
+  static constexpr int OFF_RECV = OFF_XB + 2 * XB_BYTES;
+  static constexpr int OFF_BAR = OFF_RECV + 2 * RECV_BYTES;
+  static constexpr int SMEM_BYTES = OFF_BAR + BAR_BYTES;
+  // MMA-X reads 128 rows of S per 64-row chunk although only kpad rows are
+  // real; the extra rows (whose results are never used) must stay inside the
+  // allocation: from the last chunk they reach at most 16 KB past its start.
+  static_assert(OFF_S + (MC / 64 - 1) * KPAD_MAX * 128 + 128 * 128 <= OFF_BAR,
+                "S over-read leaves the shared-memory allocation");
+  static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
+  static_assert(NST <= NST_MAX, "barrier slots");
+  static_assert(OFF_S % 1024 == 0 && OFF_XB % 1024 == 0 && XB_BYTES % 1024 == 0 &&
+                    STAGE_BYTES % 1024 == 0,
+                "swizzled operands need 1024-byte aligned atoms");
+  static_assert(OFF_RECV % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+};
+template struct Lay<256>;
+template struct Lay<512>;
 
 // barrier slots
 enum {
   B_AFULL = 0,
-  B_AEMPTY = B_AFULL + NST,
-  B_XFULL = B_AEMPTY + NST,
+  B_AEMPTY = B_AFULL + NST_MAX,
+  B_XFULL = B_AEMPTY + NST_MAX,
   B_XTEMPTY = B_XFULL + 2,
-  B_PFULL = B_XTEMPTY + 2,
-  B_PEMPTY = B_PFULL + 2,
+  B_RFULL = B_XTEMPTY + 2,
+  B_PEMPTY = B_RFULL + 2,
   B_XBFULL = B_PEMPTY + 2,
   B_XBEMPTY = B_XBFULL + 2,
-  B_YFULL = B_XBEMPTY + 2,
+  B_XREADY = B_XBEMPTY + 2,
+  B_XWDONE = B_XREADY + 2,
+  B_YFULL = B_XWDONE + 2,
   B_YFREE = B_YFULL + 1,
   B_SFULL = B_YFREE + 1,
   B_SEMPTY = B_SFULL + 1,
@@ -113,8 +126,9 @@ struct TcParams {
   double* normA2;
   int* status;
   int kp;          // leading dimension of the X / Y panels
-  int kpad;        // N of MMA-Y: padded k of this launch (16, 32 or 48)
-  int img_rank_bytes;
+  int kpad;        // rows of the S image: k rounded up to 16 (16, 32 or 48)
+  int kq;          // rows of X~_hi (and of X~_lo): k rounded up to 8; N of MMA-Y = 2 kq
+  int img_rank_bytes;  // bytes of S image per CTA: (MC / 64) chunks of kpad rows
   long long timeout_ns;
 };
 
@@ -144,22 +158,21 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar)
                : "memory");
 }
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-  asm volatile(
-      "mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
-      : "memory");
-}
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile(
       "mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
       "r"(bytes)
       : "memory");
 }
+// CTA-scope acquire is enough for every barrier of the kernel: data from
+// other CTAs arrives only by st.async and bulk copies, whose bytes complete
+// on the waiting CTA's own barrier (as TMA loads do), and the remaining
+// remote arrives only announce that a buffer has been read.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
       : "r"(bar), "r"(parity)
@@ -175,9 +188,6 @@ __device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
 // (tensor-core) reads of the same memory.
 __device__ __forceinline__ void fence_proxy_async_cta() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void named_bar(int id, int n) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
@@ -198,12 +208,34 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src,
       ::"r"(dst), "l"((uint64_t)src), "r"(bytes), "r"(bar)
       : "memory");
 }
-__device__ __forceinline__ void ld_cluster_v4(uint32_t addr, float& a, float& b,
-                                              float& c, float& d) {
-  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(a), "=f"(b), "=f"(c), "=f"(d)
-               : "r"(addr)
+// Asynchronous store of 16 bytes to the shared memory of a CTA of the
+// cluster; on landing it counts its bytes on that CTA's mbarrier `bar`
+// (addr, bar: mapa addresses).  No thread-side fence is involved.
+__device__ __forceinline__ void st_async_v4(uint32_t addr, float a, float b, float c, float d,
+                                            uint32_t bar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, "
+      "[%5];" ::"r"(addr),
+      "f"(a), "f"(b), "f"(c), "f"(d), "r"(bar)
+      : "memory");
+}
+// Arrive on a (possibly remote) mbarrier without release semantics: used
+// only to say "I have finished reading that buffer", where the reads are
+// complete (their values consumed) before the arrive is issued.
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(
+                   cluster_addr)
                : "memory");
+}
+// Bulk copy from this CTA's shared memory to a peer's (dst, bar: mapa
+// addresses); completion is counted in bytes on the peer's mbarrier.
+__device__ __forceinline__ void bulk_s2c(uint32_t dst, uint32_t src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], "
+      "%2, [%3];" ::"r"(dst),
+      "r"(src), "r"(bytes), "r"(bar)
+      : "memory");
 }
 // tcgen05
 __device__ __forceinline__ void tc_fence_before() {
@@ -226,8 +258,27 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
           bar)
       : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// Arrives, once the issuing thread's tcgen05 operations have completed, on
+// the mbarrier at the same shared-memory offset in every CTA of `mask`.
+__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster."
+      "b64 [%0], %1;" ::"r"(bar),
+      "h"(mask)
+      : "memory");
+}
+// TMEM loads write their registers asynchronously: the values may be used
+// only after tcgen05.wait::ld.  tmem_regs8 (an empty asm that claims to
+// modify the registers), placed after the wait, keeps the compiler from
+// touching them earlier.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+        "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, "
       "%9, %10, %11, %12, %13, %14, %15}, [%16];"
@@ -235,11 +286,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
         "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
         "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_regs8(uint32_t* r) {
+  asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                    "+r"(r[6]), "+r"(r[7])::"memory");
 }
 
 // Shared-memory matrix descriptor, 128-byte swizzle (SM100 layout).
@@ -302,17 +355,18 @@ __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity,
   }
 }
 
-// Sum of squares of one A stage (MC x 64 BF16), shared by 128 threads
-// (t = 0..127).  Eight independent FP32 accumulators per thread, each summing
-// 32 squares per stage, keep the dependent chains short; stages are summed
-// in FP64.
+// Sum of squares of one A stage (MC x 64 BF16, SB bytes), shared by 128
+// threads (t = 0..127).  Eight independent FP32 accumulators per thread,
+// each summing at most 32 squares per stage, keep the dependent chains
+// short; stages are summed in FP64.
+template <int SB>
 __device__ __forceinline__ double stage_sumsq(const unsigned char* stage, int t) {
   const uint4* st = reinterpret_cast<const uint4*>(stage);
   float a[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) a[i] = 0.f;
 #pragma unroll 4
-  for (int e = t; e < STAGE_BYTES / 16; e += 128) {
+  for (int e = t; e < SB / 16; e += 128) {
     const uint4 w = st[e];
     const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -331,9 +385,13 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-template <int C>
+template <int C, int MC>
 __global__ void __launch_bounds__(NTHREADS, 1)
 sketch_tc_kernel(const __grid_constant__ TcParams P) {
+  using L = Lay<MC>;
+  constexpr int NST = L::NST, STAGE_BYTES = L::STAGE_BYTES;
+  constexpr int OFF_A = L::OFF_A, OFF_S = L::OFF_S, OFF_XB = L::OFF_XB;
+  constexpr int OFF_RECV = L::OFF_RECV, OFF_BAR = L::OFF_BAR;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw;
   const uint32_t sb = smem_u32(sm);  // 1024-aligned shared address
@@ -344,13 +402,14 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t rank = (C > 1) ? cluster_rank() : 0;
   const uint32_t cid = (C > 1) ? cluster_id() : blockIdx.x;
-  const int kpad = P.kpad;
+  const int kpad = P.kpad, kq = P.kq;
+  const int R = kq / C;  // rows of X this CTA reduces (C divides kq: kq % 8 == 0)
   auto bar = [&](int i) -> uint32_t { return sb + OFF_BAR + 8 * i; };
   volatile Ctl* ctl = (volatile Ctl*)(sm + OFF_BAR + 8 * B_COUNT);
   uint32_t* tmem_slot = (uint32_t*)(sm + OFF_BAR + 8 * B_COUNT + 8);
 
   const int w0 = P.work_off[cid], w1 = P.work_off[cid + 1];
-  const uint32_t tmem_cols_needed = 2 * NB + (MC / 128) * 2 * kpad;
+  const uint32_t tmem_cols_needed = 2 * NB + (MC / 128) * 2 * kq;
   const uint32_t tmem_cols = tmem_cols_needed <= 256 ? 256 : 512;
 
   if (tid == 0) {
@@ -361,10 +420,12 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
     for (int h = 0; h < 2; ++h) {
       mbar_init(bar(B_XFULL + h), 1);
       mbar_init(bar(B_XTEMPTY + h), 2);
-      mbar_init(bar(B_PFULL + h), C);
-      mbar_init(bar(B_PEMPTY + h), C);
-      mbar_init(bar(B_XBFULL + h), 1);   // own epilogue built X~ locally
-      mbar_init(bar(B_XBEMPTY + h), 1);  // own MMA-Y finished reading it
+      mbar_init(bar(B_RFULL + h), 1);    // own expect-tx; senders' bytes by st.async
+      mbar_init(bar(B_PEMPTY + h), C);   // every owner consumed this CTA's rows
+      mbar_init(bar(B_XBFULL + h), 1);   // own rows written (+ bytes from peers)
+      mbar_init(bar(B_XBEMPTY + h), C);  // every CTA's MMA-Y finished reading
+      mbar_init(bar(B_XREADY + h), 64);  // own rows of X~ written by the 64 threads
+      mbar_init(bar(B_XWDONE + h), 1);   // X writer has read those rows
     }
     mbar_init(bar(B_YFULL), 1);
     mbar_init(bar(B_YFREE), 4);
@@ -392,7 +453,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc_x = idesc_bf16(128, NB, 0, 1);
-  const uint32_t idesc_y = idesc_bf16(128, 2 * kpad, 0, 0);
+  const uint32_t idesc_y = idesc_bf16(128, 2 * kq, 0, 0);
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -520,11 +581,15 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
               const uint64_t a =
                   sdesc(sb + OFF_A + s * STAGE_BYTES + t * 128 * 128 + kk * 32, 16, 1024);
               const uint64_t b = sdesc(sb + OFF_XB + h * XB_BYTES + kk * 32, 16, 1024);
-              tc_mma(tmem + 2 * NB + t * 2 * kpad, a, b, idesc_y, (q > 0 || kk > 0) ? 1u : 0u);
+              tc_mma(tmem + 2 * NB + t * 2 * kq, a, b, idesc_y, (q > 0 || kk > 0) ? 1u : 0u);
             }
           }
           tc_commit(bar(B_AEMPTY + s));
-          tc_commit(bar(B_XBEMPTY + h));
+          // X~ buffer h is read: every owner may refill its rows here
+          if (C > 1)
+            tc_commit_mc(bar(B_XBEMPTY + h), (uint16_t)((1u << C) - 1));
+          else
+            tc_commit(bar(B_XBEMPTY + h));
           if (q == nblk - 1) tc_commit(bar(B_YFULL));
         }
       }
@@ -539,11 +604,9 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
     const int c = lane_base + lane;  // TMEM lane = row c of D_x / row of D_y tile
     long long g = 0;
     int mi = 0;
-    constexpr int WC = NB / C;  // columns of X this CTA writes to HBM
     for (int wi = w0; wi < w1; ++wi, ++mi) {
       const int d = P.work[wi];
       const MatDev& md = P.mats[d];
-      const int k = md.k;
       const long long n = md.n, m = md.m;
       const int nblk = (int)((n + NB - 1) / NB);
       for (int q = 0; q < nblk; ++q, ++g) {
@@ -551,121 +614,108 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
           const int s = (int)(g % NST);
           const uint32_t u = (uint32_t)(g / NST);
           if (bwait_warp(bar(B_AFULL + s), u & 1, ctl, P))
-            tot += stage_sumsq(sm + OFF_A + s * STAGE_BYTES, tid - 64);
+            tot += stage_sumsq<STAGE_BYTES>(sm + OFF_A + s * STAGE_BYTES, tid - 64);
           __syncwarp();
           if (lane == 0) mbar_arrive(bar(B_AEMPTY + s));
           continue;
         }
         const int h = (int)(g & 1);
         const uint32_t v = (uint32_t)(g >> 1);
-        // publish this CTA's partial D_x rows, 16 columns at a time (peers
-        // read them once they have all arrived on this CTA's PFULL)
-        bwait(bar(B_PEMPTY + h), (v & 1) ^ 1, ctl, P);
-        float* prow = (float*)(sm + OFF_P + h * P_BYTES + c * P_ROW);
+        const int xt = tid - 128;  // 0..63 over the two exchange warps
+        // (a) Send.  Row c of this CTA's partial D_x goes to its owner
+        // c / R, into slot rank of the owner's receive buffer h, straight
+        // from the TMEM registers by asynchronous remote stores that count
+        // their bytes on the owner's RFULL barrier.  After a timeout nothing
+        // new goes to peers.
+        bwait_warp(bar(B_PEMPTY + h), (v & 1) ^ 1, ctl, P);
         if (bwait_warp(bar(B_XFULL + h), v & 1, ctl, P)) {
           tc_fence_after();
-#pragma unroll 1
-          for (int j = 0; j < NB; j += 16) {
-            float xr[16];
-            tmem_ld16(tmem + ((uint32_t)lane_base << 16) + h * NB + j, xr);
-            tmem_wait_ld();
-            if (c < k) {
+          const int own = c / R;
+          const uint32_t owner = (uint32_t)(own < C ? own : 0);
+          const uint32_t dst0 = mapa(
+              sb + OFF_RECV + h * RECV_BYTES + (rank * R + (c - own * R)) * RECV_ROW, owner);
+          const uint32_t rfull = mapa(bar(B_RFULL + h), owner);
+          uint32_t xr[NB];
 #pragma unroll
-              for (int e = 0; e < 16; e += 4)
-                *reinterpret_cast<float4*>(prow + j + e) =
-                    make_float4(xr[e], xr[e + 1], xr[e + 2], xr[e + 3]);
-            }
+          for (int j = 0; j < NB; j += 16)
+            tmem_ld16(tmem + ((uint32_t)lane_base << 16) + h * NB + j, xr + j);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < NB; j += 8) tmem_regs8(xr + j);
+          if (c < kq && !ctl->abort) {
+#pragma unroll
+            for (int e = 0; e < NB; e += 4)
+              st_async_v4(dst0 + e * 4, __uint_as_float(xr[e]), __uint_as_float(xr[e + 1]),
+                          __uint_as_float(xr[e + 2]), __uint_as_float(xr[e + 3]), rfull);
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_XTEMPTY + h));
-        // The CTA barrier orders both warps' writes before one thread's
-        // cluster-scope release arrive, which publishes them to the peers.
-        named_bar(1, 64);
-        if (warp == 4 && lane == 0) {
-          const uint32_t pf = bar(B_PFULL + h);
-#pragma unroll
-          for (int r = 0; r < C; ++r) mbar_arrive_cluster(mapa(pf, r));
-        }
-        bwait(bar(B_PFULL + h), v & 1, ctl, P);
-        // X row c of this block = sum of the C partials (every CTA forms the
-        // whole block itself: one round trip instead of reduce + gather).
-        // Two-term BF16 split X = X_hi + X_lo (X_hi = BF16(X), X_lo =
-        // BF16(X - X_hi)); MMA-Y multiplies A by both, so Y = A (X_hi + X_lo)
-        // carries about 16 significant bits of X instead of 8.  X in HBM
-        // holds X_hi + X_lo, the values Y is built from.  Done 16 columns at
-        // a time to bound register use.
-        bwait(bar(B_XBEMPTY + h), (v & 1) ^ 1, ctl, P);
-        if (c < k) {
-          const uint32_t src = smem_u32(prow);
-          float* Xm = P.X + md.offX;
+        // The owner expects R rows of 256 bytes from each of the C CTAs.
+        if (xt == 63) mbar_expect_tx(bar(B_RFULL + h), (uint32_t)(C * R * 256));
+        // (b) Reduce.  X rows [rank*R, rank*R + R) of this block = sum of the
+        // C slots, eight columns per work item.  Two-term BF16 split X =
+        // X_hi + X_lo (X_hi = BF16(X), X_lo = BF16(X - X_hi)); MMA-Y
+        // multiplies A by both, so Y = A (X_hi + X_lo) carries about 16
+        // significant bits of X instead of 8.  The rows are written only
+        // when every CTA's MMA-Y and this CTA's X writer are done with the
+        // previous contents of buffer h.
+        bwait_warp(bar(B_XBEMPTY + h), (v & 1) ^ 1, ctl, P);
+        bwait_warp(bar(B_XWDONE + h), (v & 1) ^ 1, ctl, P);
+        bwait_warp(bar(B_RFULL + h), v & 1, ctl, P);
+        const unsigned char* rb = sm + OFF_RECV + h * RECV_BYTES;
+        unsigned char* xb = sm + OFF_XB + h * XB_BYTES;
 #pragma unroll 1
-          for (int qb = 0; qb < 4; ++qb) {
-            float acc[16];
+        for (int it = xt; it < R * 8; it += 64) {
+          const int ri = it % R, ob = it / R;  // row, octet of columns
+          const int cr = (int)rank * R + ri;
+          float acc[8];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+          for (int j = 0; j < 8; ++j) acc[j] = 0.f;
 #pragma unroll
-            for (int r = 0; r < C; ++r) {
-              const uint32_t ra = mapa(src + qb * 64, r);
+          for (int sl = 0; sl < C; ++sl) {
+            const float4* src =
+                reinterpret_cast<const float4*>(rb + (sl * R + ri) * RECV_ROW + ob * 32);
+            const float4 w0 = src[0], w1 = src[1];
+            acc[0] += w0.x;
+            acc[1] += w0.y;
+            acc[2] += w0.z;
+            acc[3] += w0.w;
+            acc[4] += w1.x;
+            acc[5] += w1.y;
+            acc[6] += w1.z;
+            acc[7] += w1.w;
+          }
+          uint32_t phi[4], plo[4];
 #pragma unroll
-              for (int j = 0; j < 16; j += 4) {
-                float a0, a1, a2, a3;
-                ld_cluster_v4(ra + j * 4, a0, a1, a2, a3);
-                acc[j] += a0;
-                acc[j + 1] += a1;
-                acc[j + 2] += a2;
-                acc[j + 3] += a3;
-              }
-            }
-            uint32_t phi[8], plo[8];
+          for (int j = 0; j < 8; j += 2) {
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(acc[j]);
+            const __nv_bfloat16 h1 = __float2bfloat16_rn(acc[j + 1]);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(acc[j] - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(acc[j + 1] - __bfloat162float(h1));
+            __nv_bfloat162 hh, ll;
+            hh.x = h0;
+            hh.y = h1;
+            ll.x = l0;
+            ll.y = l1;
+            phi[j / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+            plo[j / 2] = *reinterpret_cast<const uint32_t*>(&ll);
+          }
 #pragma unroll
-            for (int j = 0; j < 16; j += 2) {
-              const __nv_bfloat16 h0 = __float2bfloat16_rn(acc[j]);
-              const __nv_bfloat16 h1 = __float2bfloat16_rn(acc[j + 1]);
-              const float f0 = __bfloat162float(h0), f1 = __bfloat162float(h1);
-              const __nv_bfloat16 l0 = __float2bfloat16_rn(acc[j] - f0);
-              const __nv_bfloat16 l1 = __float2bfloat16_rn(acc[j + 1] - f1);
-              acc[j] = f0 + __bfloat162float(l0);
-              acc[j + 1] = f1 + __bfloat162float(l1);
-              __nv_bfloat162 hh, ll;
-              hh.x = h0;
-              hh.y = h1;
-              ll.x = l0;
-              ll.y = l1;
-              phi[j / 2] = *reinterpret_cast<const uint32_t*>(&hh);
-              plo[j / 2] = *reinterpret_cast<const uint32_t*>(&ll);
-            }
-            const long long jb = (long long)q * NB + qb * 16;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {  // this CTA's 64/C columns go to HBM
-              const long long jj = jb + j;
-              if ((qb * 16 + j) / WC == (int)rank && jj < n) Xm[jj * P.kp + c] = acc[j];
-            }
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-              const int row = c + half * kpad;
-              const uint32_t* w = half ? plo : phi;
-              unsigned char* xrow =
-                  sm + OFF_XB + h * XB_BYTES + (row >> 3) * 1024 + (row & 7) * 128;
-#pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                const int unit = qb * 2 + u;
-                *reinterpret_cast<uint4*>(xrow + (((unit ^ (row & 7)) & 7) << 4)) =
-                    make_uint4(w[u * 4], w[u * 4 + 1], w[u * 4 + 2], w[u * 4 + 3]);
-              }
-            }
+          for (int half = 0; half < 2; ++half) {
+            const int row = cr + half * kq;
+            const uint32_t* w = half ? plo : phi;
+            *reinterpret_cast<uint4*>(xb + (row >> 3) * 1024 + (row & 7) * 128 +
+                                      (((ob ^ (row & 7)) & 7) << 4)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
           }
         }
+        // (c) Hand the owned rows of X~ to the signalling warp, which copies
+        // them to the peers.  The proxy fence makes these generic writes
+        // visible to the bulk copies and to the tensor cores.
         fence_proxy_async_cta();
-        named_bar(1, 64);
-        if (warp == 4 && lane == 0) {
-          // peers' partials are consumed: they may reuse their P buffers
-          const uint32_t pe = bar(B_PEMPTY + h);
-#pragma unroll
-          for (int r = 0; r < C; ++r) mbar_arrive_cluster(mapa(pe, r));
-        }
-        if (warp == 4 && lane == 0) mbar_arrive(bar(B_XBFULL + h));
+        mbar_arrive(bar(B_XREADY + h));
       }
       if (!xwarp) {
         tot = warp_sum(tot);
@@ -680,18 +730,21 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
         for (int t = 0; t < MC / 128; ++t) {
           const long long row = (long long)rank * MC + t * 128 + lane_base + lane;
 #pragma unroll 1
-          for (int j = 0; j < kpad; j += 16) {
-            float yv[16], yl[16];
-            const uint32_t col = tmem + ((uint32_t)lane_base << 16) + 2 * NB + t * 2 * kpad + j;
-            tmem_ld16(col, yv);
-            tmem_ld16(col + kpad, yl);
+          for (int j = 0; j < kq; j += 8) {
+            uint32_t yv[8], yl[8];
+            const uint32_t col = tmem + ((uint32_t)lane_base << 16) + 2 * NB + t * 2 * kq + j;
+            tmem_ld8(col, yv);
+            tmem_ld8(col + kq, yl);
             tmem_wait_ld();
+            tmem_regs8(yv);
+            tmem_regs8(yl);
             if (row < m) {
               float4* dst = reinterpret_cast<float4*>(Ym + row * P.kp + j);
+              float y[8];
 #pragma unroll
-              for (int e = 0; e < 4; ++e)
-                dst[e] = make_float4(yv[4 * e] + yl[4 * e], yv[4 * e + 1] + yl[4 * e + 1],
-                                     yv[4 * e + 2] + yl[4 * e + 2], yv[4 * e + 3] + yl[4 * e + 3]);
+              for (int e = 0; e < 8; ++e) y[e] = __uint_as_float(yv[e]) + __uint_as_float(yl[e]);
+              dst[0] = make_float4(y[0], y[1], y[2], y[3]);
+              dst[1] = make_float4(y[4], y[5], y[6], y[7]);
             }
           }
         }
@@ -700,13 +753,95 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_YFREE));
     }
-    // Peers read this CTA's partials until they arrive on PEMPTY: wait for
-    // the last phase of each buffer before leaving.
-    if (xwarp && g > 0) {
+    // Owners arrive on PEMPTY and every CTA's MMA-Y on XBEMPTY after this
+    // CTA's last use of a buffer: wait for those final phases, so that no
+    // remote arrive is still in flight toward this CTA when it leaves.
+    if (xwarp && lane == 0 && g > 0) {
       for (int h = 0; h < 2; ++h) {
         if (g > h) {
           const long long last = ((g - 1 - h) / 2) * 2 + h;
           drain_wait(bar(B_PEMPTY + h), (uint32_t)((last >> 1) & 1), P);
+          drain_wait(bar(B_XBEMPTY + h), (uint32_t)((last >> 1) & 1), P);
+        }
+      }
+    }
+  } else if (warp == 10) {
+    // ------------------------------------------------------ X writer
+    // X in HBM holds X_hi + X_lo, the values Y is built from: once the owned
+    // rows of X~ of a block are written (XREADY), this warp reads them back
+    // and stores X rows [rank*R, rank*R + R) (rows < k) of the block's
+    // columns, keeping global stores off the exchange warps.
+    // Element e = lane + 32 t of a block is (column j, row ri) = (e / R,
+    // e % R): consecutive lanes write consecutive rows of one column of X.
+    // The pair advances by (32 / R, 32 % R) per step, so no division is
+    // needed inside the loop.
+    const int dj = 32 / R, dr = 32 % R;
+    const int j0 = lane / R, r0 = lane % R;
+    long long g = 0;
+    for (int wi = w0; wi < w1; ++wi) {
+      const MatDev& md = P.mats[P.work[wi]];
+      const long long n = md.n;
+      const int k = md.k;
+      float* Xm = P.X + md.offX;
+      const int nblk = (int)((n + NB - 1) / NB);
+      for (int q = 0; q < nblk; ++q, ++g) {
+        const int h = (int)(g & 1);
+        const uint32_t v = (uint32_t)(g >> 1);
+        if (bwait_warp(bar(B_XREADY + h), v & 1, ctl, P)) {
+          const unsigned char* xb = sm + OFF_XB + h * XB_BYTES;
+          const long long jb = (long long)q * NB;
+          const int jmax = (int)min((long long)NB, n - jb);
+          int j = j0, ri = r0;
+#pragma unroll 4
+          for (int e = lane; e < R * NB; e += 32) {
+            const int cr = (int)rank * R + ri;
+            if (cr < k && j < jmax) {
+              const int rl = cr + kq, un = j >> 3, w = (j & 7) * 2;
+              const __nv_bfloat16 vh = *reinterpret_cast<const __nv_bfloat16*>(
+                  xb + (cr >> 3) * 1024 + (cr & 7) * 128 + (((un ^ (cr & 7)) & 7) << 4) + w);
+              const __nv_bfloat16 vl = *reinterpret_cast<const __nv_bfloat16*>(
+                  xb + (rl >> 3) * 1024 + (rl & 7) * 128 + (((un ^ (rl & 7)) & 7) << 4) + w);
+              Xm[(jb + j) * P.kp + cr] = __bfloat162float(vh) + __bfloat162float(vl);
+            }
+            j += dj;
+            ri += dr;
+            if (ri >= R) {
+              ri -= R;
+              ++j;
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_XWDONE + h));
+      }
+    }
+  } else if (warp == 9) {
+    // ---------------------------------------- signalling (lanes 0..C-1)
+    // Once the owned rows of X~ are written (XREADY), lane r copies them
+    // into peer r's X~ buffer (bulk copy; bytes complete on the peer's
+    // XBFULL) or, for r == rank, announces the bytes the C - 1 peers will
+    // send; then it tells CTA r that its slot of this CTA's receive buffer
+    // is free again.  Remote operations can hold the issuing thread for a
+    // microsecond or more, so they run here and not in the exchange warps.
+    if (lane < C) {
+      const uint32_t peer = (uint32_t)lane;
+      long long g = 0;
+      for (int wi = w0; wi < w1; ++wi) {
+        const int nblk = (int)((P.mats[P.work[wi]].n + NB - 1) / NB);
+        for (int q = 0; q < nblk; ++q, ++g) {
+          const int h = (int)(g & 1);
+          const uint32_t v = (uint32_t)(g >> 1);
+          if (!bwait(bar(B_XREADY + h), v & 1, ctl, P)) continue;
+          const uint32_t xs = sb + OFF_XB + h * XB_BYTES;
+          const uint32_t xf = bar(B_XBFULL + h);
+          if (peer != rank) {
+            const uint32_t hi = xs + rank * R * 128, lo = xs + (kq + rank * R) * 128;
+            bulk_s2c(mapa(hi, peer), hi, R * 128, mapa(xf, peer));
+            bulk_s2c(mapa(lo, peer), lo, R * 128, mapa(xf, peer));
+          } else {
+            mbar_expect_tx(xf, (uint32_t)((C - 1) * 2 * R * 128));
+          }
+          mbar_arrive_cluster_relaxed(mapa(bar(B_PEMPTY + h), peer));
         }
       }
     }
@@ -722,7 +857,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
         const int s = (int)(g % NST);
         const uint32_t u = (uint32_t)(g / NST);
         if (bwait_warp(bar(B_AFULL + s), u & 1, ctl, P))
-          tot += stage_sumsq(sm + OFF_A + s * STAGE_BYTES, tid - 128);
+          tot += stage_sumsq<STAGE_BYTES>(sm + OFF_A + s * STAGE_BYTES, tid - 128);
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_AEMPTY + s));
       }
@@ -734,7 +869,18 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
   // ---- teardown: nobody leaves while a peer may still touch its memory
   tc_fence_before();
   __syncthreads();
-  if (C > 1) cluster_sync();
+  if (C > 1) {
+    cluster_sync();
+    // After a timeout the waits above were cut short, so stores, copies or
+    // arrives that peers issued before the cluster barrier may still be
+    // landing here: give them time (they take microseconds) before leaving.
+    if (ctl->abort && tid == 0) {
+      const uint64_t t0 = globaltimer();
+      while (globaltimer() - t0 < 200000ull) {
+      }
+    }
+    __syncthreads();
+  }
   tc_fence_after();
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -743,40 +889,40 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
   }
 }
 
-// Pre-swizzled BF16 image of S for every (distinct sketch, cluster rank):
-// the exact shared-memory layout the MMA-X A operand reads (K-major,
-// 128-byte swizzle, one 64-column chunk of k_pad rows after another).
+// Pre-swizzled BF16 image of every distinct sketch S: the exact
+// shared-memory layout the MMA-X A operand reads (K-major, 128-byte swizzle),
+// one 64-row chunk of S^T (kpad rows of 128 bytes) after another.  The
+// image of cluster rank rho is the contiguous run of chunks covering rows
+// [rho*MC, rho*MC + MC), so one image serves every cluster size.
 struct SImgDesc {
   const float* S;
   long long m;
   int k;
-  int pad;
+  int nchunks;  // 64-row chunks in this image (covers C * MC rows)
   long long off;
 };
 
 __global__ void simg_prep_kernel(const SImgDesc* __restrict__ descs, int kpad,
-                                 int img_rank_bytes, unsigned char* __restrict__ simg) {
+                                 unsigned char* __restrict__ simg) {
   const SImgDesc sd = descs[blockIdx.x];
-  const int rank = blockIdx.y;
-  unsigned char* img = simg + sd.off + (long long)rank * img_rank_bytes;
-  const int nunits = (MC / 64) * kpad * 8;
-  for (int e = threadIdx.x; e < nunits; e += blockDim.x) {
-    const int qc = e / (kpad * 8);
-    const int rem = e % (kpad * 8);
-    const int c = rem / 8, u = rem % 8;
+  const int qc = blockIdx.y;  // chunk
+  if (qc >= sd.nchunks) return;
+  unsigned char* img = simg + sd.off + (long long)qc * kpad * 128;
+  for (int e = threadIdx.x; e < kpad * 8; e += blockDim.x) {
+    const int c = e / 8, u = e % 8;
     uint32_t w[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       float v2[2];
 #pragma unroll
       for (int z = 0; z < 2; ++z) {
-        const long long i = (long long)rank * MC + qc * 64 + u * 8 + 2 * t + z;
+        const long long i = (long long)qc * 64 + u * 8 + 2 * t + z;
         v2[z] = (c < sd.k && i < sd.m) ? sd.S[(long long)c * sd.m + i] : 0.f;
       }
       w[t] = pack_bf16x2(v2[0], v2[1]);
     }
-    uint4* dst = reinterpret_cast<uint4*>(img + qc * kpad * 128 + (c >> 3) * 1024 +
-                                          (c & 7) * 128 + (((u ^ (c & 7)) & 7) << 4));
+    uint4* dst = reinterpret_cast<uint4*>(img + (c >> 3) * 1024 + (c & 7) * 128 +
+                                          (((u ^ (c & 7)) & 7) << 4));
     *dst = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
@@ -794,21 +940,21 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-template <int C>
+template <int C, int MC>
 cudaError_t set_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(sketch_tc_kernel<C>,
+  cudaError_t e = cudaFuncSetAttribute(sketch_tc_kernel<C, MC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       SMEM_BYTES);
+                                       Lay<MC>::SMEM_BYTES);
   return e;
 }
 
-template <int C>
+template <int C, int MC>
 int max_clusters() {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   cfg.gridDim = dim3(C * 256, 1, 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.dynamicSmemBytes = Lay<MC>::SMEM_BYTES;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = C;
   attr[0].val.clusterDim.y = 1;
@@ -816,7 +962,8 @@ int max_clusters() {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, sketch_tc_kernel<C>, &cfg) != cudaSuccess || n < 1) {
+  if (cudaOccupancyMaxActiveClusters(&n, sketch_tc_kernel<C, MC>, &cfg) != cudaSuccess ||
+      n < 1) {
     cudaGetLastError();
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -826,13 +973,13 @@ int max_clusters() {
   return n;
 }
 
-template <int C>
+template <int C, int MC>
 cudaError_t launch_class(const TcParams& prm, int nclusters, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   cfg.gridDim = dim3(C * nclusters, 1, 1);
   cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.dynamicSmemBytes = Lay<MC>::SMEM_BYTES;
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = C;
@@ -840,13 +987,52 @@ cudaError_t launch_class(const TcParams& prm, int nclusters, cudaStream_t s) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, sketch_tc_kernel<C>, prm);
+  return cudaLaunchKernelEx(&cfg, sketch_tc_kernel<C, MC>, prm);
+}
+
+// Cluster shape for an m-row matrix: MC rows per CTA and C CTAs, C the
+// smallest power of two with C * MC >= m.  The X exchange costs about the
+// same per column block whatever MC is, so 512 rows per CTA (two 64 KB
+// stages) beat 256 rows (four 32 KB stages) once a cluster is needed; a
+// matrix of at most 256 rows takes one CTA with four stages.
+void cluster_shape(long long m, int* C, int* MC) {
+  *MC = m <= 256 ? 256 : 512;
+  int c = 1;
+  while ((long long)c * *MC < m) c *= 2;
+  *C = c;
+}
+
+// The instantiated (C, MC) pairs, in one place for attributes and launches.
+cudaError_t class_attrs(int C, int MC, int* ncl) {
+  cudaError_t e = cudaErrorInvalidValue;
+#define TSK_TC_CASE(c_, mc_)                 \
+  if (C == c_ && MC == mc_) {                \
+    e = set_attrs<c_, mc_>();                \
+    if (e == cudaSuccess) *ncl = max_clusters<c_, mc_>(); \
+  }
+  TSK_TC_CASE(1, 256)
+  TSK_TC_CASE(1, 512)
+  TSK_TC_CASE(2, 512)
+  TSK_TC_CASE(4, 512)
+  TSK_TC_CASE(8, 512)
+#undef TSK_TC_CASE
+  return e;
+}
+
+cudaError_t class_launch(int C, int MC, const TcParams& prm, int nclusters, cudaStream_t s) {
+  if (C == 1 && MC == 256) return launch_class<1, 256>(prm, nclusters, s);
+  if (C == 1 && MC == 512) return launch_class<1, 512>(prm, nclusters, s);
+  if (C == 2 && MC == 512) return launch_class<2, 512>(prm, nclusters, s);
+  if (C == 4 && MC == 512) return launch_class<4, 512>(prm, nclusters, s);
+  if (C == 8 && MC == 512) return launch_class<8, 512>(prm, nclusters, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
 struct TcClass {
   int C;
+  int MC;
   int nclusters;
   TcParams prm;
 };
@@ -858,8 +1044,8 @@ struct TcPlan {
   const SImgDesc* d_sdesc = nullptr;
   int nsdesc = 0;
   int kpad = 16;
-  int img_rank_bytes = 0;
-  int cmax = 1;
+  int kq = 8;
+  int max_chunks = 1;
   unsigned char* simg = nullptr;
 };
 
@@ -884,19 +1070,18 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
   int kmax = 1;
   for (int i = 0; i < count; ++i) {
     if (hm[i].k > KPAD_MAX) return fail("k > 48 is not supported by the tensor-core kernel");
-    if (hm[i].m > 8LL * MC) return fail("m > 4096 is not supported by the tensor-core kernel");
+    if (hm[i].m > 4096) return fail("m > 4096 is not supported by the tensor-core kernel");
     kmax = std::max(kmax, hm[i].k);
   }
   TcPlan* p = new TcPlan();
   p->kpad = ((kmax + 15) / 16) * 16;
-  p->img_rank_bytes = (MC / 64) * p->kpad * 128;
-  // classes by cluster size
-  std::map<int, std::vector<int>> byC;
+  p->kq = ((kmax + 7) / 8) * 8;
+  // classes by cluster shape (C, MC)
+  std::map<std::pair<int, int>, std::vector<int>> byC;
   for (int i = 0; i < count; ++i) {
-    const long long m = hm[i].m;
-    const int C = m <= MC ? 1 : (m <= 2 * MC ? 2 : (m <= 4 * MC ? 4 : 8));
-    byC[C].push_back(i);
-    p->cmax = std::max(p->cmax, C);
+    int C, mc;
+    cluster_shape(hm[i].m, &C, &mc);
+    byC[std::make_pair(C, mc)].push_back(i);
   }
   // distinct sketch images
   std::map<std::tuple<const void*, long long, int>, long long> img_of;
@@ -907,14 +1092,16 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
     auto key = std::make_tuple(hm[i].S, hm[i].m, hm[i].k);
     auto it = img_of.find(key);
     if (it == img_of.end()) {
-      const int C = hm[i].m <= MC ? 1 : (hm[i].m <= 2 * MC ? 2 : (hm[i].m <= 4 * MC ? 4 : 8));
+      int C, mc;
+      cluster_shape(hm[i].m, &C, &mc);
       SImgDesc sd;
       sd.S = (const float*)hm[i].S;
       sd.m = hm[i].m;
       sd.k = hm[i].k;
-      sd.pad = C;
+      sd.nchunks = C * mc / 64;
       sd.off = img_total;
-      img_total += (long long)p->cmax * p->img_rank_bytes;
+      p->max_chunks = std::max(p->max_chunks, sd.nchunks);
+      img_total += (long long)sd.nchunks * p->kpad * 128;
       it = img_of.emplace(key, sd.off).first;
       sdesc.push_back(sd);
     }
@@ -923,21 +1110,15 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
   // schedules: longest-processing-time-first over clusters of each class
   std::vector<int> work, work_off_all;
   struct ClassTmp {
-    int C, ncl;
+    int C, MC, ncl;
     size_t woff_start, work_start;
   };
   std::vector<ClassTmp> ctmp;
   for (auto& kv : byC) {
-    const int C = kv.first;
+    const int C = kv.first.first, MCc = kv.first.second;
     std::vector<int> ids = kv.second;
     int ncl = 1;
-    cudaError_t ae = cudaSuccess;
-    switch (C) {
-      case 1: ae = set_attrs<1>(); if (ae == cudaSuccess) ncl = max_clusters<1>(); break;
-      case 2: ae = set_attrs<2>(); if (ae == cudaSuccess) ncl = max_clusters<2>(); break;
-      case 4: ae = set_attrs<4>(); if (ae == cudaSuccess) ncl = max_clusters<4>(); break;
-      default: ae = set_attrs<8>(); if (ae == cudaSuccess) ncl = max_clusters<8>(); break;
-    }
+    const cudaError_t ae = class_attrs(C, MCc, &ncl);
     if (ae != cudaSuccess) {
       int dev = 0, optin = 0;
       cudaGetDevice(&dev);
@@ -946,7 +1127,8 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
         snprintf(msg, msglen,
                  "cudaFuncSetAttribute(%d bytes of shared memory) failed: %s (device opt-in "
                  "limit %d bytes)",
-                 SMEM_BYTES, cudaGetErrorString(ae), optin);
+                 MCc == 256 ? Lay<256>::SMEM_BYTES : Lay<512>::SMEM_BYTES,
+                 cudaGetErrorString(ae), optin);
       cudaGetLastError();
       delete p;
       return ae;
@@ -964,6 +1146,7 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
     }
     ClassTmp ct;
     ct.C = C;
+    ct.MC = MCc;
     ct.ncl = ncl;
     ct.woff_start = work_off_all.size();
     ct.work_start = work.size();
@@ -1032,6 +1215,7 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
   for (const ClassTmp& ct : ctmp) {
     TcClass cl;
     cl.C = ct.C;
+    cl.MC = ct.MC;
     cl.nclusters = ct.ncl;
     TcParams& prm = cl.prm;
     prm.mats = d_mats;
@@ -1046,7 +1230,8 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
     prm.status = status;
     prm.kp = kp;
     prm.kpad = p->kpad;
-    prm.img_rank_bytes = p->img_rank_bytes;
+    prm.kq = p->kq;
+    prm.img_rank_bytes = (ct.MC / 64) * p->kpad * 128;
     prm.timeout_ns = timeout_ns;
     p->classes.push_back(cl);
   }
@@ -1056,17 +1241,12 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
 
 cudaError_t tc_launch(TcPlan* p, cudaStream_t s) {
   if (!p) return cudaErrorInvalidValue;
-  simg_prep_kernel<<<dim3(p->nsdesc, p->cmax), 256, 0, s>>>(p->d_sdesc, p->kpad,
-                                                             p->img_rank_bytes, p->simg);
+  simg_prep_kernel<<<dim3(p->nsdesc, p->max_chunks), 256, 0, s>>>(p->d_sdesc, p->kpad,
+                                                                    p->simg);
   cudaError_t e = cudaGetLastError();
   for (const TcClass& cl : p->classes) {
     if (e != cudaSuccess) break;
-    switch (cl.C) {
-      case 1: e = launch_class<1>(cl.prm, cl.nclusters, s); break;
-      case 2: e = launch_class<2>(cl.prm, cl.nclusters, s); break;
-      case 4: e = launch_class<4>(cl.prm, cl.nclusters, s); break;
-      default: e = launch_class<8>(cl.prm, cl.nclusters, s); break;
-    }
+    e = class_launch(cl.C, cl.MC, cl.prm, cl.nclusters, s);
   }
   return e;
 }

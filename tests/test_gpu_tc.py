@@ -64,10 +64,10 @@ def test_tc_small_single_cta(tsk):
 
 
 @pytest.mark.parametrize("m,n,k,r", [
-    (512, 200, 20, 10),     # C = 1, ragged n
-    (1000, 448, 40, 20),    # C = 2, ragged m
-    (2048, 576, 40, 20),    # C = 4
-    (3000, 136, 10, 5),     # C = 8, ragged m and n
+    (512, 200, 20, 10),     # 1 CTA of 512 rows, ragged n
+    (1000, 448, 40, 20),    # 2 CTAs of 512 rows, ragged m
+    (2048, 576, 40, 20),    # 4 CTAs of 512 rows
+    (3000, 136, 10, 5),     # 8 CTAs of 512 rows, ragged m and n
     (300, 72, 48, 24),      # k = 48 (largest the kernel takes)
 ])
 def test_tc_matches_oracle(tsk, m, n, k, r):
