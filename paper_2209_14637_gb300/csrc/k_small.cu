@@ -14,6 +14,8 @@
 #include <cuda_bf16.h>
 #include <float.h>
 
+#include <algorithm>
+
 #include "tsk_internal.cuh"
 
 namespace tsk {
@@ -432,97 +434,154 @@ cudaError_t launch_sym_eig(bool dbl, const void* H, int p, void* theta,
 //
 // Y itself is not factored: its columns grow like sigma_i^2 and Y^T Y would
 // lose everything in FP32.  Partial Gram matrices are summed in FP32 over
-// chunks of 256 rows and in FP64 across chunks; the k x k Cholesky and
-// inverse run in FP64; the captured energy sum_{i<=r} v_i^T (M^T M) v_i is
-// formed in FP64 from the FP32 eigenvectors.
+// blocks of 64 rows, compensated (Kahan) across the blocks of a chunk of up
+// to 1024 rows, and across chunks in FP64 (Cholesky) or FP32 (eigenpairs);
+// the k x k Cholesky, its inverse and the eigenpairs run in FP32; the
+// captured energy sum_{i<=r} v_i^T (M^T M) v_i is summed in FP64 from FP32
+// products.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int GCHUNK = 256;  // rows per partial Gram
-constexpr int GSUB = 64;     // rows staged in shared memory at a time
+constexpr int GCHUNK = 1024;  // rows per partial Gram
+constexpr int GSUB = 64;      // rows staged in shared memory at a time
+constexpr int GTHREADS = 256;
 }  // namespace
 
-// One CTA per (panel, chunk): partial G = P_c^T P_c over the chunk's rows,
-// where P_c = P or P R^{-1} (Rinv: kp x kp FP32, upper, per panel).  Only the
-// upper triangle is formed: the 4x4 tiles with tile-row <= tile-column are
-// spread over the threads, and when there are fewer tiles than threads,
-// several row groups share the rows of each staged block and are summed at
-// the end.  Entries below the diagonal of the partial are left unwritten.
-__global__ void __launch_bounds__(256)
+// Shared memory of panel_gram_kernel: the staged rows (transposed, kp x
+// (GSUB + 1), when a transform follows; else row-major GSUB x (kp + 4)), the
+// transformed rows (GSUB x (kp + 4)) and R^{-1} (kp x kp); at the end the
+// same space holds the row groups' tiles (at most GTHREADS x 16 floats).
+size_t panel_gram_smem(int kp) {
+  const size_t a = (size_t)kp * (GSUB + 1), b = (size_t)GSUB * (kp + 4);
+  return std::max(std::max(a, b) + b + (size_t)kp * kp, (size_t)GTHREADS * 16) * sizeof(float);
+}
+
+// One CTA per (panel, chunk of GCHUNK rows): partial G = P_c^T P_c over the
+// chunk's rows, where P_c = P or P R^{-1} (Rinv: kp x kp FP32, upper, per
+// panel).  The rows stream through shared memory GSUB at a time; the next
+// block is loaded into registers while the current one is processed.  The
+// transform gives each thread a 4 x 4 tile of P R^{-1} (4 rows of the staged
+// block, stored transposed, times 4 columns of R^{-1}); the Gram gives each
+// thread a 4 x 4 tile of the upper triangle, several row groups per tile
+// when there are fewer tiles than threads.  Each block's FP32 sums are added
+// into a compensated (Kahan) FP32 accumulator, so the chunk's error stays
+// near that of one block.  Entries below the diagonal of the partial are
+// left unwritten.
+__global__ void __launch_bounds__(GTHREADS)
 panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __restrict__ chunks,
                   const float* __restrict__ rinv, float* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int2 ch = chunks[blockIdx.x];
   const PanelDev pd = panels[ch.x];
   const int k = pd.k, ld = pd.ld;
-  const int ldp = kp + 4;              // 16-byte aligned rows
-  float* Ps = (float*)smem_raw;        // GSUB x ldp
-  float* Ts = Ps + GSUB * ldp;         // GSUB x ldp transformed rows
-  float* Rs = Ts + GSUB * ldp;         // kp x kp
-  float* Red = Rs + kp * kp;           // 256 x 16 partial tiles of the row groups
-  const float* P = (const float*)pd.P;
   const bool tr = (rinv != nullptr);
+  const int ldt = GSUB + 1, ldp = kp + 4;
+  float* Ps = (float*)smem_raw;  // staged rows: transposed (tr) or row-major
+  float* Ts = Ps + max(kp * ldt, GSUB * ldp);
+  float* Rs = Ts + GSUB * ldp;
+  const float* P = (const float*)pd.P;
+  const int tid = threadIdx.x;
   if (tr) {
     const float* R = rinv + (long long)ch.x * kp * kp;
-    for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) Rs[e] = R[e];
+    for (int e = tid; e < kp * kp; e += GTHREADS) Rs[e] = R[e];
   }
   const int nt = kp / 4;
   const int ntiles = nt * (nt + 1) / 2;
-  const int groups = max(1, (int)blockDim.x / ntiles);
-  const int tid = threadIdx.x;
+  const int groups = max(1, GTHREADS / ntiles);
   const bool active = tid < groups * ntiles;
   const int tile = tid % ntiles, grp = tid / ntiles;
-  // tile -> (ty, tx) with ty <= tx
-  int ty = 0, rem = tile;
+  int ty = 0, rem = tile;  // tile -> (ty, tx) with ty <= tx
   while (rem >= nt - ty) {
     rem -= nt - ty;
     ++ty;
   }
   const int tx = ty + rem;
-  float acc[4][4];
+  // transform tile of this thread: rows 4 rg .. 4 rg + 3, columns 4 cg .. 4 cg + 3
+  const int rg = tid / nt, cg = tid % nt;
+  const bool tact = tr && rg < GSUB / 4;
+  float hi[4][4], lo[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int b2 = 0; b2 < 4; ++b2) hi[a][b2] = lo[a][b2] = 0.f;
   const long long r0 = (long long)ch.y * GCHUNK;
   const long long r1 = min(pd.rows, r0 + GCHUNK);
   const int q4 = kp / 4;  // float4 per row
-  for (long long s0 = r0; s0 < r1; s0 += GSUB) {
-    __syncthreads();
-    for (int e = tid; e < GSUB * q4; e += blockDim.x) {
-      const int ii = e / q4, c4 = (e % q4) * 4;
-      const long long i = s0 + ii;
+  constexpr int PER = (GSUB * (TSK_MAX_K / 4) + GTHREADS - 1) / GTHREADS;  // float4 per thread
+  float4 pre[PER];
+  auto fetch = [&](long long s0) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + u * GTHREADS;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (i < r1) {
-        v = *reinterpret_cast<const float4*>(P + i * ld + c4);
-        if (c4 + 0 >= k) v.x = 0.f;
-        if (c4 + 1 >= k) v.y = 0.f;
-        if (c4 + 2 >= k) v.z = 0.f;
-        if (c4 + 3 >= k) v.w = 0.f;
+      if (e < GSUB * q4) {
+        const int ii = e / q4, c4 = (e % q4) * 4;
+        const long long i = s0 + ii;
+        if (i < r1) {
+          v = *reinterpret_cast<const float4*>(P + i * ld + c4);
+          if (c4 + 0 >= k) v.x = 0.f;
+          if (c4 + 1 >= k) v.y = 0.f;
+          if (c4 + 2 >= k) v.z = 0.f;
+          if (c4 + 3 >= k) v.w = 0.f;
+        }
       }
-      *reinterpret_cast<float4*>(Ps + ii * ldp + c4) = v;
+      pre[u] = v;
+    }
+  };
+  fetch(r0);
+  for (long long s0 = r0; s0 < r1; s0 += GSUB) {
+    __syncthreads();  // the previous block is fully consumed
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + u * GTHREADS;
+      if (e < GSUB * q4) {
+        const int ii = e / q4, c4 = (e % q4) * 4;
+        const float4 v = pre[u];
+        if (tr) {
+          Ps[(c4 + 0) * ldt + ii] = v.x;
+          Ps[(c4 + 1) * ldt + ii] = v.y;
+          Ps[(c4 + 2) * ldt + ii] = v.z;
+          Ps[(c4 + 3) * ldt + ii] = v.w;
+        } else {
+          *reinterpret_cast<float4*>(Ps + ii * ldp + c4) = v;
+        }
+      }
     }
     __syncthreads();
+    if (s0 + GSUB < r1) fetch(s0 + GSUB);  // overlaps the work below
     const float* src = Ps;
     if (tr) {
-      // Ts = Ps Rinv (Rinv upper triangular), four columns per work item
-      for (int e = tid; e < GSUB * q4; e += blockDim.x) {
-        const int ii = e / q4, c4 = (e % q4) * 4;
-        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int top = min(k, c4 + 4);
+      // Ts = Ps R^{-1}: R^{-1} is upper, so column c needs rows cc <= c of it
+      if (tact) {
+        float t[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b2 = 0; b2 < 4; ++b2) t[a][b2] = 0.f;
+        const int top = min(k, 4 * cg + 4);
         for (int cc = 0; cc < top; ++cc) {
-          const float p = Ps[ii * ldp + cc];
-          const float4 r = *reinterpret_cast<const float4*>(Rs + cc * kp + c4);
-          t.x = fmaf(p, r.x, t.x);
-          t.y = fmaf(p, r.y, t.y);
-          t.z = fmaf(p, r.z, t.z);
-          t.w = fmaf(p, r.w, t.w);
+          const float* pc = Ps + cc * ldt + 4 * rg;
+          const float pv[4] = {pc[0], pc[1], pc[2], pc[3]};
+          const float4 rr = *reinterpret_cast<const float4*>(Rs + cc * kp + 4 * cg);
+          const float rv[4] = {rr.x, rr.y, rr.z, rr.w};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b2 = 0; b2 < 4; ++b2) t[a][b2] = fmaf(pv[a], rv[b2], t[a][b2]);
         }
-        *reinterpret_cast<float4*>(Ts + ii * ldp + c4) = t;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+          *reinterpret_cast<float4*>(Ts + (4 * rg + a) * ldp + 4 * cg) =
+              make_float4(t[a][0], t[a][1], t[a][2], t[a][3]);
       }
       __syncthreads();
       src = Ts;
     }
     if (active) {
+      float acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = 0.f;
 #pragma unroll 4
       for (int ii = grp; ii < GSUB; ii += groups) {
         const float4 x4 = *reinterpret_cast<const float4*>(src + ii * ldp + ty * 4);
@@ -532,31 +591,47 @@ panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __res
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(x[a], y[b], acc[a][b]);
+          for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = fmaf(x[a], y[b2], acc[a][b2]);
       }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) {  // Kahan: (hi, lo) += acc
+          const float yv = acc[a][b2] - lo[a][b2];
+          const float tv = hi[a][b2] + yv;
+          lo[a][b2] = (tv - hi[a][b2]) - yv;
+          hi[a][b2] = tv;
+        }
     }
   }
-  // sum the row groups
+  // sum the row groups (the staging buffers are free now)
+  __syncthreads();
+  float* Red = Ps;
   if (active && grp > 0) {
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) Red[tid * 16 + a * 4 + b] = acc[a][b];
+      for (int b2 = 0; b2 < 4; ++b2) Red[(tid - ntiles) * 16 + a * 4 + b2] = hi[a][b2] - lo[a][b2];
   }
   __syncthreads();
   if (active && grp == 0) {
+    float out4[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) out4[a][b2] = hi[a][b2] - lo[a][b2];
     for (int g2 = 1; g2 < groups; ++g2) {
-      const int t2 = g2 * ntiles + tile;
+      const int t2 = (g2 - 1) * ntiles + tile;
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] += Red[t2 * 16 + a * 4 + b];
+        for (int b2 = 0; b2 < 4; ++b2) out4[a][b2] += Red[t2 * 16 + a * 4 + b2];
     }
     float* out = partial + (long long)blockIdx.x * kp * kp;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
       *reinterpret_cast<float4*>(out + (ty * 4 + a) * kp + tx * 4) =
-          make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+          make_float4(out4[a][0], out4[a][1], out4[a][2], out4[a][3]);
   }
 }
 
@@ -652,169 +727,206 @@ chol_kernel(int kp, const MatDev* __restrict__ mats, const int* __restrict__ chu
   }
 }
 
-// Two-sided cyclic Jacobi on the symmetric A (k x k, leading dimension ld) in
-// the parallel round-robin order: each round computes the rotations of its
-// disjoint pairs from (A_pp, A_qq, A_pq), then applies them to the columns
-// of A and V, then to the rows of A.  Whole-block cooperative.  On return
-// diag(A) holds the eigenvalues and the columns of V the eigenvectors.
-template <typename T>
-__device__ void jacobi_sym(T* A, T* V, int k, int ld, int max_sweeps, T tol, T* cs,
-                           int* pq, int* rotated) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int kk = k + (k & 1), np = kk / 2;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) *rotated = 0;
-    __syncthreads();
-    for (int round = 0; round < kk - 1; ++round) {
-      for (int i = tid; i < np; i += nt) {
-        int p, q;
-        rr_pair(round, i, kk, p, q);
-        T c = T(1), sn = T(0);
-        if (p < k && q < k) {
-          const T apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
-          if (fabs(apq) > tol * sqrt(fabs(app * aqq)) && fabs(apq) > Eps<T>::tiny) {
-            const T tau = (aqq - app) / (T(2) * apq);
-            const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-            c = T(1) / sqrt(T(1) + t * t);
-            sn = t * c;
-            *rotated = 1;
-          }
-        } else {
-          p = -1;
-        }
-        cs[2 * i] = c;
-        cs[2 * i + 1] = sn;
-        pq[2 * i] = p;
-        pq[2 * i + 1] = q;
-      }
-      __syncthreads();
-      for (int e = tid; e < np * k; e += nt) {  // columns of A and V
-        const int i = e / k, r = e % k;
-        const int p = pq[2 * i], q = pq[2 * i + 1];
-        if (p < 0) continue;
-        const T c = cs[2 * i], sn = cs[2 * i + 1];
-        const T x = A[r * ld + p], y = A[r * ld + q];
-        A[r * ld + p] = c * x - sn * y;
-        A[r * ld + q] = sn * x + c * y;
-        const T vx = V[r * ld + p], vy = V[r * ld + q];
-        V[r * ld + p] = c * vx - sn * vy;
-        V[r * ld + q] = sn * vx + c * vy;
-      }
-      __syncthreads();
-      for (int e = tid; e < np * k; e += nt) {  // rows of A
-        const int i = e / k, r = e % k;
-        const int p = pq[2 * i], q = pq[2 * i + 1];
-        if (p < 0) continue;
-        const T c = cs[2 * i], sn = cs[2 * i + 1];
-        const T x = A[p * ld + r], y = A[q * ld + r];
-        A[p * ld + r] = c * x - sn * y;
-        A[q * ld + r] = sn * x + c * y;
-      }
-      __syncthreads();
-    }
-    if (*rotated == 0) break;
-  }
+// eig_finish_kernel: CTAs of EIG_THREADS threads; each holds EIG_THREADS /
+// ks matrices (ks = the largest k of the batch, <= EIG_KMAX), one thread per
+// column.
+constexpr int EIG_KMAX = 48;
+constexpr int EIG_THREADS = 128;
+// Shared memory of one matrix slot: G and two buffers of B columns
+// (ks x (ks + 1) floats each), eigenvalues and their order.
+__host__ __device__ constexpr size_t eig_slot_bytes(int ks) {
+  return (size_t)3 * ks * (ks + 1) * sizeof(float) + (size_t)ks * (sizeof(float) + sizeof(int));
 }
 
-// One CTA per matrix: G_M (FP64) from its partials; eigenpairs of G_M by
-// two-sided Jacobi in FP32; V_r brought back to orthonormal in FP64 with one
-// step V <- V (I - (V^T V - I) / 2) (its error is quadratic in the FP32
-// orthogonality error); captured energy tr(V_r^T G_M V_r) in FP64 (Ky Fan:
-// equal to sum_{i<=r} lambda_i up to second-order terms); err, sigma and
-// W = R_X^{-1} V_r.
-__global__ void __launch_bounds__(256)
-eig_finish_kernel(int kp, const MatDev* __restrict__ mats, const int* __restrict__ chunk_off,
-                  const float* __restrict__ partial, const float* __restrict__ rinv,
-                  float* __restrict__ Wm, const double* __restrict__ normA2,
-                  double* __restrict__ err, int* __restrict__ flags, int err_mode, double tau) {
+// Partner of column j in round `round` of the round-robin order on kk = 2 m'
+// columns (mm = kk - 1): the pairs of a round are (round, mm) and
+// (round + i, round - i) mod mm, i = 1 .. kk/2 - 1, so two columns other than
+// mm pair up when their indices sum to 2 round mod mm.
+__device__ __forceinline__ int rr_partner(int round, int j, int mm) {
+  const int r0 = round % mm;
+  if (j == mm) return r0;
+  if (j == r0) return mm;
+  return ((2 * round - j) % mm + mm) % mm;
+}
+
+// G_M = sum of its FP32 partial Grams; eigenpairs of the symmetric positive
+// semidefinite G_M by one-sided (Hestenes) Jacobi on B = G_M: rotations that
+// make the columns of B mutually orthogonal leave B = G_M V = V Lambda, so
+// the column norms are the eigenvalues and the normalised columns the
+// eigenvectors (whose errors reach the captured energy, a Rayleigh quotient,
+// only at second order).  Thread j keeps column j of B in registers; each
+// round of the parallel round-robin order it reads its partner's column
+// from shared memory (double-buffered, one barrier per round), and both
+// threads of a pair compute the same rotation from the same three dot
+// products.  Then V_r is brought back to orthonormal with one step
+// V <- V (I - (V^T V - I) / 2); the captured energy tr(V_r^T G_M V_r) (Ky
+// Fan: sum_{i<=r} lambda_i up to second-order terms) gives
+// err^2 = ||A||^2 - energy; sigma = sqrt(lambda) and W = R_X^{-1} V_r.
+// Arithmetic is FP32 (the partial Grams are FP32 sums already); per-thread
+// parts of the energy are added in FP64.
+__global__ void __launch_bounds__(EIG_THREADS)
+eig_finish_kernel(int kp, int ks, int count, const MatDev* __restrict__ mats,
+                  const int* __restrict__ chunk_off, const float* __restrict__ partial,
+                  const float* __restrict__ rinv, float* __restrict__ Wm,
+                  const double* __restrict__ normA2, double* __restrict__ err,
+                  int* __restrict__ flags, int err_mode, double tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ld = kp + 1;
-  double* G = (double*)smem_raw;      // kp x kp
-  double* Vd = G + kp * kp;           // kp x kp : V_r (FP64 copy of the FP32 result)
-  double* Ed = Vd + kp * kp;          // kp x kp : V_r^T V_r - I
-  double* Vc = Ed + kp * kp;          // kp x kp : corrected V_r
-  float* Af = (float*)(Vc + kp * kp); // kp x ld
-  float* V = Af + kp * ld;            // kp x ld
-  float* cs = V + kp * ld;            // 2 * kp
-  float* lam = cs + 2 * kp;           // kp
-  int* pq = (int*)(lam + kp);         // 2 * kp
-  int* order = pq + 2 * kp;           // kp
-  __shared__ int rotated;
-  __shared__ double red[8];
-  const int b = blockIdx.x, tid = threadIdx.x;
-  const MatDev md = mats[b];
-  const int k = md.k, r = md.r;
-  const int c0 = chunk_off[b], c1 = chunk_off[b + 1];
-  for (int e = tid; e < kp * kp; e += blockDim.x) {
-    const int i = e / kp, c = e % kp;
-    const double g = (i < k && c < k) ? gram_entry(partial, c0, c1, kp, i, c) : 0.0;
-    G[e] = g;
-    Af[i * ld + c] = (float)g;
-    V[i * ld + c] = (i == c) ? 1.f : 0.f;
+  const int tid = threadIdx.x, mpc = EIG_THREADS / ks;
+  const int slot = tid / ks, j = tid % ks;  // this thread: column j of slot's matrix
+  const int b = blockIdx.x * mpc + slot;
+  const bool live = slot < mpc && b < count;
+  const int ld = ks + 1, plane = ks * ld;
+  float* Gs = (float*)(smem_raw + (size_t)min(slot, mpc - 1) * eig_slot_bytes(ks));
+  float* Bs = Gs + plane;        // 2 planes: column j at Bs[buf * plane + j * ld]
+  float* lam = Bs + 2 * plane;   // ks
+  int* order = (int*)(lam + ks); // ks
+  MatDev md;
+  int k = 0, r = 0;
+  if (live) {
+    md = mats[b];
+    k = md.k;
+    r = md.r;
+    const int c0 = chunk_off[b], c1 = chunk_off[b + 1];
+    for (int e = j; e < k * k; e += ks) {
+      const int i = e / k, c = e % k;
+      const int a = min(i, c), bb = max(i, c);  // partials hold the upper triangle
+      float g = 0.f;
+      for (int q = c0; q < c1; ++q) g += partial[(long long)q * kp * kp + a * kp + bb];
+      Gs[i * ld + c] = g;
+    }
   }
   __syncthreads();
-  jacobi_sym<float>(Af, V, k, ld, 12, 4.0e-6f, cs, pq, &rotated);
-  for (int c = tid; c < k; c += blockDim.x) lam[c] = Af[c * ld + c];
+  float bc[EIG_KMAX];
+#pragma unroll
+  for (int i = 0; i < EIG_KMAX; ++i) bc[i] = (j < k && i < k) ? Gs[i * ld + j] : 0.f;
+  const int kk = k + (k & 1), mm = kk - 1;
+  int t = 0;  // rounds so far: selects the buffer
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    int rot = 0;
+    // every slot runs the rounds of the largest k in the CTA (barriers are
+    // CTA-wide); a slot whose own rounds are done idles through the rest
+    for (int round = 0; round < ks + (ks & 1) - 1; ++round, ++t) {
+      float* Bb = Bs + (t & 1) * plane;
+      if (j < k && round < mm) {
+#pragma unroll
+        for (int i = 0; i < EIG_KMAX; ++i)
+          if (i < k) Bb[j * ld + i] = bc[i];
+      }
+      __syncthreads();
+      const int pj = (round < mm) ? rr_partner(round, j, mm) : k;
+      if (j < k && pj < k) {
+        const float* pb = Bb + pj * ld;
+        float y[EIG_KMAX];
+        float aa0 = 0.f, aa1 = 0.f, pp0 = 0.f, pp1 = 0.f, ap0 = 0.f, ap1 = 0.f;
+#pragma unroll
+        for (int i = 0; i < EIG_KMAX; i += 2) {
+          y[i] = (i < k) ? pb[i] : 0.f;
+          y[i + 1] = (i + 1 < k) ? pb[i + 1] : 0.f;
+          aa0 = fmaf(bc[i], bc[i], aa0);
+          pp0 = fmaf(y[i], y[i], pp0);
+          ap0 = fmaf(bc[i], y[i], ap0);
+          aa1 = fmaf(bc[i + 1], bc[i + 1], aa1);
+          pp1 = fmaf(y[i + 1], y[i + 1], pp1);
+          ap1 = fmaf(bc[i + 1], y[i + 1], ap1);
+        }
+        const float aa = aa0 + aa1, pp = pp0 + pp1, ap = ap0 + ap1;
+        const bool low = j < pj;  // the lower index is p of the pair (p, q)
+        const float alpha = low ? aa : pp, beta = low ? pp : aa, gamma = ap;
+        if (fabsf(gamma) > 4.0e-6f * sqrtf(alpha * beta) && fabsf(gamma) > 1.0e-30f) {
+          const float zeta = (beta - alpha) / (2.f * gamma);
+          const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float c = 1.f / sqrtf(1.f + tt * tt), sn = tt * c;
+          // [b_p b_q] <- [c b_p - s b_q, s b_p + c b_q]
+          const float cp = low ? -sn : sn;
+#pragma unroll
+          for (int i = 0; i < EIG_KMAX; ++i) bc[i] = fmaf(c, bc[i], cp * y[i]);
+          rot = 1;
+        }
+      }
+    }
+    if (!__syncthreads_or(rot)) break;
+  }
+  // eigenvalues = column norms; normalised columns = eigenvectors (plane 0)
+  float* Vs = Bs;           // column j at Vs[j * ld + i]
+  float* Vc = Bs + plane;   // corrected V_r, column c at Vc[c * ld + i]
+  if (j < k) {
+    float nn = 0.f;
+#pragma unroll
+    for (int i = 0; i < EIG_KMAX; ++i) nn = fmaf(bc[i], bc[i], nn);
+    const float l = sqrtf(nn);
+    lam[j] = l;
+    const float inv = l > 1.0e-30f ? 1.f / l : 0.f;
+#pragma unroll
+    for (int i = 0; i < EIG_KMAX; ++i)
+      if (i < k) Vs[j * ld + i] = (inv > 0.f) ? bc[i] * inv : (i == j ? 1.f : 0.f);
+  }
   __syncthreads();
-  for (int c = tid; c < k; c += blockDim.x) {  // descending eigenvalues
+  if (j < k) {  // descending eigenvalues
     int rank = 0;
-    for (int c2 = 0; c2 < k; ++c2) rank += (lam[c2] > lam[c]) || (lam[c2] == lam[c] && c2 < c);
-    order[rank] = c;
+    for (int c2 = 0; c2 < k; ++c2) rank += (lam[c2] > lam[j]) || (lam[c2] == lam[j] && c2 < j);
+    order[rank] = j;
   }
   __syncthreads();
-  for (int e = tid; e < k * r; e += blockDim.x) {
-    const int i = e / r, c = e % r;
-    Vd[i * kp + c] = (double)V[i * ld + order[c]];
+  if (live && md.sigma != nullptr && j < k) ((float*)md.sigma)[j] = sqrtf(lam[order[j]]);
+  // column c < r of V_r (E = V_r^T V_r - I, then V_r <- V_r - V_r E / 2)
+  if (j < r) {
+    const float* vc = Vs + order[j] * ld;
+    float e[EIG_KMAX];
+#pragma unroll
+    for (int a = 0; a < EIG_KMAX; ++a) {
+      float s2 = 0.f;
+      if (a < r) {
+        const float* va = Vs + order[a] * ld;
+        s2 = (a == j) ? -1.f : 0.f;
+        for (int i = 0; i < k; ++i) s2 = fmaf(va[i], vc[i], s2);
+      }
+      e[a] = s2;
+    }
+    for (int i = 0; i < k; ++i) {
+      float s2 = 0.f;
+#pragma unroll
+      for (int a = 0; a < EIG_KMAX; ++a)
+        if (a < r) s2 = fmaf(Vs[order[a] * ld + i], e[a], s2);
+      Vc[j * ld + i] = fmaf(-0.5f, s2, vc[i]);
+    }
   }
   __syncthreads();
-  for (int e = tid; e < r * r; e += blockDim.x) {  // E = V_r^T V_r - I
-    const int a = e / r, c = e % r;
-    double t = (a == c) ? -1.0 : 0.0;
-    for (int i = 0; i < k; ++i) t += Vd[i * kp + a] * Vd[i * kp + c];
-    Ed[a * kp + c] = t;
+  // row i of G V_r and of W = R_X^{-1} V_r; energy tr(V_r^T G V_r)
+  double part = 0.0;
+  if (live) {
+    const float* Ri = rinv + (long long)b * kp * kp;
+    float* Wout = Wm + (long long)b * kp * kp;
+    for (int i = j; i < kp; i += ks) {
+      for (int c = 0; c < kp; ++c) {
+        float w = 0.f;
+        if (i < k && c < r) {
+          const float* v = Vc + c * ld;
+          float gv = 0.f;
+          for (int q = 0; q < k; ++q) gv = fmaf(Gs[i * ld + q], v[q], gv);
+          part += (double)v[i] * (double)gv;
+          for (int q = i; q < k; ++q) w = fmaf(Ri[i * kp + q], v[q], w);  // R_X^{-1} upper
+        }
+        Wout[i * kp + c] = w;
+      }
+    }
   }
+  // per-slot sums: lanes of a slot may span warps, so go through shared memory
   __syncthreads();
-  for (int e = tid; e < k * r; e += blockDim.x) {  // V_r <- V_r - V_r E / 2
-    const int i = e / r, c = e % r;
-    double t = 0.0;
-    for (int a = 0; a < r; ++a) t += Vd[i * kp + a] * Ed[a * kp + c];
-    Vc[i * kp + c] = Vd[i * kp + c] - 0.5 * t;
-  }
+  double* acc = (double*)Gs;  // the slot's G is no longer needed: ks doubles fit in it
+  if (slot < mpc) acc[j] = part;
   __syncthreads();
-  double part = 0.0;  // tr(V_r^T G V_r)
-  for (int e = tid; e < k * r; e += blockDim.x) {
-    const int i = e / r, c = e % r;
-    double gv = 0.0;
-    for (int j = 0; j < k; ++j) gv += G[i * kp + j] * Vc[j * kp + c];
-    part += Vc[i * kp + c] * gv;
-  }
-  part = warp_sum(part);
-  if ((tid & 31) == 0) red[tid >> 5] = part;
-  __syncthreads();
-  if (tid == 0) {
-    double cap = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) cap += red[w];
+  if (live && j == 0) {
+    double energy = 0.0;
+    for (int q = 0; q < ks; ++q) energy += acc[q];
     const double tot = normA2[b];
-    const double e2 = tot - cap;
+    const double e2 = tot - energy;
     err[b] = sqrt(e2 > 0.0 ? e2 : 0.0);
     flags[b] = (err_mode == 2) || (err_mode == 0 && e2 < tau * tot);
   }
-  if (md.sigma != nullptr)
-    for (int c = tid; c < k; c += blockDim.x)
-      ((float*)md.sigma)[c] = sqrtf(fmaxf(lam[order[c]], 0.f));
-  // W = R_X^{-1} V_r
-  const float* Ri = rinv + (long long)b * kp * kp;
-  float* Wout = Wm + (long long)b * kp * kp;
-  for (int e = tid; e < kp * kp; e += blockDim.x) {
-    const int i = e / kp, c = e % kp;
-    float t = 0.f;
-    if (i < k && c < r)
-      for (int q = i; q < k; ++q) t = fmaf(Ri[i * kp + q], (float)Vc[q * kp + c], t);
-    Wout[e] = t;
-  }
 }
 
-cudaError_t launch_gram_route(int kp, const MatDev* mats, int count, const PanelDev* xpanels,
+cudaError_t launch_gram_route(int kp, int kmax, const MatDev* mats, int count,
+                              const PanelDev* xpanels,
                               const PanelDev* ypanels, const int2* xchunks, int nxc,
                               const int* xoff, const int2* ychunks, int nyc, const int* yoff,
                               float* partial_x, float* partial_y, float* r1, float* r2,
@@ -822,11 +934,11 @@ cudaError_t launch_gram_route(int kp, const MatDev* mats, int count, const Panel
                               int err_mode, double tau, int refine, int* status,
                               cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  const size_t gsm = (size_t)(2 * GSUB * (kp + 4) + kp * kp + 256 * 16) * sizeof(float);
+  const size_t gsm = panel_gram_smem(kp);
   const size_t csm = (size_t)3 * kp * (kp + 1) * sizeof(float);
-  const size_t esm = (size_t)4 * kp * kp * sizeof(double) +
-                     (size_t)2 * kp * (kp + 1) * sizeof(float) + 3 * kp * sizeof(float) +
-                     3 * kp * sizeof(int) + 16;
+  const int ks = std::max(1, std::min(kmax, EIG_KMAX));
+  const int mpc = EIG_THREADS / ks;
+  const size_t esm = (size_t)mpc * eig_slot_bytes(ks);
   cudaError_t e = cudaFuncSetAttribute(eig_finish_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm);
   if (e == cudaSuccess)
@@ -836,17 +948,17 @@ cudaError_t launch_gram_route(int kp, const MatDev* mats, int count, const Panel
                              (int)gsm);
   if (e != cudaSuccess) return e;
   // R1 = chol(X^T X)
-  panel_gram_kernel<<<nxc, 256, gsm, s>>>(kp, xpanels, xchunks, nullptr, partial_x);
+  panel_gram_kernel<<<nxc, GTHREADS, gsm, s>>>(kp, xpanels, xchunks, nullptr, partial_x);
   chol_kernel<<<count, 256, csm, s>>>(kp, mats, xoff, partial_x, nullptr, r1, rinv, status);
   if (refine) {
     // R = chol(Q1^T Q1) R1 with Q1 = X R1^{-1}
-    panel_gram_kernel<<<nxc, 256, gsm, s>>>(kp, xpanels, xchunks, rinv, partial_x);
+    panel_gram_kernel<<<nxc, GTHREADS, gsm, s>>>(kp, xpanels, xchunks, rinv, partial_x);
     chol_kernel<<<count, 256, csm, s>>>(kp, mats, xoff, partial_x, r1, r2, rinv, status);
   }
   // G_M = (Y R^{-1})^T (Y R^{-1})
-  panel_gram_kernel<<<nyc, 256, gsm, s>>>(kp, ypanels, ychunks, rinv, partial_y);
-  eig_finish_kernel<<<count, 256, esm, s>>>(kp, mats, yoff, partial_y, rinv, Wm, normA2, err,
-                                            flags, err_mode, tau);
+  panel_gram_kernel<<<nyc, GTHREADS, gsm, s>>>(kp, ypanels, ychunks, rinv, partial_y);
+  eig_finish_kernel<<<(count + mpc - 1) / mpc, EIG_THREADS, esm, s>>>(
+      kp, ks, count, mats, yoff, partial_y, rinv, Wm, normA2, err, flags, err_mode, tau);
   return cudaGetLastError();
 }
 

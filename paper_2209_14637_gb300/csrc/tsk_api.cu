@@ -20,6 +20,7 @@ struct tsk_plan_s {
   int count = 0;
   tsk_prec prec = TSK_FP32;
   int kp = 16;
+  int kmax = 1;
   bool dbl = false;
   bool use_tc = false;
   void* ws = nullptr;
@@ -280,7 +281,7 @@ static cudaError_t capture_plan(tsk_plan p, cudaEvent_t evb, cudaEvent_t eve) {
   } else if (ce == cudaSuccess) {
     // FP32 / BF16: Cholesky of X^T X (+ one refinement), eigenpairs of M^T M
     const PanelDev* pan = (const PanelDev*)(base + p->o_pan);
-    ce = launch_gram_route(kp, d_mats, count, pan, pan + count,
+    ce = launch_gram_route(kp, p->kmax, d_mats, count, pan, pan + count,
                            (const int2*)(base + p->o_xch), p->nxc,
                            (const int*)(base + p->o_xoff), (const int2*)(base + p->o_ych),
                            p->nyc, (const int*)(base + p->o_yoff), (float*)(base + p->o_px),
@@ -375,6 +376,7 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   p->prec = prec;
   p->dbl = (prec == TSK_FP64);
   p->kp = ((kmax + 15) / 16) * 16;
+  p->kmax = kmax;
   p->use_tc = use_tc;
   const int kp = p->kp;
   const size_t cs = compute_size(prec);

@@ -114,7 +114,8 @@ cudaError_t launch_small_svd(bool dbl, int kp, const MatDev* mats, int count,
                              cudaStream_t s);
 cudaError_t launch_sym_eig(bool dbl, const void* H, int p, void* theta,
                            void* V, cudaStream_t s);
-cudaError_t launch_gram_route(int kp, const MatDev* mats, int count, const PanelDev* xpanels,
+cudaError_t launch_gram_route(int kp, int kmax, const MatDev* mats, int count,
+                              const PanelDev* xpanels,
                               const PanelDev* ypanels, const int2* xchunks, int nxc,
                               const int* xoff, const int2* ychunks, int nyc, const int* yoff,
                               float* partial_x, float* partial_y, float* r1, float* r2,
