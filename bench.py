@@ -33,6 +33,11 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0,
                   "bf16_tflops_sustained": 1700.0}
 
 
+# DRAM bytes (read + write) per 2048 x 2048 BF16 matrix of the tcgen05 sketch
+# kernel with k = 40, from ncu on a 64-matrix launch (537.21 MB read, 33.16 MB
+# written); re-measure whenever that kernel changes.
+SKETCH_TRAFFIC_PER_MATRIX = (537.21e6 + 33.16e6) / 64
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -385,7 +390,13 @@ def run_tsk(args):
                          "peak_source": f"hbm_gbs of {peak_src}",
                          "kernel": "sketch pass (X = A^T S^T, Y = A X)",
                          "kernel_ms": stage_avg,
-                         "algorithmic_bytes": alg_bytes, "traffic": None},
+                         "algorithmic_bytes": alg_bytes,
+                         "traffic": (SKETCH_TRAFFIC_PER_MATRIX * count
+                                     if plan_kind == "tcgen05" else None),
+                         "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                                            "of one 64-matrix launch, scaled to this launch "
+                                            "by the number of matrices"
+                                            if plan_kind == "tcgen05" else None)},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,

@@ -10,20 +10,22 @@
 // loaded from HBM once and used twice while it sits in shared memory.
 //
 // Work split.  A cluster of C CTAs owns one matrix at a time; CTA rank rho
-// owns rows [rho*MC, (rho+1)*MC).  For every block of 64 columns:
+// owns rows [rho*MC, (rho+1)*MC) of A and rows [rho*R, (rho+1)*R) of X
+// (R = kq / C).  For every block of 64 columns:
 //   1. TMA loads the CTA's MC x 64 tile (128-byte swizzle) into a stage.
 //   2. MMA-X:  D_x(c, j) = sum_i S(c, i) A(i, j) over the CTA's rows
 //      (A operand: the CTA's slice of S as BF16, K-major; B operand: the A
 //      tile read MN-major), accumulated in TMEM (M = 128 lanes, N = 64).
-//   3. The partial D_x of the C CTAs are reduce-scattered through
-//      distributed shared memory; each CTA sums 64/C columns, rounds them
-//      to BF16 (X~), writes them to X in HBM and into every peer's X~
-//      buffer (st.shared::cluster).
+//   3. The partial D_x rows go to their owners by st.async (bytes counted
+//      on the owner's barrier); each owner sums the C partials of its rows,
+//      rounds them to X~ = X_hi + X_lo (two BF16 terms) and a signalling
+//      warp bulk-copies those rows into every peer's X~ buffer; an X writer
+//      warp stores the owner's rows of X~ to HBM.
 //   4. MMA-Y:  D_y(i, c) += sum_j A(i, j) X~(j, c), the same A tile now read
 //      K-major, accumulated in TMEM across all column blocks.
-// After the last block D_y (the CTA's MC rows of Y) goes to HBM.  Two warps
-// meanwhile sum the squares of every tile (Kahan-compensated, FP32 per
-// block, FP64 across blocks) for ||A||_F^2.
+// After the last block D_y (the CTA's MC rows of Y) goes to HBM.  Four warps
+// meanwhile sum the squares of every tile (FP32 per block, FP64 across
+// blocks) for ||A||_F^2.
 //
 // Y uses the BF16-rounded X~, so the R factor must be taken from X~ too;
 // X holds exactly those values.
