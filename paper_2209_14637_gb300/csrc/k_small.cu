@@ -434,56 +434,91 @@ cudaError_t launch_sym_eig(bool dbl, const void* H, int p, void* theta,
 //
 // Y itself is not factored: its columns grow like sigma_i^2 and Y^T Y would
 // lose everything in FP32.  Partial Gram matrices are summed in FP32 over
-// blocks of 64 rows, compensated (Kahan) across the blocks of a chunk of up
-// to 1024 rows, and across chunks in FP64 (Cholesky) or FP32 (eigenpairs);
+// chunks of up to 512 rows, and across chunks in FP64 (Cholesky) or FP32
+// (eigenpairs);
 // the k x k Cholesky, its inverse and the eigenpairs run in FP32; the
 // captured energy sum_{i<=r} v_i^T (M^T M) v_i is summed in FP64 from FP32
 // products.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int GCHUNK = 1024;  // rows per partial Gram
-constexpr int GSUB = 64;      // rows staged in shared memory at a time
+constexpr int GCHUNK = 512;  // rows per partial Gram
+constexpr int GSUB = 64;     // rows per block
+constexpr int GSTAGES = 4;   // blocks in flight
 constexpr int GTHREADS = 256;
+constexpr long long GWAIT_NS = 4000000000ll;  // bound on one wait for a block
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 }  // namespace
 
-// Shared memory of panel_gram_kernel: the staged rows (transposed, kp x
-// (GSUB + 1), when a transform follows; else row-major GSUB x (kp + 4)), the
-// transformed rows (GSUB x (kp + 4)) and R^{-1} (kp x kp); at the end the
-// same space holds the row groups' tiles (at most GTHREADS x 16 floats).
+// Shared memory of panel_gram_kernel: GSTAGES blocks of GSUB rows (kp floats
+// each, as stored: the panels have leading dimension kp), the transformed rows (GSUB x (kp + 4)), R^{-1} (kp x kp)
+// and one mbarrier per stage; at the end the stages hold the row groups'
+// tiles (at most GTHREADS x 16 floats).
 size_t panel_gram_smem(int kp) {
-  const size_t a = (size_t)kp * (GSUB + 1), b = (size_t)GSUB * (kp + 4);
-  return std::max(std::max(a, b) + b + (size_t)kp * kp, (size_t)GTHREADS * 16) * sizeof(float);
+  const size_t st = (size_t)GSTAGES * GSUB * kp, ts = (size_t)GSUB * (kp + 4);
+  return (std::max(st, (size_t)GTHREADS * 16) + ts + (size_t)kp * kp) * sizeof(float) +
+         GSTAGES * sizeof(uint64_t);
 }
 
 // One CTA per (panel, chunk of GCHUNK rows): partial G = P_c^T P_c over the
 // chunk's rows, where P_c = P or P R^{-1} (Rinv: kp x kp FP32, upper, per
-// panel).  The rows stream through shared memory GSUB at a time; the next
-// block is loaded into registers while the current one is processed.  The
-// transform gives each thread a 4 x 4 tile of P R^{-1} (4 rows of the staged
-// block, stored transposed, times 4 columns of R^{-1}); the Gram gives each
-// thread a 4 x 4 tile of the upper triangle, several row groups per tile
-// when there are fewer tiles than threads.  Each block's FP32 sums are added
-// into a compensated (Kahan) FP32 accumulator, so the chunk's error stays
-// near that of one block.  Entries below the diagonal of the partial are
-// left unwritten.
-__global__ void __launch_bounds__(GTHREADS)
+// panel).  A block of GSUB rows of a panel is one contiguous run of memory,
+// so one thread brings each block in with a bulk copy (its bytes counted on
+// the stage's mbarrier), GSTAGES blocks ahead.  The transform gives each
+// thread a 4 x 4 tile of P R^{-1} (four rows of R^{-1} per step: eight
+// 16-byte loads per 64 FMAs); the Gram gives each thread a 4 x 4 tile of the
+// upper triangle, several row groups per tile when there are fewer tiles
+// than threads.  Columns k .. kp-1 of the panels are zero (the plan clears
+// them once).  Entries below the diagonal of the partial are left unwritten.
+// A wait for a block is bounded; on expiry the kernel raises kStatusTimeout.
+__global__ void __launch_bounds__(GTHREADS, 2)
 panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __restrict__ chunks,
-                  const float* __restrict__ rinv, float* __restrict__ partial) {
+                  const float* __restrict__ rinv, float* __restrict__ partial,
+                  int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int2 ch = chunks[blockIdx.x];
   const PanelDev pd = panels[ch.x];
-  const int k = pd.k, ld = pd.ld;
+  const int k = pd.k;
   const bool tr = (rinv != nullptr);
-  const int ldt = GSUB + 1, ldp = kp + 4;
-  float* Ps = (float*)smem_raw;  // staged rows: transposed (tr) or row-major
-  float* Ts = Ps + max(kp * ldt, GSUB * ldp);
+  const int ldp = kp + 4, blk = GSUB * kp;
+  float* Ps = (float*)smem_raw;  // GSTAGES blocks, rows of kp floats
+  float* Ts = Ps + max(GSTAGES * blk, GTHREADS * 16);
   float* Rs = Ts + GSUB * ldp;
+  uint64_t* bars = (uint64_t*)(Rs + kp * kp);
   const float* P = (const float*)pd.P;
   const int tid = threadIdx.x;
-  if (tr) {
-    const float* R = rinv + (long long)ch.x * kp * kp;
-    for (int e = tid; e < kp * kp; e += GTHREADS) Rs[e] = R[e];
+  const long long r0 = (long long)ch.y * GCHUNK;
+  const long long r1 = min(pd.rows, r0 + GCHUNK);
+  const int nblk = (int)((r1 - r0 + GSUB - 1) / GSUB);
+  auto bar = [&](int s) { return (uint32_t)__cvta_generic_to_shared(bars + s); };
+  auto issue = [&](int b) {  // thread 0: block b into stage b % GSTAGES
+    const int s = b % GSTAGES;
+    const long long s0 = r0 + (long long)b * GSUB;
+    const uint32_t bytes = (uint32_t)(min((long long)GSUB, r1 - s0) * kp * sizeof(float));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(s)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"((uint32_t)__cvta_generic_to_shared(Ps + s * blk)),
+        "l"(P + s0 * pd.ld), "r"(bytes), "r"(bar(s))
+        : "memory");
+  };
+  if (tid == 0) {
+    for (int s = 0; s < GSTAGES; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(s)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  __syncthreads();
+  if (tid == 0)
+    for (int b = 0; b < min(GSTAGES - 1, nblk); ++b) issue(b);
+  if (tr)
+    for (int e = tid; e < kp * kp; e += GTHREADS) Rs[e] = rinv[(long long)ch.x * kp * kp + e];
+  __syncthreads();  // R^{-1} in place before the first transform
   const int nt = kp / 4;
   const int ntiles = nt * (nt + 1) / 2;
   const int groups = max(1, GTHREADS / ntiles);
@@ -498,75 +533,68 @@ panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __res
   // transform tile of this thread: rows 4 rg .. 4 rg + 3, columns 4 cg .. 4 cg + 3
   const int rg = tid / nt, cg = tid % nt;
   const bool tact = tr && rg < GSUB / 4;
-  float hi[4][4], lo[4][4];
+  const int top = min((k + 3) & ~3, 4 * cg + 4);  // R^{-1} is upper: rows < top
+  float acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b2 = 0; b2 < 4; ++b2) hi[a][b2] = lo[a][b2] = 0.f;
-  const long long r0 = (long long)ch.y * GCHUNK;
-  const long long r1 = min(pd.rows, r0 + GCHUNK);
-  const int q4 = kp / 4;  // float4 per row
-  constexpr int PER = (GSUB * (TSK_MAX_K / 4) + GTHREADS - 1) / GTHREADS;  // float4 per thread
-  float4 pre[PER];
-  auto fetch = [&](long long s0) {
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int e = tid + u * GTHREADS;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (e < GSUB * q4) {
-        const int ii = e / q4, c4 = (e % q4) * 4;
-        const long long i = s0 + ii;
-        if (i < r1) {
-          v = *reinterpret_cast<const float4*>(P + i * ld + c4);
-          if (c4 + 0 >= k) v.x = 0.f;
-          if (c4 + 1 >= k) v.y = 0.f;
-          if (c4 + 2 >= k) v.z = 0.f;
-          if (c4 + 3 >= k) v.w = 0.f;
-        }
-      }
-      pre[u] = v;
-    }
-  };
-  fetch(r0);
-  for (long long s0 = r0; s0 < r1; s0 += GSUB) {
-    __syncthreads();  // the previous block is fully consumed
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int e = tid + u * GTHREADS;
-      if (e < GSUB * q4) {
-        const int ii = e / q4, c4 = (e % q4) * 4;
-        const float4 v = pre[u];
-        if (tr) {
-          Ps[(c4 + 0) * ldt + ii] = v.x;
-          Ps[(c4 + 1) * ldt + ii] = v.y;
-          Ps[(c4 + 2) * ldt + ii] = v.z;
-          Ps[(c4 + 3) * ldt + ii] = v.w;
-        } else {
-          *reinterpret_cast<float4*>(Ps + ii * ldp + c4) = v;
+    for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = 0.f;
+  bool ok = true;
+  for (int b = 0; b < nblk; ++b) {
+    const int s = b % GSTAGES;
+    if (tid == 0 && ok && b + GSTAGES - 1 < nblk) issue(b + GSTAGES - 1);  // stage freed
+    if (ok) {  // wait for block b (bounded)
+      const uint32_t parity = (uint32_t)((b / GSTAGES) & 1);
+      uint32_t done = 0;
+      const uint64_t t0 = gtimer();
+      for (;;) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar(s)), "r"(parity)
+            : "memory");
+        if (done) break;
+        if ((long long)(gtimer() - t0) > GWAIT_NS) {
+          atomicOr(status, kStatusTimeout);
+          ok = false;
+          break;
         }
       }
     }
-    __syncthreads();
-    if (s0 + GSUB < r1) fetch(s0 + GSUB);  // overlaps the work below
-    const float* src = Ps;
+    const float* Pb = Ps + s * blk;
+    const int nrows = (int)min((long long)GSUB, r1 - r0 - (long long)b * GSUB);
+    const float* src = Pb;
+    int lds = kp;
     if (tr) {
-      // Ts = Ps R^{-1}: R^{-1} is upper, so column c needs rows cc <= c of it
+      // Ts = Pb R^{-1}, four rows of R^{-1} per step
       if (tact) {
         float t[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
           for (int b2 = 0; b2 < 4; ++b2) t[a][b2] = 0.f;
-        const int top = min(k, 4 * cg + 4);
-        for (int cc = 0; cc < top; ++cc) {
-          const float* pc = Ps + cc * ldt + 4 * rg;
-          const float pv[4] = {pc[0], pc[1], pc[2], pc[3]};
-          const float4 rr = *reinterpret_cast<const float4*>(Rs + cc * kp + 4 * cg);
-          const float rv[4] = {rr.x, rr.y, rr.z, rr.w};
+        for (int cc = 0; cc < top; cc += 4) {
+          float pv[4][4], rv[4][4];
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
+          for (int a = 0; a < 4; ++a) {
+            const float4 p4 = *reinterpret_cast<const float4*>(Pb + (4 * rg + a) * kp + cc);
+            pv[a][0] = p4.x;
+            pv[a][1] = p4.y;
+            pv[a][2] = p4.z;
+            pv[a][3] = p4.w;
+            const float4 r4 = *reinterpret_cast<const float4*>(Rs + (cc + a) * kp + 4 * cg);
+            rv[a][0] = r4.x;
+            rv[a][1] = r4.y;
+            rv[a][2] = r4.z;
+            rv[a][3] = r4.w;
+          }
 #pragma unroll
-            for (int b2 = 0; b2 < 4; ++b2) t[a][b2] = fmaf(pv[a], rv[b2], t[a][b2]);
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int b2 = 0; b2 < 4; ++b2) t[a][b2] = fmaf(pv[a][q], rv[q][b2], t[a][b2]);
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -575,17 +603,13 @@ panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __res
       }
       __syncthreads();
       src = Ts;
+      lds = ldp;
     }
     if (active) {
-      float acc[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = 0.f;
 #pragma unroll 4
-      for (int ii = grp; ii < GSUB; ii += groups) {
-        const float4 x4 = *reinterpret_cast<const float4*>(src + ii * ldp + ty * 4);
-        const float4 y4 = *reinterpret_cast<const float4*>(src + ii * ldp + tx * 4);
+      for (int ii = grp; ii < nrows; ii += groups) {
+        const float4 x4 = *reinterpret_cast<const float4*>(src + ii * lds + ty * 4);
+        const float4 y4 = *reinterpret_cast<const float4*>(src + ii * lds + tx * 4);
         const float x[4] = {x4.x, x4.y, x4.z, x4.w};
         const float y[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
@@ -593,45 +617,31 @@ panel_gram_kernel(int kp, const PanelDev* __restrict__ panels, const int2* __res
 #pragma unroll
           for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = fmaf(x[a], y[b2], acc[a][b2]);
       }
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) {  // Kahan: (hi, lo) += acc
-          const float yv = acc[a][b2] - lo[a][b2];
-          const float tv = hi[a][b2] + yv;
-          lo[a][b2] = (tv - hi[a][b2]) - yv;
-          hi[a][b2] = tv;
-        }
     }
+    __syncthreads();  // stage s and Ts consumed: stage s may be refilled
   }
-  // sum the row groups (the staging buffers are free now)
-  __syncthreads();
+  // sum the row groups (the stages are free now; every issued copy landed)
   float* Red = Ps;
   if (active && grp > 0) {
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) Red[(tid - ntiles) * 16 + a * 4 + b2] = hi[a][b2] - lo[a][b2];
+      for (int b2 = 0; b2 < 4; ++b2) Red[(tid - ntiles) * 16 + a * 4 + b2] = acc[a][b2];
   }
   __syncthreads();
   if (active && grp == 0) {
-    float out4[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) out4[a][b2] = hi[a][b2] - lo[a][b2];
     for (int g2 = 1; g2 < groups; ++g2) {
       const int t2 = (g2 - 1) * ntiles + tile;
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) out4[a][b2] += Red[t2 * 16 + a * 4 + b2];
+        for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] += Red[t2 * 16 + a * 4 + b2];
     }
     float* out = partial + (long long)blockIdx.x * kp * kp;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
       *reinterpret_cast<float4*>(out + (ty * 4 + a) * kp + tx * 4) =
-          make_float4(out4[a][0], out4[a][1], out4[a][2], out4[a][3]);
+          make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
   }
 }
 
@@ -948,15 +958,18 @@ cudaError_t launch_gram_route(int kp, int kmax, const MatDev* mats, int count,
                              (int)gsm);
   if (e != cudaSuccess) return e;
   // R1 = chol(X^T X)
-  panel_gram_kernel<<<nxc, GTHREADS, gsm, s>>>(kp, xpanels, xchunks, nullptr, partial_x);
+  panel_gram_kernel<<<nxc, GTHREADS, gsm, s>>>(kp, xpanels, xchunks, nullptr, partial_x,
+                                                status);
   chol_kernel<<<count, 256, csm, s>>>(kp, mats, xoff, partial_x, nullptr, r1, rinv, status);
   if (refine) {
     // R = chol(Q1^T Q1) R1 with Q1 = X R1^{-1}
-    panel_gram_kernel<<<nxc, GTHREADS, gsm, s>>>(kp, xpanels, xchunks, rinv, partial_x);
+    panel_gram_kernel<<<nxc, GTHREADS, gsm, s>>>(kp, xpanels, xchunks, rinv, partial_x,
+                                                  status);
     chol_kernel<<<count, 256, csm, s>>>(kp, mats, xoff, partial_x, r1, r2, rinv, status);
   }
   // G_M = (Y R^{-1})^T (Y R^{-1})
-  panel_gram_kernel<<<nyc, GTHREADS, gsm, s>>>(kp, ypanels, ychunks, rinv, partial_y);
+  panel_gram_kernel<<<nyc, GTHREADS, gsm, s>>>(kp, ypanels, ychunks, rinv, partial_y,
+                                                status);
   eig_finish_kernel<<<(count + mpc - 1) / mpc, EIG_THREADS, esm, s>>>(
       kp, ks, count, mats, yoff, partial_y, rinv, Wm, normA2, err, flags, err_mode, tau);
   return cudaGetLastError();

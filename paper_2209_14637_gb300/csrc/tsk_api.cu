@@ -492,6 +492,11 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
     memcpy(staging.data() + o_yoff, yoff.data(), sizeof(int) * (count + 1));
   }
   ce = cudaMemcpy(p->ws, staging.data(), host_part, cudaMemcpyHostToDevice);
+  // The X and Y panels start zeroed: the kernels write columns < k (the
+  // tensor-core kernel: < k rounded up to 8) and never the rest, which the
+  // Gram kernel reads as zeros.
+  if (ce == cudaSuccess) ce = cudaMemset(base + o_X, 0, cs * offX);
+  if (ce == cudaSuccess) ce = cudaMemset(base + o_Y, 0, cs * offY);
   if (ce != cudaSuccess) {
     set_err(h, "plan upload: %s", cudaGetErrorString(ce));
     plan_free(p);
