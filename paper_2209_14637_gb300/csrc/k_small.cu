@@ -737,15 +737,19 @@ chol_kernel(int kp, const MatDev* __restrict__ mats, const int* __restrict__ chu
   }
 }
 
-// eig_finish_kernel: CTAs of EIG_THREADS threads; each holds EIG_THREADS /
-// ks matrices (ks = the largest k of the batch, <= EIG_KMAX), one thread per
-// column.
+// eig_finish_kernel: each matrix slot has 2 ks threads (ks = the largest k of
+// the batch, <= EIG_KMAX), two per column; a CTA holds max(1, 128 / (2 ks))
+// slots.
 constexpr int EIG_KMAX = 48;
-constexpr int EIG_THREADS = 128;
 // Shared memory of one matrix slot: G and two buffers of B columns
-// (ks x (ks + 1) floats each), eigenvalues and their order.
+// (ks x (ks + 1) floats each), eigenvalues, their order and the slot's
+// energy parts.
 __host__ __device__ constexpr size_t eig_slot_bytes(int ks) {
-  return (size_t)3 * ks * (ks + 1) * sizeof(float) + (size_t)ks * (sizeof(float) + sizeof(int));
+  return (size_t)3 * ks * (ks + 1) * sizeof(float) + (size_t)ks * (sizeof(float) + sizeof(int)) +
+         (size_t)2 * ks * sizeof(double);
+}
+__host__ __device__ constexpr size_t eig_slot_stride(int ks) {  // 16-byte multiple
+  return (eig_slot_bytes(ks) + 15) / 16 * 16;
 }
 
 // Partner of column j in round `round` of the round-robin order on kk = 2 m'
@@ -764,32 +768,40 @@ __device__ __forceinline__ int rr_partner(int round, int j, int mm) {
 // make the columns of B mutually orthogonal leave B = G_M V = V Lambda, so
 // the column norms are the eigenvalues and the normalised columns the
 // eigenvectors (whose errors reach the captured energy, a Rayleigh quotient,
-// only at second order).  Thread j keeps column j of B in registers; each
-// round of the parallel round-robin order it reads its partner's column
-// from shared memory (double-buffered, one barrier per round), and both
-// threads of a pair compute the same rotation from the same three dot
-// products.  Then V_r is brought back to orthonormal with one step
-// V <- V (I - (V^T V - I) / 2); the captured energy tr(V_r^T G_M V_r) (Ky
-// Fan: sum_{i<=r} lambda_i up to second-order terms) gives
-// err^2 = ||A||^2 - energy; sigma = sqrt(lambda) and W = R_X^{-1} V_r.
-// Arithmetic is FP32 (the partial Grams are FP32 sums already); per-thread
-// parts of the energy are added in FP64.
-__global__ void __launch_bounds__(EIG_THREADS)
+// only at second order).  Two adjacent threads keep the two halves of
+// column j of B in registers (HMAX >= ceil(k / 2) rows each); each round of
+// the parallel round-robin order they read their halves of the partner
+// column from shared memory (double-buffered, one barrier per round), add
+// their partial dot products with one shuffle, and all four threads of a
+// pair of columns compute the same rotation from the same three sums.  Then
+// V_r is brought back to orthonormal with one step V <- V (I - (V^T V - I) / 2);
+// the captured energy tr(V_r^T G_M V_r) (Ky Fan: sum_{i<=r} lambda_i up to
+// second-order terms) gives err^2 = ||A||^2 - energy; sigma = sqrt(lambda)
+// and W = R_X^{-1} V_r.  Arithmetic is FP32 (the partial Grams are FP32
+// sums already); the energy's per-thread parts are added in FP64.
+template <int HMAX>
+__global__ void __launch_bounds__(128, 4)
 eig_finish_kernel(int kp, int ks, int count, const MatDev* __restrict__ mats,
                   const int* __restrict__ chunk_off, const float* __restrict__ partial,
                   const float* __restrict__ rinv, float* __restrict__ Wm,
                   const double* __restrict__ normA2, double* __restrict__ err,
                   int* __restrict__ flags, int err_mode, double tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int tid = threadIdx.x, mpc = EIG_THREADS / ks;
-  const int slot = tid / ks, j = tid % ks;  // this thread: column j of slot's matrix
+  const unsigned full = 0xffffffffu;
+  const int tid = threadIdx.x, per = 2 * ks;
+  const int mpc = max(1, 128 / per);
+  const int slot = tid / per, q = tid % per;  // q: thread within the slot
+  const int j = q >> 1, half = q & 1;         // column j, rows of this half
   const int b = blockIdx.x * mpc + slot;
   const bool live = slot < mpc && b < count;
   const int ld = ks + 1, plane = ks * ld;
-  float* Gs = (float*)(smem_raw + (size_t)min(slot, mpc - 1) * eig_slot_bytes(ks));
-  float* Bs = Gs + plane;        // 2 planes: column j at Bs[buf * plane + j * ld]
-  float* lam = Bs + 2 * plane;   // ks
-  int* order = (int*)(lam + ks); // ks
+  unsigned char* base = smem_raw + (size_t)min(slot, mpc - 1) * eig_slot_stride(ks);
+  float* Gs = (float*)base;            // G_M, row-major
+  float* Bs = Gs + plane;              // 2 planes: column j at Bs[buf * plane + j * ld]
+  float* lam = Bs + 2 * plane;         // ks
+  int* order = (int*)(lam + ks);       // ks
+  double* acc = (double*)(base + ((size_t)3 * plane * sizeof(float) +
+                                  (size_t)ks * (sizeof(float) + sizeof(int)) + 7) / 8 * 8);
   MatDev md;
   int k = 0, r = 0;
   if (live) {
@@ -797,49 +809,50 @@ eig_finish_kernel(int kp, int ks, int count, const MatDev* __restrict__ mats,
     k = md.k;
     r = md.r;
     const int c0 = chunk_off[b], c1 = chunk_off[b + 1];
-    for (int e = j; e < k * k; e += ks) {
-      const int i = e / k, c = e % k;
+    for (int e = q; e < k * k; e += per) {
+      const int i = e / k, c = e - i * k;
       const int a = min(i, c), bb = max(i, c);  // partials hold the upper triangle
       float g = 0.f;
-      for (int q = c0; q < c1; ++q) g += partial[(long long)q * kp * kp + a * kp + bb];
+      for (int t = c0; t < c1; ++t) g += partial[(long long)t * kp * kp + a * kp + bb];
       Gs[i * ld + c] = g;
     }
   }
   __syncthreads();
-  float bc[EIG_KMAX];
+  const int hr = (k + 1) >> 1;          // rows per half
+  const int r0h = half * hr;            // first row of this half
+  const int nh = max(0, min(hr, k - r0h));  // rows of this half
+  float bc[HMAX];
 #pragma unroll
-  for (int i = 0; i < EIG_KMAX; ++i) bc[i] = (j < k && i < k) ? Gs[i * ld + j] : 0.f;
+  for (int i = 0; i < HMAX; ++i) bc[i] = (j < k && i < nh) ? Gs[(r0h + i) * ld + j] : 0.f;
   const int kk = k + (k & 1), mm = kk - 1;
-  int t = 0;  // rounds so far: selects the buffer
+  const int rounds = ks + (ks & 1) - 1;  // of the largest k in the CTA
+  int t = 0;                             // rounds so far: selects the buffer
   for (int sweep = 0; sweep < 12; ++sweep) {
     int rot = 0;
-    // every slot runs the rounds of the largest k in the CTA (barriers are
-    // CTA-wide); a slot whose own rounds are done idles through the rest
-    for (int round = 0; round < ks + (ks & 1) - 1; ++round, ++t) {
+    for (int round = 0; round < rounds; ++round, ++t) {
       float* Bb = Bs + (t & 1) * plane;
       if (j < k && round < mm) {
 #pragma unroll
-        for (int i = 0; i < EIG_KMAX; ++i)
-          if (i < k) Bb[j * ld + i] = bc[i];
+        for (int i = 0; i < HMAX; ++i)
+          if (i < nh) Bb[j * ld + r0h + i] = bc[i];
       }
       __syncthreads();
-      const int pj = (round < mm) ? rr_partner(round, j, mm) : k;
-      if (j < k && pj < k) {
-        const float* pb = Bb + pj * ld;
-        float y[EIG_KMAX];
-        float aa0 = 0.f, aa1 = 0.f, pp0 = 0.f, pp1 = 0.f, ap0 = 0.f, ap1 = 0.f;
+      const int pj = (j < k && round < mm) ? rr_partner(round, j, mm) : k;
+      if (pj < k) {  // both threads of the column take this branch together
+        const float* pb = Bb + pj * ld + r0h;
+        float y[HMAX];
+        float aa = 0.f, pp = 0.f, ap = 0.f;
 #pragma unroll
-        for (int i = 0; i < EIG_KMAX; i += 2) {
-          y[i] = (i < k) ? pb[i] : 0.f;
-          y[i + 1] = (i + 1 < k) ? pb[i + 1] : 0.f;
-          aa0 = fmaf(bc[i], bc[i], aa0);
-          pp0 = fmaf(y[i], y[i], pp0);
-          ap0 = fmaf(bc[i], y[i], ap0);
-          aa1 = fmaf(bc[i + 1], bc[i + 1], aa1);
-          pp1 = fmaf(y[i + 1], y[i + 1], pp1);
-          ap1 = fmaf(bc[i + 1], y[i + 1], ap1);
+        for (int i = 0; i < HMAX; ++i) {
+          y[i] = (i < nh) ? pb[i] : 0.f;
+          aa = fmaf(bc[i], bc[i], aa);
+          pp = fmaf(y[i], y[i], pp);
+          ap = fmaf(bc[i], y[i], ap);
         }
-        const float aa = aa0 + aa1, pp = pp0 + pp1, ap = ap0 + ap1;
+        const unsigned m2 = 3u << (threadIdx.x & 30);  // this column's two lanes
+        aa += __shfl_xor_sync(m2, aa, 1);
+        pp += __shfl_xor_sync(m2, pp, 1);
+        ap += __shfl_xor_sync(m2, ap, 1);
         const bool low = j < pj;  // the lower index is p of the pair (p, q)
         const float alpha = low ? aa : pp, beta = low ? pp : aa, gamma = ap;
         if (fabsf(gamma) > 4.0e-6f * sqrtf(alpha * beta) && fabsf(gamma) > 1.0e-30f) {
@@ -849,45 +862,50 @@ eig_finish_kernel(int kp, int ks, int count, const MatDev* __restrict__ mats,
           // [b_p b_q] <- [c b_p - s b_q, s b_p + c b_q]
           const float cp = low ? -sn : sn;
 #pragma unroll
-          for (int i = 0; i < EIG_KMAX; ++i) bc[i] = fmaf(c, bc[i], cp * y[i]);
+          for (int i = 0; i < HMAX; ++i) bc[i] = fmaf(c, bc[i], cp * y[i]);
           rot = 1;
         }
       }
     }
     if (!__syncthreads_or(rot)) break;
   }
+  (void)full;
   // eigenvalues = column norms; normalised columns = eigenvectors (plane 0)
   float* Vs = Bs;           // column j at Vs[j * ld + i]
   float* Vc = Bs + plane;   // corrected V_r, column c at Vc[c * ld + i]
-  if (j < k) {
+  {
     float nn = 0.f;
 #pragma unroll
-    for (int i = 0; i < EIG_KMAX; ++i) nn = fmaf(bc[i], bc[i], nn);
-    const float l = sqrtf(nn);
-    lam[j] = l;
-    const float inv = l > 1.0e-30f ? 1.f / l : 0.f;
+    for (int i = 0; i < HMAX; ++i) nn = fmaf(bc[i], bc[i], nn);
+    nn += __shfl_xor_sync(0xffffffffu, nn, 1);
+    if (j < k) {
+      const float l = sqrtf(nn);
+      if (half == 0) lam[j] = l;
+      const float inv = l > 1.0e-30f ? 1.f / l : 0.f;
 #pragma unroll
-    for (int i = 0; i < EIG_KMAX; ++i)
-      if (i < k) Vs[j * ld + i] = (inv > 0.f) ? bc[i] * inv : (i == j ? 1.f : 0.f);
+      for (int i = 0; i < HMAX; ++i)
+        if (i < nh) Vs[j * ld + r0h + i] = (inv > 0.f) ? bc[i] * inv : (r0h + i == j ? 1.f : 0.f);
+    }
   }
   __syncthreads();
-  if (j < k) {  // descending eigenvalues
+  for (int c = q; c < k; c += per) {  // descending eigenvalues
     int rank = 0;
-    for (int c2 = 0; c2 < k; ++c2) rank += (lam[c2] > lam[j]) || (lam[c2] == lam[j] && c2 < j);
-    order[rank] = j;
+    for (int c2 = 0; c2 < k; ++c2) rank += (lam[c2] > lam[c]) || (lam[c2] == lam[c] && c2 < c);
+    order[rank] = c;
   }
   __syncthreads();
-  if (live && md.sigma != nullptr && j < k) ((float*)md.sigma)[j] = sqrtf(lam[order[j]]);
+  if (live && md.sigma != nullptr)
+    for (int c = q; c < k; c += per) ((float*)md.sigma)[c] = sqrtf(lam[order[c]]);
   // column c < r of V_r (E = V_r^T V_r - I, then V_r <- V_r - V_r E / 2)
-  if (j < r) {
-    const float* vc = Vs + order[j] * ld;
+  for (int c = q; c < r; c += per) {
+    const float* vc = Vs + order[c] * ld;
     float e[EIG_KMAX];
 #pragma unroll
     for (int a = 0; a < EIG_KMAX; ++a) {
       float s2 = 0.f;
       if (a < r) {
         const float* va = Vs + order[a] * ld;
-        s2 = (a == j) ? -1.f : 0.f;
+        s2 = (a == c) ? -1.f : 0.f;
         for (int i = 0; i < k; ++i) s2 = fmaf(va[i], vc[i], s2);
       }
       e[a] = s2;
@@ -897,7 +915,7 @@ eig_finish_kernel(int kp, int ks, int count, const MatDev* __restrict__ mats,
 #pragma unroll
       for (int a = 0; a < EIG_KMAX; ++a)
         if (a < r) s2 = fmaf(Vs[order[a] * ld + i], e[a], s2);
-      Vc[j * ld + i] = fmaf(-0.5f, s2, vc[i]);
+      Vc[c * ld + i] = fmaf(-0.5f, s2, vc[i]);
     }
   }
   __syncthreads();
@@ -906,33 +924,58 @@ eig_finish_kernel(int kp, int ks, int count, const MatDev* __restrict__ mats,
   if (live) {
     const float* Ri = rinv + (long long)b * kp * kp;
     float* Wout = Wm + (long long)b * kp * kp;
-    for (int i = j; i < kp; i += ks) {
+    for (int i = q; i < kp; i += per) {
       for (int c = 0; c < kp; ++c) {
         float w = 0.f;
         if (i < k && c < r) {
           const float* v = Vc + c * ld;
           float gv = 0.f;
-          for (int q = 0; q < k; ++q) gv = fmaf(Gs[i * ld + q], v[q], gv);
+          for (int qq = 0; qq < k; ++qq) gv = fmaf(Gs[i * ld + qq], v[qq], gv);
           part += (double)v[i] * (double)gv;
-          for (int q = i; q < k; ++q) w = fmaf(Ri[i * kp + q], v[q], w);  // R_X^{-1} upper
+          for (int qq = i; qq < k; ++qq) w = fmaf(Ri[i * kp + qq], v[qq], w);  // R_X^{-1} upper
         }
         Wout[i * kp + c] = w;
       }
     }
   }
-  // per-slot sums: lanes of a slot may span warps, so go through shared memory
+  if (slot < mpc) acc[q] = part;
   __syncthreads();
-  double* acc = (double*)Gs;  // the slot's G is no longer needed: ks doubles fit in it
-  if (slot < mpc) acc[j] = part;
-  __syncthreads();
-  if (live && j == 0) {
+  if (live && q == 0) {
     double energy = 0.0;
-    for (int q = 0; q < ks; ++q) energy += acc[q];
+    for (int qq = 0; qq < per; ++qq) energy += acc[qq];
     const double tot = normA2[b];
     const double e2 = tot - energy;
     err[b] = sqrt(e2 > 0.0 ? e2 : 0.0);
     flags[b] = (err_mode == 2) || (err_mode == 0 && e2 < tau * tot);
   }
+}
+
+// Launch shape of eig_finish_kernel for the largest k of a batch.
+struct EigShape {
+  int ks, mpc, threads;
+  size_t smem;
+};
+EigShape eig_shape(int kmax) {
+  EigShape e;
+  e.ks = std::max(1, std::min(kmax, EIG_KMAX));
+  const int per = 2 * e.ks;
+  e.mpc = std::max(1, 128 / per);
+  e.threads = (e.mpc * per + 31) / 32 * 32;
+  e.smem = (size_t)e.mpc * eig_slot_stride(e.ks);
+  return e;
+}
+
+template <int HMAX>
+cudaError_t launch_eig_finish(const EigShape& es, int kp, int count, const MatDev* mats,
+                              const int* yoff, const float* partial_y, const float* rinv,
+                              float* Wm, double* normA2, double* err, int* flags, int err_mode,
+                              double tau, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(eig_finish_kernel<HMAX>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)es.smem);
+  if (e != cudaSuccess) return e;
+  eig_finish_kernel<HMAX><<<(count + es.mpc - 1) / es.mpc, es.threads, es.smem, s>>>(
+      kp, es.ks, count, mats, yoff, partial_y, rinv, Wm, normA2, err, flags, err_mode, tau);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gram_route(int kp, int kmax, const MatDev* mats, int count,
@@ -946,13 +989,8 @@ cudaError_t launch_gram_route(int kp, int kmax, const MatDev* mats, int count,
   if (count <= 0) return cudaSuccess;
   const size_t gsm = panel_gram_smem(kp);
   const size_t csm = (size_t)3 * kp * (kp + 1) * sizeof(float);
-  const int ks = std::max(1, std::min(kmax, EIG_KMAX));
-  const int mpc = EIG_THREADS / ks;
-  const size_t esm = (size_t)mpc * eig_slot_bytes(ks);
-  cudaError_t e = cudaFuncSetAttribute(eig_finish_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+  cudaError_t e = cudaSuccess;
+  e = cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(panel_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)gsm);
@@ -970,9 +1008,25 @@ cudaError_t launch_gram_route(int kp, int kmax, const MatDev* mats, int count,
   // G_M = (Y R^{-1})^T (Y R^{-1})
   panel_gram_kernel<<<nyc, GTHREADS, gsm, s>>>(kp, ypanels, ychunks, rinv, partial_y,
                                                 status);
-  eig_finish_kernel<<<(count + mpc - 1) / mpc, EIG_THREADS, esm, s>>>(
-      kp, ks, count, mats, yoff, partial_y, rinv, Wm, normA2, err, flags, err_mode, tau);
-  return cudaGetLastError();
+  const EigShape es = eig_shape(kmax);
+  const int hm = (es.ks + 1) / 2;
+  if (hm <= 4)
+    return launch_eig_finish<4>(es, kp, count, mats, yoff, partial_y, rinv, Wm, normA2, err,
+                                flags, err_mode, tau, s);
+  if (hm <= 8)
+    return launch_eig_finish<8>(es, kp, count, mats, yoff, partial_y, rinv, Wm, normA2, err,
+                                flags, err_mode, tau, s);
+  if (hm <= 12)
+    return launch_eig_finish<12>(es, kp, count, mats, yoff, partial_y, rinv, Wm, normA2, err,
+                                 flags, err_mode, tau, s);
+  if (hm <= 16)
+    return launch_eig_finish<16>(es, kp, count, mats, yoff, partial_y, rinv, Wm, normA2, err,
+                                 flags, err_mode, tau, s);
+  if (hm <= 20)
+    return launch_eig_finish<20>(es, kp, count, mats, yoff, partial_y, rinv, Wm, normA2, err,
+                                 flags, err_mode, tau, s);
+  return launch_eig_finish<24>(es, kp, count, mats, yoff, partial_y, rinv, Wm, normA2, err, flags,
+                               err_mode, tau, s);
 }
 
 int gram_route_chunks(long long rows) { return (int)((rows + GCHUNK - 1) / GCHUNK); }
