@@ -203,6 +203,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+// Prefetch of one TMA box into L2 (no shared memory, no completion).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   (uint64_t)map),
+               "r"(x), "r"(y)
+               : "memory");
+}
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src,
                                           uint32_t bytes, uint32_t bar) {
   asm volatile(
@@ -464,6 +471,19 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
       int sloads = 0;
       const unsigned char* cur_img = nullptr;
       bool stop = false;
+      // L2 prefetch cursor, NST blocks ahead of the loads: a block is pulled
+      // into L2 while the stage it will occupy is still busy, so its TMA
+      // load later hits L2 instead of waiting on HBM.
+      auto nblk_of = [&](int wi) { return (int)((P.mats[P.work[wi]].n + NB - 1) / NB); };
+      int pwi = w0, pq = 0, pn = (w0 < w1) ? nblk_of(w0) : 0;
+      auto padv = [&]() {
+        if (++pq >= pn) {
+          ++pwi;
+          pq = 0;
+          pn = (pwi < w1) ? nblk_of(pwi) : 0;
+        }
+      };
+      for (int i = 0; i < NST && pwi < w1; ++i) padv();
       for (int wi = w0; wi < w1 && !stop; ++wi) {
         const int d = P.work[wi];
         const MatDev& md = P.mats[d];
@@ -492,6 +512,13 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
           for (int b = 0; b < MC / BOX_ROWS; ++b)
             tma_load_2d(sb + OFF_A + s * STAGE_BYTES + b * BOX_ROWS * 128, map, q * NB,
                         (int)(rank * MC + b * BOX_ROWS), bar(B_AFULL + s));
+          if (pwi < w1) {
+            const CUtensorMap* pmap = P.tmaps + P.work[pwi];
+#pragma unroll
+            for (int b = 0; b < MC / BOX_ROWS; ++b)
+              tma_prefetch_2d(pmap, pq * NB, (int)(rank * MC + b * BOX_ROWS));
+            padv();
+          }
         }
       }
       // Drain: every load this thread issued must land before the CTA exits.
