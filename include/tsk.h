@@ -35,9 +35,10 @@
  *     two host threads at the same time.
  *   - Requirements on sizes: 1 <= r <= k <= min(m, n) (thin QR of the n x k
  *     matrix (SA)^T needs k <= n; Theorem 1 needs k > r for its bound but
- *     r = k is accepted) and k <= TSK_MAX_K.  A and S must be 16-byte
- *     aligned and lda * element size must be a multiple of 16 bytes for the
- *     tensor-core path; the SIMT paths need only natural alignment.
+ *     r = k is accepted) and k <= TSK_MAX_K.  The tensor-core path also
+ *     needs k <= 48, m <= 4096, A and S 16-byte aligned and lda * element
+ *     size a multiple of 16 bytes; the SIMT paths need only natural
+ *     alignment.
  */
 #ifndef TSK_H_
 #define TSK_H_
@@ -66,7 +67,7 @@ typedef enum { TSK_FP64 = 0, TSK_FP32 = 1, TSK_BF16 = 2 } tsk_prec;
 
 /* Which kernels run the test-side sketch pass (X = A^T S^T and Y = A X). */
 typedef enum {
-  TSK_KERNEL_AUTO = 0, /* tensor cores for TSK_BF16, SIMT otherwise          */
+  TSK_KERNEL_AUTO = 0, /* tensor cores for TSK_BF16 when eligible, else SIMT */
   TSK_KERNEL_SIMT = 1, /* CUDA-core kernels, two passes over A               */
   TSK_KERNEL_TC = 2    /* tcgen05/TMA kernel, one pass over A (TSK_BF16 only) */
 } tsk_kernel;

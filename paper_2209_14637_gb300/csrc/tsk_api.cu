@@ -203,8 +203,11 @@ static tsk_status check_desc(tsk_handle h, const tsk_mat_desc& d, int64_t i,
   return TSK_OK;
 }
 
+// The tensor-core kernel takes k <= 48 and m <= 4096 (clusters of at most 8
+// CTAs of 512 rows) and needs 16-byte aligned rows for TMA.
 static bool tc_eligible(const tsk_mat_desc* mats, int64_t count) {
   for (int64_t i = 0; i < count; ++i) {
+    if (mats[i].k > 48 || mats[i].m > 4096) return false;
     if (((uintptr_t)mats[i].A) % 16 != 0) return false;
     if ((mats[i].lda * 2) % 16 != 0) return false;
     if (((uintptr_t)mats[i].S) % 16 != 0) return false;
@@ -279,18 +282,13 @@ static cudaError_t capture_plan(tsk_plan p, cudaEvent_t evb, cudaEvent_t eve) {
                             h->d_status, s);
     ++launches;
   } else if (ce == cudaSuccess) {
-    // FP32 / BF16: Cholesky of X^T X (+ one refinement), eigenpairs of M^T M
+    // FP32 / BF16: Cholesky of X^T X (+ one refinement), eigenpairs of M^T M,
+    // one CTA per matrix
     const PanelDev* pan = (const PanelDev*)(base + p->o_pan);
-    ce = launch_gram_route(kp, p->kmax, d_mats, count, pan, pan + count,
-                           (const int2*)(base + p->o_xch), p->nxc,
-                           (const int*)(base + p->o_xoff), (const int2*)(base + p->o_ych),
-                           p->nyc, (const int*)(base + p->o_yoff), (float*)(base + p->o_px),
-                           (float*)(base + p->o_py), (float*)(base + p->o_r1),
-                           (float*)(base + p->o_r2), (float*)(base + p->o_ri32),
-                           (float*)(base + p->o_W), d_norm, d_err,
-                           (int*)(base + p->o_flag), h->opts.err_mode, tau,
-                           h->opts.refine_q ? 1 : 0, h->d_status, s);
-    launches += h->opts.refine_q ? 6 : 4;
+    ce = launch_finish(kp, p->kmax, d_mats, count, pan, pan + count, (float*)(base + p->o_W),
+                       d_norm, d_err, (int*)(base + p->o_flag), h->opts.err_mode, tau,
+                       h->opts.refine_q ? 1 : 0, h->d_status, s);
+    ++launches;
   }
   if (ce == cudaSuccess && h->opts.err_mode != 1) {
     ce = cudaMemsetAsync(base + p->o_e2, 0, sizeof(double) * count, s);
@@ -360,7 +358,8 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
     const bool ok = tc_supported() && tc_eligible(mats, count);
     if (req == TSK_KERNEL_TC && !ok) {
       set_err(h, "tensor-core kernel requested but unavailable for these "
-                 "arguments (needs a GB300 and 16-byte aligned A, S, lda)");
+                 "arguments (needs a GB300, k <= 48, m <= 4096 and 16-byte aligned A, S, "
+                 "lda)");
       return TSK_EUNSUPPORTED;
     }
     use_tc = ok;

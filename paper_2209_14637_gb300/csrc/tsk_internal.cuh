@@ -123,6 +123,12 @@ cudaError_t launch_gram_route(int kp, int kmax, const MatDev* mats, int count,
                               int err_mode, double tau, int refine, int* status,
                               cudaStream_t s);
 int gram_route_chunks(long long rows);
+// Fused small factors of the FP32 / BF16 paths (k_finish.cu): one CTA per
+// matrix takes the X and Y panels to W = R_X^{-1} V_r, sigma and err.
+cudaError_t launch_finish(int kp, int kmax, const MatDev* mats, int count,
+                          const PanelDev* xpanels, const PanelDev* ypanels, float* Wm,
+                          double* normA2, double* err, int* flags, int err_mode, double tau,
+                          int refine, int* status, cudaStream_t s);
 
 // k_refine.cu
 cudaError_t launch_zt(bool dbl, int kp, const MatDev* mats, int count, const void* Y,

@@ -163,6 +163,24 @@ def test_reduced_precision_scaled(tsk, handle, storage):
     assert _gap(_np(out2["err"]), [o["err"] for o in ref]) <= 1e-2
 
 
+@pytest.mark.parametrize("storage,k", [("f32", 56), ("f32", 64), ("bf16", 64)])
+def test_reduced_precision_large_k(tsk, handle, storage, k):
+    # k up to TSK_MAX_K = 64 on the FP32 / BF16 small-factor kernel (the
+    # tensor-core sketch takes k <= 48; above it the automatic choice runs the
+    # CUDA-core sketch)
+    spec = synth.scaled(synth.C2, 320, 264, 24, 4, k=k, r=k // 2, storage=storage)
+    tr = synth.stream(spec, "train", device="cuda")
+    te = synth.stream(spec, "test", device="cuda")
+    S_o, _, _, _ = oracle.train_sketch(list(_np(tr)), k)
+    S = torch.tensor(S_o, device="cuda", dtype=torch.float32)
+    out = handle.approx_batch(te, S, k // 2, outputs=True)
+    ref = _oracle_errs(list(_np(te)), _np(S), k // 2)
+    assert _gap(_np(out["err"]), [o["err"] for o in ref]) <= GAP
+    for i in range(te.shape[0]):
+        np.testing.assert_allclose(_np(out["sigma"][i])[:k // 2], ref[i]["sigma"][:k // 2],
+                                   rtol=2e-3)
+
+
 def test_bf16_ragged_batch(tsk, handle):
     items = synth.ragged_sizes(12, m_range=(64, 600), n_range=(64, 400))
     As, Ss, rs = [], [], []
