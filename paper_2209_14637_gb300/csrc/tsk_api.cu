@@ -37,9 +37,6 @@ struct tsk_plan_s {
   size_t o_mats = 0, o_ix = 0, o_iy = 0, o_io = 0, o_pan = 0, o_X = 0, o_Y = 0,
          o_RX = 0, o_RY = 0, o_W = 0, o_flag = 0, o_U2 = 0, o_V2 = 0, o_e2 = 0;
   // Gram route (FP32 / BF16)
-  int nxc = 0, nyc = 0;
-  size_t o_xch = 0, o_ych = 0, o_xoff = 0, o_yoff = 0, o_px = 0, o_py = 0, o_r1 = 0,
-         o_r2 = 0, o_ri64 = 0, o_ri32 = 0;
   double* d_norm = nullptr;
   double* d_err = nullptr;
   cudaGraphNode_t probe_begin = nullptr, probe_end = nullptr;
@@ -417,22 +414,6 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   const size_t o_iy = cv.take(sizeof(int2) * iy.size());
   const size_t o_io = cv.take(sizeof(int4) * std::max<size_t>(1, io.size()));
   const size_t o_pan = cv.take(sizeof(PanelDev) * 2 * count);
-  // Gram route: row chunks of the X and Y panels and their partial Grams
-  std::vector<int2> xch, ych;
-  std::vector<int> xoff(count + 1, 0), yoff(count + 1, 0);
-  for (int64_t i = 0; i < count; ++i) {
-    xoff[i] = (int)xch.size();
-    for (int c = 0; c < gram_route_chunks(hm[i].n); ++c) xch.push_back(make_int2((int)i, c));
-    yoff[i] = (int)ych.size();
-    for (int c = 0; c < gram_route_chunks(hm[i].m); ++c) ych.push_back(make_int2((int)i, c));
-  }
-  xoff[count] = (int)xch.size();
-  yoff[count] = (int)ych.size();
-  const bool gram = (prec != TSK_FP64);
-  const size_t o_xch = cv.take(gram ? sizeof(int2) * xch.size() : 0);
-  const size_t o_ych = cv.take(gram ? sizeof(int2) * ych.size() : 0);
-  const size_t o_xoff = cv.take(gram ? sizeof(int) * (count + 1) : 0);
-  const size_t o_yoff = cv.take(gram ? sizeof(int) * (count + 1) : 0);
   const size_t o_X = cv.take(cs * offX);
   const size_t o_Y = cv.take(cs * offY);
   const size_t o_RX = cv.take(cs * count * kp * kp);
@@ -446,13 +427,6 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   const size_t o_V2 = cv.take(fallback ? cs * offX : 0);
   const size_t o_e2 = cv.take(sizeof(double) * count);
   const size_t host_part = o_X;  // descriptors live before X
-  const size_t kk2 = (size_t)kp * kp;
-  const size_t o_px = cv.take(gram ? sizeof(float) * kk2 * xch.size() : 0);
-  const size_t o_py = cv.take(gram ? sizeof(float) * kk2 * ych.size() : 0);
-  const size_t o_r1 = cv.take(gram ? sizeof(double) * kk2 * count : 0);
-  const size_t o_r2 = cv.take(gram ? sizeof(double) * kk2 * count : 0);
-  const size_t o_ri64 = cv.take(gram ? sizeof(double) * kk2 * count : 0);
-  const size_t o_ri32 = cv.take(gram ? sizeof(float) * kk2 * count : 0);
   p->ws_bytes = cv.off;
   cudaError_t ce = cudaMalloc(&p->ws, p->ws_bytes);
   if (ce != cudaSuccess) {
@@ -484,12 +458,6 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   memcpy(staging.data() + o_iy, iy.data(), sizeof(int2) * iy.size());
   if (!io.empty()) memcpy(staging.data() + o_io, io.data(), sizeof(int4) * io.size());
   memcpy(staging.data() + o_pan, hp.data(), sizeof(PanelDev) * 2 * count);
-  if (gram) {
-    memcpy(staging.data() + o_xch, xch.data(), sizeof(int2) * xch.size());
-    memcpy(staging.data() + o_ych, ych.data(), sizeof(int2) * ych.size());
-    memcpy(staging.data() + o_xoff, xoff.data(), sizeof(int) * (count + 1));
-    memcpy(staging.data() + o_yoff, yoff.data(), sizeof(int) * (count + 1));
-  }
   ce = cudaMemcpy(p->ws, staging.data(), host_part, cudaMemcpyHostToDevice);
   // The X and Y panels start zeroed: the kernels write columns < k (the
   // tensor-core kernel: < k rounded up to 8) and never the rest, which the
@@ -532,18 +500,6 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   p->o_U2 = o_U2;
   p->o_V2 = o_V2;
   p->o_e2 = o_e2;
-  p->nxc = (int)xch.size();
-  p->nyc = (int)ych.size();
-  p->o_xch = o_xch;
-  p->o_ych = o_ych;
-  p->o_xoff = o_xoff;
-  p->o_yoff = o_yoff;
-  p->o_px = o_px;
-  p->o_py = o_py;
-  p->o_r1 = o_r1;
-  p->o_r2 = o_r2;
-  p->o_ri64 = o_ri64;
-  p->o_ri32 = o_ri32;
   p->d_norm = d_norm;
   p->d_err = d_err;
   ce = capture_plan(p, nullptr, nullptr);

@@ -114,15 +114,6 @@ cudaError_t launch_small_svd(bool dbl, int kp, const MatDev* mats, int count,
                              cudaStream_t s);
 cudaError_t launch_sym_eig(bool dbl, const void* H, int p, void* theta,
                            void* V, cudaStream_t s);
-cudaError_t launch_gram_route(int kp, int kmax, const MatDev* mats, int count,
-                              const PanelDev* xpanels,
-                              const PanelDev* ypanels, const int2* xchunks, int nxc,
-                              const int* xoff, const int2* ychunks, int nyc, const int* yoff,
-                              float* partial_x, float* partial_y, float* r1, float* r2,
-                              float* rinv, float* Wm, double* normA2, double* err, int* flags,
-                              int err_mode, double tau, int refine, int* status,
-                              cudaStream_t s);
-int gram_route_chunks(long long rows);
 // Fused small factors of the FP32 / BF16 paths (k_finish.cu): one CTA per
 // matrix takes the X and Y panels to W = R_X^{-1} V_r, sigma and err.
 cudaError_t launch_finish(int kp, int kmax, const MatDev* mats, int count,
