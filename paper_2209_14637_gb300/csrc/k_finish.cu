@@ -108,35 +108,31 @@ __device__ void fin_gram(const FinLay& L, float* sm, uint64_t* bars, const float
   __syncthreads();
   if (tid == 0 && ok)
     for (int b = 0; b < min(FSTAGES - 1, nblk); ++b) issue(b);
-  // Gram tiles: 4 x 4 blocks of the upper triangle.  With more tiles than
-  // threads (kp = 64) a thread keeps a second tile; with fewer, several row
-  // groups share each tile and are summed at the end.
-  const int nt = kp / 4;
-  const int ntiles = nt * (nt + 1) / 2;
-  const int groups = max(1, FT / ntiles);
+  // Gram tiles: 8 x 4 blocks (8 rows, 4 columns) that meet the upper
+  // triangle (column tile j >= 2 x row tile i); several row groups share each
+  // tile when there are fewer tiles than threads and are summed at the end
+  // (the groups' tiles must fit in the stages and Ts).
+  const int nt = kp / 4;       // column tiles (and transform tiles per row)
+  const int ntr = kp / 8;      // row tiles
+  const int ntiles = ntr * nt - ntr * (ntr - 1);  // sum over i of (nt - 2 i)
+  const int room = (FSTAGES * FSB * kp + FSB * (kp + 4)) / (ntiles * 32);
+  const int groups = max(1, min(FT / ntiles, 1 + room));
   const bool active = tid < groups * ntiles;
   const int tile = tid % ntiles, grp = tid / ntiles;
-  const bool active2 = ntiles > FT && tid + FT < ntiles;  // second tile tid + FT
-  auto tile_rc = [&](int tl, int& ty_, int& tx_) {  // tile -> (ty, tx) with ty <= tx
-    int r2 = tl;
-    ty_ = 0;
-    while (r2 >= nt - ty_) {
-      r2 -= nt - ty_;
-      ++ty_;
-    }
-    tx_ = ty_ + r2;
-  };
-  int ty, tx, ty2 = 0, tx2 = 0;
-  tile_rc(tile, ty, tx);
-  if (active2) tile_rc(tid + FT, ty2, tx2);
+  int ty = 0, rem = tile;  // tile -> (ty, tx): row tile ty, column tile tx >= 2 ty
+  while (rem >= nt - 2 * ty) {
+    rem -= nt - 2 * ty;
+    ++ty;
+  }
+  const int tx = 2 * ty + rem;
   const int rg = tid / nt, cg = tid % nt;  // transform tile: rows 4 rg.., columns 4 cg..
   const bool tact = tr && rg < FSB / 4;
   const int top = min((k + 3) & ~3, 4 * cg + 4);  // R^{-1} is upper: rows < top
-  float acc[4][4], acc2[4][4];
+  float acc[8][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = acc2[a][b2] = 0.f;
+    for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = 0.f;
   for (int b = 0; b < nblk; ++b) {
     const long long gi = gb + b;
     const int s = (int)(gi % FSTAGES);
@@ -203,28 +199,17 @@ __device__ void fin_gram(const FinLay& L, float* sm, uint64_t* bars, const float
       lds = ldp;
     }
     if (active) {
-#pragma unroll 4
+#pragma unroll 2
       for (int ii = grp; ii < nrows; ii += groups) {
-        const float4 x4 = *reinterpret_cast<const float4*>(src + ii * lds + ty * 4);
+        const float4 x0 = *reinterpret_cast<const float4*>(src + ii * lds + ty * 8);
+        const float4 x1 = *reinterpret_cast<const float4*>(src + ii * lds + ty * 8 + 4);
         const float4 y4 = *reinterpret_cast<const float4*>(src + ii * lds + tx * 4);
-        const float x[4] = {x4.x, x4.y, x4.z, x4.w};
+        const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
         const float y[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 8; ++a)
 #pragma unroll
           for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = fmaf(x[a], y[b2], acc[a][b2]);
-      }
-    }
-    if (active2) {
-      for (int ii = 0; ii < nrows; ++ii) {
-        const float4 x4 = *reinterpret_cast<const float4*>(src + ii * lds + ty2 * 4);
-        const float4 y4 = *reinterpret_cast<const float4*>(src + ii * lds + tx2 * 4);
-        const float x[4] = {x4.x, x4.y, x4.z, x4.w};
-        const float y[4] = {y4.x, y4.y, y4.z, y4.w};
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b2 = 0; b2 < 4; ++b2) acc2[a][b2] = fmaf(x[a], y[b2], acc2[a][b2]);
       }
     }
     __syncthreads();  // stage s (and Ts) consumed: stage s may be refilled
@@ -233,31 +218,24 @@ __device__ void fin_gram(const FinLay& L, float* sm, uint64_t* bars, const float
   float* Red = stg;  // the row groups' tiles (stages and Ts are free now)
   if (active && grp > 0) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) Red[(tid - ntiles) * 16 + a * 4 + b2] = acc[a][b2];
+      for (int b2 = 0; b2 < 4; ++b2) Red[(tid - ntiles) * 32 + a * 4 + b2] = acc[a][b2];
   }
   __syncthreads();
   if (active && grp == 0) {
     for (int g2 = 1; g2 < groups; ++g2) {
       const int t2 = (g2 - 1) * ntiles + tile;
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] += Red[t2 * 16 + a * 4 + b2];
+        for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] += Red[t2 * 32 + a * 4 + b2];
     }
     float* G = sm + L.g;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) G[(ty * 4 + a) * L.ld + tx * 4 + b2] = acc[a][b2];
-  }
-  if (active2) {
-    float* G = sm + L.g;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) G[(ty2 * 4 + a) * L.ld + tx2 * 4 + b2] = acc2[a][b2];
+      for (int b2 = 0; b2 < 4; ++b2) G[(ty * 8 + a) * L.ld + tx * 4 + b2] = acc[a][b2];
   }
   __syncthreads();
 }
@@ -322,7 +300,7 @@ __device__ __forceinline__ int fin_partner(int round, int j, int mm) {
 
 // One CTA per matrix; HMAX >= ceil(k / 2).
 template <int HMAX>
-__global__ void __launch_bounds__(FT)
+__global__ void __launch_bounds__(FT, 4)
 finish_kernel(int kp, const MatDev* __restrict__ mats, const PanelDev* __restrict__ xpanels,
               const PanelDev* __restrict__ ypanels, float* __restrict__ Wm,
               const double* __restrict__ normA2, double* __restrict__ err,
