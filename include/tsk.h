@@ -78,8 +78,15 @@ typedef void* tsk_stream; /* cudaStream_t */
 
 typedef struct {
   int32_t kernel;     /* tsk_kernel; default TSK_KERNEL_AUTO                  */
-  int32_t refine_q;   /* 1: one refinement step on the thin QR factors of the
-                         n x k and m x k panels (default 1)                   */
+  int32_t refine_q;   /* one CholeskyQR2 / Householder refinement step on the
+                         thin QR factor of the n x k panel X = (SA)^T:
+                         0 never; 1 always; 2 (default) always on the FP64
+                         path, and on the FP32 / BF16 paths only for matrices
+                         where the first-order bound on the captured energy's
+                         change from the FP32 rounding of X^T X,
+                           u sum_{i<=r} lambda_i (sum_j ||x_j|| |W_ji|)^2,
+                         u = 2^-24, W = R^{-1} V_r, exceeds 1e-3 of the
+                         residual ||A||^2 - sum_{i<=r} lambda_i             */
   int32_t max_iter;   /* subspace-iteration cap of the eigensolver (300)      */
   int32_t err_mode;   /* how tsk_approx_batch gets ||A - B||_F:
                          0 (default): the projection identity

@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(_PKG, "libtsk.so")
 
 FP64, FP32, BF16 = 0, 1, 2
 KERNEL_AUTO, KERNEL_SIMT, KERNEL_TC = 0, 1, 2
+REFINE_NEVER, REFINE_ALWAYS, REFINE_AUTO = 0, 1, 2
 MAX_K = 64
 
 STATUS = {0: "TSK_OK", 1: "TSK_EINVAL", 2: "TSK_ENOMEM", 3: "TSK_ECUDA",
@@ -134,7 +135,7 @@ def default_options() -> Options:
 class Handle:
     """A library handle bound to the current CUDA device."""
 
-    def __init__(self, kernel: int = KERNEL_AUTO, refine_q: bool = True,
+    def __init__(self, kernel: int = KERNEL_AUTO, refine_q: int = REFINE_AUTO,
                  max_iter: int = 300, eig_tol: float = 0.0,
                  spin_limit: int = 1 << 24, err_mode: int = 0):
         lib = load_library()

@@ -3,24 +3,35 @@
 //
 // From the panels X (n x k) and Y = A X (m x k) written by the sketch pass:
 //
-//   R1   = chol(X^T X)                         (X = Q R_X; kappa(X) modest)
-//   R2   = chol(Q1^T Q1),  Q1 = X R1^{-1}      (one CholeskyQR2 step)
-//   R_X  = R2 R1,  R_X^{-1} = R1^{-1} R2^{-1}
-//   G_M  = M^T M,  M = Y R_X^{-1} = A Q        (m x k, well conditioned)
+//   R1   = chol(X^T X)                        (X = Q R_X)
+//   Q1   = X R1^{-1},  M1 = Y R1^{-1}         (one streaming pass over both)
+//   R2   = chol(Q1^T Q1)                      (one CholeskyQR2 step)
+//   G_M  = R2^{-T} (M1^T M1) R2^{-1} = M^T M,  M = Y R_X^{-1} = A Q,
+//          R_X = R2 R1
 //   sigma_i(AQ)^2 = lambda_i(G_M),  V = eigenvectors,  W = R_X^{-1} V_r
 //   err^2 = ||A||^2 - sum_{i<=r} v_i^T G_M v_i (Eq. A.3; Ky Fan)
 //
 // Y itself is never factored: its columns scale like sigma_i^2 and Y^T Y
-// would lose everything in FP32.  Each panel streams through shared memory
-// in blocks of FSB rows (a block is one contiguous run: the panels have
-// leading dimension kp), brought in by one thread with bulk copies FSTAGES-1
-// blocks ahead; the Gram is accumulated in FP32 4 x 4 register tiles; the
-// k x k steps run in FP32 in shared memory.  Eigenpairs come from one-sided
-// (Hestenes) Jacobi on B = G_M with two threads per column (see the Jacobi
-// section below).  Keeping a matrix's whole chain in one CTA removes the
-// launches between the steps and the round trips of partial Grams through
-// global memory; the SM interleaves the FMA-bound streaming of some CTAs
-// with the latency-bound k x k steps of others.
+// would lose everything in FP32.  M1 = A Q1 is as well conditioned as A Q,
+// and R2 is within rounding of the identity, so applying it in k x k space
+// costs no accuracy.
+//
+// Streaming: each panel passes through shared memory in blocks of FSB rows
+// (16-byte cp.async copies, NST - 1 blocks in flight) into padded rows of
+// k_c + 4 floats, so eight consecutive rows fall in eight different 16-byte
+// bank groups.  For the transform P R^{-1} (R^{-1} upper), warp w
+// computes the output column tiles w and n4 - 1 - w of one row per lane, so
+// every lane takes the same n4 + 1 steps and every R^{-1} load is a
+// broadcast.  The Gram is accumulated in 8 x 4 register tiles by several
+// row groups.
+//
+// Eigenpairs: G_M = R_M^T R_M (Cholesky), then one-sided (Hestenes) Jacobi on
+// L = R_M^T.  Rotations that make the columns of L orthogonal give
+// L V = U Sigma with G_M = U Sigma^2 U^T: the column norms are the sigma_i,
+// the normalised columns the eigenvectors, and nothing is accumulated.
+// Jacobi on L needs fewer sweeps than Jacobi on G_M (L^T L = R_M R_M^T is
+// one step of the QR iteration further along).  Four threads hold a column
+// in registers.
 #include <stdint.h>
 
 #include <algorithm>
@@ -31,479 +42,658 @@ namespace tsk {
 
 namespace {
 
-constexpr int FT = 128;       // threads per CTA
-constexpr int FSB = 32;       // rows per streamed block
-constexpr int FSTAGES = 3;    // blocks in flight
-constexpr long long FWAIT_NS = 4000000000ll;  // bound on one wait for a block
+constexpr int FT = 256;                       // threads per CTA
+constexpr int FW = FT / 32;                   // warps
+constexpr int FSB = 32;                       // rows per streamed block (one per lane)
+constexpr int NST = 4;                        // stages: NST - 1 blocks in flight
 
-// Shared-memory layout (offsets in floats, kp = k rounded up to 16 <= 64).
+// Rows per quarter of a Jacobi column (a multiple of 4) for compute width kc.
+__host__ __device__ constexpr int fin_quarter(int kc) { return (((kc + 3) / 4) + 3) & ~3; }
+
+// Shared-memory layout, offsets in floats; kcm = the batch's largest k
+// rounded up to 8 (<= 64).  Sizes follow kcm, strides a matrix's own k_c.
 struct FinLay {
-  int kp, ld;  // ld = kp + 1 for the k x k work arrays
-  int ri;      // R^{-1} of the current transform, kp x kp (row stride kp)
-  int stg;     // FSTAGES blocks of FSB x kp
-  int ts;      // one transformed block, FSB x (kp + 4)
-  int g;       // Gram / Cholesky workspace, kp x ld
-  int rf;      // second k x k workspace, kp x ld
-  int bars;    // byte offset of FSTAGES mbarriers
+  int kcm;
+  int ri;     // R^{-1} of the transform, later R_X^{-1}: kcm x kcm
+  int ga;     // Gram / Cholesky workspace kept across passes: kcm x (kcm + 1)
+  int dv;     // 64 reciprocals of Cholesky diagonals
+  int dx;     // 64 column norms of X
+  int red;    // 2 FW + 2 doubles: block reductions and a broadcast slot
+  int area;   // streaming stages and the block buffer; reused between passes
+  int stage;  // floats per stage: FSB x (kcm + 4)
   size_t bytes;
 };
 
-__host__ __device__ inline FinLay fin_layout(int kp) {
+FinLay fin_layout(int kcm) {
   FinLay L;
-  L.kp = kp;
-  L.ld = kp + 1;
+  L.kcm = kcm;
+  const int gld = kcm + 1, jl = 4 * fin_quarter(kcm) + 4;
+  const int g4 = (kcm * gld + 3) & ~3;
   int o = 0;
   L.ri = o;
-  o += kp * kp;
-  L.stg = o;
-  o += FSTAGES * FSB * kp;
-  L.ts = o;
-  o += FSB * (kp + 4);
-  L.g = o;
-  o += kp * (kp + 1);
-  L.rf = o;
-  o += kp * (kp + 1);
-  o = (o + 1) & ~1;
-  L.bars = o * 4;
-  L.bytes = (size_t)o * 4 + FSTAGES * sizeof(uint64_t);
+  o += kcm * kcm;
+  L.ga = o;
+  o += g4;
+  L.dv = o;
+  o += 64;
+  L.dx = o;
+  o += 64;
+  L.red = o;  // a multiple of 4 floats: doubles align
+  o += 4 * FW + 4;
+  L.area = o;
+  L.stage = FSB * (kcm + 4);
+  // what the area holds between the passes
+  const int p5 = g4 + 2 * kcm * kcm;             // M1^T M1, R2^{-1}, product
+  const int jac = g4 + 2 * kcm * jl + 2 * kcm;   // R_M, planes, lam, order
+  o += std::max((NST + 1) * L.stage, std::max(p5, jac));
+  L.bytes = (size_t)o * 4;
   return L;
 }
 
-__device__ __forceinline__ uint64_t fin_timer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Upper triangle (4 x 4 tiles) of the Gram of a panel P (rows x kp, columns
-// >= k zero) or of P R^{-1} (tr; R^{-1} upper in sm + L.ri) into sm + L.g
-// (row stride L.ld).  gb counts the blocks streamed so far by this CTA, so
-// the stage and the mbarrier parity of every block follow from it.
-__device__ void fin_gram(const FinLay& L, float* sm, uint64_t* bars, const float* P,
-                         long long rows, int k, bool tr, long long& gb, int* status,
-                         bool& ok) {
-  const int kp = L.kp, tid = threadIdx.x;
-  float* stg = sm + L.stg;
-  float* Ts = sm + L.ts;
-  const float* Rs = sm + L.ri;
-  const int blk = FSB * kp, ldp = kp + 4;
-  const int nblk = (int)((rows + FSB - 1) / FSB);
-  auto bar = [&](int s) { return (uint32_t)__cvta_generic_to_shared(bars + s); };
-  auto issue = [&](int b) {  // thread 0: block b of this panel
-    const int s = (int)((gb + b) % FSTAGES);
-    const long long s0 = (long long)b * FSB;
-    const uint32_t bytes = (uint32_t)(min((long long)FSB, rows - s0) * kp * sizeof(float));
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(s)),
-                 "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-        "[%3];" ::"r"((uint32_t)__cvta_generic_to_shared(stg + s * blk)),
-        "l"(P + s0 * kp), "r"(bytes), "r"(bar(s))
-        : "memory");
+__device__ __forceinline__ float4 ld4(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+
+__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+
+__device__ __forceinline__ void cp16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One or two panels streamed back to back; the upper triangle (8 x 4 tiles,
+// row stride kc + 1) of the Gram of each panel P, or of P R^{-1}, goes to
+// the panel's target once its last block is in.
+struct FinPass {
+  const float *P0, *P1;
+  long long rows0, rows1;
+  float *out0, *out1;
+  int nseg;
+};
+
+// The area is free on entry (a barrier precedes its reuse); a target in the
+// area is written only after the last block.
+__device__ __forceinline__ void fin_stream(const FinLay& L, float* sm, int kc, int kp,
+                                           const FinPass& S, bool tr) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int srow = kc + 4, ldo = kc + 1, n4 = kc / 4;
+  float* area = sm + L.area;
+  float* Ts = area + NST * L.stage;
+  const float* RI = sm + L.ri;
+  const int nb0 = (int)((S.rows0 + FSB - 1) / FSB);
+  const int nb = nb0 + (S.nseg > 1 ? (int)((S.rows1 + FSB - 1) / FSB) : 0);
+  auto block_rows = [&](int bi, int& seg, long long& r0) {
+    seg = bi < nb0 ? 0 : 1;
+    r0 = (long long)(bi - (seg ? nb0 : 0)) * FSB;
+    return (int)min((long long)FSB, (seg ? S.rows1 : S.rows0) - r0);
   };
-  // Earlier generic writes to the stages (scratch) are ordered before the
-  // bulk copies that overwrite them.
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  auto issue = [&](int bi) {  // every thread: its 16-byte pieces of block bi
+    if (bi < nb) {
+      int seg;
+      long long r0;
+      const int nrows = block_rows(bi, seg, r0);
+      const float* P = (seg ? S.P1 : S.P0) + r0 * kp;
+      float* dst = area + (bi % NST) * L.stage;
+      for (int e = tid; e < FSB * 16; e += FT) {  // (row, quad) = (e / 16, e % 16)
+        const int row = e >> 4, c4 = e & 15;
+        if (row < nrows && c4 < n4) cp16(dst + row * srow + 4 * c4, P + row * kp + 4 * c4);
+      }
+    }
+    cp_commit();  // one group per block, empty ones included
+  };
   __syncthreads();
-  if (tid == 0 && ok)
-    for (int b = 0; b < min(FSTAGES - 1, nblk); ++b) issue(b);
-  // Gram tiles: 8 x 4 blocks (8 rows, 4 columns) that meet the upper
-  // triangle (column tile j >= 2 x row tile i); several row groups share each
-  // tile when there are fewer tiles than threads and are summed at the end
-  // (the groups' tiles must fit in the stages and Ts).
-  const int nt = kp / 4;       // column tiles (and transform tiles per row)
-  const int ntr = kp / 8;      // row tiles
-  const int ntiles = ntr * nt - ntr * (ntr - 1);  // sum over i of (nt - 2 i)
-  const int room = (FSTAGES * FSB * kp + FSB * (kp + 4)) / (ntiles * 32);
-  const int groups = max(1, min(FT / ntiles, 1 + room));
+  for (int bi = 0; bi < NST - 1; ++bi) issue(bi);
+  // Gram tiles (ty, tx) of 8 rows x 4 columns meeting the upper triangle
+  // (tx >= 2 ty); `groups` row groups share each tile.
+  const int n8 = kc / 8;
+  const int ntiles = n8 * n4 - n8 * (n8 - 1);  // sum over ty of (n4 - 2 ty)
+  const int groups = max(1, min(FT / ntiles, 8));
   const bool active = tid < groups * ntiles;
   const int tile = tid % ntiles, grp = tid / ntiles;
-  int ty = 0, rem = tile;  // tile -> (ty, tx): row tile ty, column tile tx >= 2 ty
-  while (rem >= nt - 2 * ty) {
-    rem -= nt - 2 * ty;
+  int ty = 0, rem = tile;
+  while (rem >= n4 - 2 * ty) {
+    rem -= n4 - 2 * ty;
     ++ty;
   }
   const int tx = 2 * ty + rem;
-  const int rg = tid / nt, cg = tid % nt;  // transform tile: rows 4 rg.., columns 4 cg..
-  const bool tact = tr && rg < FSB / 4;
-  const int top = min((k + 3) & ~3, 4 * cg + 4);  // R^{-1} is upper: rows < top
+  const int npairs = n4 / 2;
   float acc[8][4];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = 0.f;
-  for (int b = 0; b < nblk; ++b) {
-    const long long gi = gb + b;
-    const int s = (int)(gi % FSTAGES);
-    if (tid == 0 && ok && b + FSTAGES - 1 < nblk) issue(b + FSTAGES - 1);  // stage freed
-    if (ok) {
-      const uint32_t parity = (uint32_t)((gi / FSTAGES) & 1);
-      const uint64_t t0 = fin_timer();
-      for (;;) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar(s)), "r"(parity)
-            : "memory");
-        if (done) break;
-        if ((long long)(fin_timer() - t0) > FWAIT_NS) {
-          atomicOr(status, kStatusTimeout);
-          ok = false;
-          break;
-        }
-      }
-    }
-    const float* Pb = stg + s * blk;
-    const int nrows = (int)min((long long)FSB, rows - (long long)b * FSB);
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+  cp_wait<NST - 2>();  // this thread's pieces of block 0 have landed
+  __syncthreads();
+  for (int bi = 0; bi < nb; ++bi) {
+    issue(bi + NST - 1);  // into the stage block bi - 1 used
+    int seg;
+    long long r0;
+    const int nrows = block_rows(bi, seg, r0);
+    const float* Pb = area + (bi % NST) * L.stage;
     const float* src = Pb;
-    int lds = kp;
     if (tr) {
-      if (tact) {  // 4 x 4 tile of Pb R^{-1}, four rows of R^{-1} per step
-        float t[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b2 = 0; b2 < 4; ++b2) t[a][b2] = 0.f;
-        for (int cc = 0; cc < top; cc += 4) {
-          float pv[4][4], rv[4][4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            const float4 p4 = *reinterpret_cast<const float4*>(Pb + (4 * rg + a) * kp + cc);
-            pv[a][0] = p4.x;
-            pv[a][1] = p4.y;
-            pv[a][2] = p4.z;
-            pv[a][3] = p4.w;
-            const float4 r4 = *reinterpret_cast<const float4*>(Rs + (cc + a) * kp + 4 * cg);
-            rv[a][0] = r4.x;
-            rv[a][1] = r4.y;
-            rv[a][2] = r4.z;
-            rv[a][3] = r4.w;
+      if (warp < npairs) {
+        // row `lane` of Pb R^{-1}: column tile cg (R^{-1} rows < 4 cg + 4)
+        // and column tile c2 = n4 - 1 - cg (rows < 4 c2 + 4); n4 + 1 steps
+        // of four rows for every warp
+        const int cg = warp, c2 = n4 - 1 - warp;
+        const float* prow = Pb + lane * srow;
+        float* trow = Ts + lane * srow;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          const int c = h ? c2 : cg;
+          float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+#pragma unroll 2
+          for (int q = 0; q <= c; ++q) {
+            const float4 p = ld4(prow + 4 * q);
+            const float* rr = RI + (4 * q) * kc + 4 * c;
+            const float4 e0 = ld4(rr), e1 = ld4(rr + kc), e2 = ld4(rr + 2 * kc),
+                         e3 = ld4(rr + 3 * kc);
+            t0 = fmaf(p.x, e0.x, t0);
+            t1 = fmaf(p.x, e0.y, t1);
+            t2 = fmaf(p.x, e0.z, t2);
+            t3 = fmaf(p.x, e0.w, t3);
+            t0 = fmaf(p.y, e1.x, t0);
+            t1 = fmaf(p.y, e1.y, t1);
+            t2 = fmaf(p.y, e1.z, t2);
+            t3 = fmaf(p.y, e1.w, t3);
+            t0 = fmaf(p.z, e2.x, t0);
+            t1 = fmaf(p.z, e2.y, t1);
+            t2 = fmaf(p.z, e2.z, t2);
+            t3 = fmaf(p.z, e2.w, t3);
+            t0 = fmaf(p.w, e3.x, t0);
+            t1 = fmaf(p.w, e3.y, t1);
+            t2 = fmaf(p.w, e3.z, t2);
+            t3 = fmaf(p.w, e3.w, t3);
           }
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-              for (int b2 = 0; b2 < 4; ++b2) t[a][b2] = fmaf(pv[a][q], rv[q][b2], t[a][b2]);
+          st4(trow + 4 * c, t0, t1, t2, t3);
         }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-          *reinterpret_cast<float4*>(Ts + (4 * rg + a) * ldp + 4 * cg) =
-              make_float4(t[a][0], t[a][1], t[a][2], t[a][3]);
       }
       __syncthreads();
       src = Ts;
-      lds = ldp;
     }
     if (active) {
 #pragma unroll 2
       for (int ii = grp; ii < nrows; ii += groups) {
-        const float4 x0 = *reinterpret_cast<const float4*>(src + ii * lds + ty * 8);
-        const float4 x1 = *reinterpret_cast<const float4*>(src + ii * lds + ty * 8 + 4);
-        const float4 y4 = *reinterpret_cast<const float4*>(src + ii * lds + tx * 4);
-        const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-        const float y[4] = {y4.x, y4.y, y4.z, y4.w};
+        const float4 x0 = ld4(src + ii * srow + 8 * ty);
+        const float4 x1 = ld4(src + ii * srow + 8 * ty + 4);
+        const float4 y = ld4(src + ii * srow + 4 * tx);
+        const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        const float yv[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
         for (int a = 0; a < 8; ++a)
 #pragma unroll
-          for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = fmaf(x[a], y[b2], acc[a][b2]);
+          for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(xv[a], yv[c], acc[a][c]);
       }
     }
-    __syncthreads();  // stage s (and Ts) consumed: stage s may be refilled
-  }
-  gb += nblk;
-  float* Red = stg;  // the row groups' tiles (stages and Ts are free now)
-  if (active && grp > 0) {
+    cp_wait<NST - 2>();  // this thread's pieces of block bi + 1 have landed
+    __syncthreads();     // block bi (and Ts) consumed; block bi + 1 visible
+    if (bi == nb0 - 1 || bi == nb - 1) {
+      // the row groups' tiles summed in a fixed order into the target
+      float* out = seg ? S.out1 : S.out0;
+      for (int g = 0; g < groups; ++g) {
+        if (active && grp == g) {
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+          for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) Red[(tid - ntiles) * 32 + a * 4 + b2] = acc[a][b2];
-  }
-  __syncthreads();
-  if (active && grp == 0) {
-    for (int g2 = 1; g2 < groups; ++g2) {
-      const int t2 = (g2 - 1) * ntiles + tile;
+            for (int c = 0; c < 4; ++c) {
+              float* o = out + (8 * ty + a) * ldo + 4 * tx + c;
+              *o = (g == 0) ? acc[a][c] : *o + acc[a][c];
+            }
+        }
+        __syncthreads();
+      }
 #pragma unroll
       for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] += Red[t2 * 32 + a * 4 + b2];
+        for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
     }
-    float* G = sm + L.g;
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) G[(ty * 8 + a) * L.ld + tx * 4 + b2] = acc[a][b2];
   }
-  __syncthreads();
+  cp_wait<0>();
 }
 
-// Cholesky of the upper triangle of G (k x k, row stride ld) in place
-// (right-looking, FP32) and R^{-1} (upper, zero below the diagonal) into Ri
-// (row stride ldr).  A non-positive or tiny pivot raises kStatusRankDef.
-__device__ void fin_chol(float* G, int ld, int k, float* Ri, int ldr, int nrows_ri,
-                         int* status) {
-  __shared__ float inv_d;
-  __shared__ int bad;
+// Cholesky of the upper triangle of G (k x k, row stride ld) in place, right
+// looking: at step j, thread (a0, c) = (t / 64, t % 64) updates entries
+// (a, c), j < a <= c, a = a0 mod 4, from row j; one barrier per step.
+// Afterwards row j of R = U_j / sqrt(U_jj), U_j the j-th row of the Schur
+// complement at step j, and dinv[j] = 1 / R_jj.  A pivot
+// U_jj <= 1e-12 max_i G_ii (|R_jj| <= 1e-6 max sqrt(G_ii)) is dropped (its
+// row of R is zero, dinv 0) and, with `check`, raises kStatusRankDef.
+__device__ void fin_chol(float* G, int ld, int k, float* dinv, bool check, int* status) {
   const int tid = threadIdx.x;
-  for (int e = tid; e < nrows_ri * ldr; e += FT) Ri[e] = 0.f;
-  if (tid == 0) bad = 0;
+  const int a0 = tid >> 6, c = tid & 63;
+  float mx = 0.f;
+  for (int a = 0; a < k; ++a) mx = fmaxf(mx, G[a * ld + a]);
+  const float thr = 1e-12f * mx;
   __syncthreads();
   for (int j = 0; j < k; ++j) {
-    if (tid == 0) {
-      const float d = G[j * ld + j];
-      if (!(d > 0.f)) bad = 1;
-      const float r = d > 0.f ? sqrtf(d) : 0.f;
-      G[j * ld + j] = r;
-      inv_d = r > 0.f ? 1.f / r : 0.f;
-    }
-    __syncthreads();
-    for (int c = j + 1 + tid; c < k; c += FT) G[j * ld + c] *= inv_d;
-    __syncthreads();
-    const int w = k - j - 1;
-    for (int e = tid; e < w * w; e += FT) {
-      const int a = j + 1 + e / w, c = j + 1 + e % w;
-      if (a <= c) G[a * ld + c] = fmaf(-G[j * ld + a], G[j * ld + c], G[a * ld + c]);
+    const float d = G[j * ld + j];
+    if (d > thr && c > j && c < k) {
+      const float gc = G[j * ld + c] / d;
+      for (int a = j + 1 + ((a0 - j - 1) & 3); a <= c; a += 4)
+        G[a * ld + c] = fmaf(-G[j * ld + a], gc, G[a * ld + c]);
     }
     __syncthreads();
   }
-  if (tid == 0) {
-    float mx = 0.f;
-    for (int c = 0; c < k; ++c) mx = fmaxf(mx, fabsf(G[c * ld + c]));
-    for (int c = 0; c < k; ++c) bad |= !(fabsf(G[c * ld + c]) > 1e-6f * mx);
-    if (bad) atomicOr(status, kStatusRankDef);
+  if (tid < 32) {
+    bool bad = false;
+    for (int a = tid; a < k; a += 32) {
+      const float d = G[a * ld + a];
+      const bool drop = !(d > thr);
+      bad |= drop;
+      dinv[a] = drop ? 0.f : rsqrtf(d);
+    }
+    if (check && __any_sync(0xffffffffu, bad) && tid == 0) atomicOr(status, kStatusRankDef);
   }
   __syncthreads();
-  for (int c = tid; c < k; c += FT) {  // column c by back substitution
-    for (int i = c; i >= 0; --i) {
-      float t = (i == c) ? 1.f : 0.f;
-      for (int q = i + 1; q <= c; ++q) t = fmaf(-G[i * ld + q], Ri[q * ldr + c], t);
-      const float d = G[i * ld + i];
-      Ri[i * ldr + c] = (d != 0.f) ? t / d : 0.f;
-    }
+  for (int e = tid; e < k * 64; e += FT) {
+    const int a = e >> 6, cc = e & 63;
+    if (cc >= a && cc < k) G[a * ld + cc] *= dinv[a];
   }
   __syncthreads();
 }
 
-// Partner of column j in round `round` of the round-robin order on kk = 2 m'
-// columns (mm = kk - 1): the pairs of a round are (round, mm) and
-// (round + i, round - i) mod mm, i = 1 .. kk/2 - 1, so two columns other than
-// mm pair up when their indices sum to 2 round mod mm.
-__device__ __forceinline__ int fin_partner(int round, int j, int mm) {
-  const int r0 = round % mm;
-  if (j == mm) return r0;
-  if (j == r0) return mm;
-  return ((2 * round - j) % mm + mm) % mm;
-}
-
-// One CTA per matrix; HMAX >= ceil(k / 2).
-template <int HMAX>
-__global__ void __launch_bounds__(FT, 4)
-finish_kernel(int kp, const MatDev* __restrict__ mats, const PanelDev* __restrict__ xpanels,
-              const PanelDev* __restrict__ ypanels, float* __restrict__ Wm,
-              const double* __restrict__ normA2, double* __restrict__ err,
-              int* __restrict__ flags, int err_mode, double tau, int refine,
-              int* __restrict__ status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sm = (float*)smem_raw;
-  const FinLay L = fin_layout(kp);
-  uint64_t* bars = (uint64_t*)(smem_raw + L.bars);
-  const int b = blockIdx.x, tid = threadIdx.x;
-  const MatDev md = mats[b];
-  const int k = md.k, r = md.r;
-  const PanelDev px = xpanels[b], py = ypanels[b];
-  if (tid == 0) {
-    for (int s = 0; s < FSTAGES; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(
-          (uint32_t)__cvta_generic_to_shared(bars + s)));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  long long gb = 0;
-  bool ok = true;
-  float* G = sm + L.g;
-  float* RF = sm + L.rf;
-  float* RI = sm + L.ri;
-  // ---- R1 = chol(X^T X), R1^{-1} into RI
-  fin_gram(L, sm, bars, (const float*)px.P, px.rows, k, false, gb, status, ok);
-  fin_chol(G, L.ld, k, RI, kp, kp, status);
-  if (refine) {
-    // ---- R2 = chol(Q1^T Q1), Q1 = X R1^{-1}; R_X^{-1} = R1^{-1} R2^{-1}
-    fin_gram(L, sm, bars, (const float*)px.P, px.rows, k, true, gb, status, ok);
-    fin_chol(G, L.ld, k, RF, L.ld, kp, status);  // R2^{-1} into RF
-    for (int e = tid; e < kp * kp; e += FT) {   // product (upper) into G
-      const int i = e / kp, c = e % kp;
+// R^{-1} (upper, k x k, from fin_chol's R with row stride ld and dinv) into
+// Ri (kc x kc, row stride kc, zero below the diagonal and past k): column c
+// by back substitution in the four threads 4c .. 4c + 3, each summing every
+// fourth term.
+__device__ void fin_rinv(const float* __restrict__ R, int ld, const float* __restrict__ dinv,
+                         int k, int kc, float* __restrict__ Ri) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kc * kc; e += FT) Ri[e] = 0.f;
+  __syncthreads();
+  const int c = tid >> 2, qq = tid & 3;
+  const unsigned m4 = 0xFu << (tid & 28);
+  if (c < k) {  // the column's four lanes together
+    if (qq == 0) Ri[c * kc + c] = dinv[c];
+    __syncwarp(m4);
+    for (int i = c - 1; i >= 0; --i) {
       float t = 0.f;
-      if (i <= c && c < k)
-        for (int q = i; q <= c; ++q) t = fmaf(RI[i * kp + q], RF[q * L.ld + c], t);
-      G[i * L.ld + c] = t;
+      for (int q = i + 1 + qq; q <= c; q += 4) t = fmaf(R[i * ld + q], Ri[q * kc + c], t);
+      t += __shfl_xor_sync(m4, t, 1);
+      t += __shfl_xor_sync(m4, t, 2);
+      if (qq == 0) Ri[i * kc + c] = -t * dinv[i];
+      __syncwarp(m4);
     }
-    __syncthreads();
-    for (int e = tid; e < kp * kp; e += FT) RI[e] = G[(e / kp) * L.ld + e % kp];
-    __syncthreads();
-  }
-  // ---- G_M = (Y R_X^{-1})^T (Y R_X^{-1}) (upper, in G)
-  fin_gram(L, sm, bars, (const float*)py.P, py.rows, k, true, gb, status, ok);
-
-  // ---- eigenpairs of G_M: one-sided Jacobi on B = G_M.  Rotations that
-  // make the columns of B mutually orthogonal leave B = G_M V = V Lambda, so
-  // the column norms are the eigenvalues and the normalised columns the
-  // eigenvectors (whose errors reach the captured energy, a Rayleigh
-  // quotient, only at second order).  Two adjacent threads keep the two
-  // halves of column j of B in registers; each round of the parallel
-  // round-robin order they read their halves of the partner column from
-  // shared memory (double-buffered, one barrier per round), add their
-  // partial dot products with one shuffle, and all four threads of a pair of
-  // columns compute the same rotation from the same three sums.
-  const int jl = k + 1;  // row stride of the Jacobi planes
-  float* Gs = sm + L.stg;            // G_M, full symmetric
-  float* Bs = Gs + k * jl;           // 2 planes
-  float* lam = Bs + 2 * k * jl;      // k
-  int* order = (int*)(lam + k);      // k
-  double* acc = (double*)(order + k);  // FT; float offset stg + 3k(k+1) + 2k is even
-  for (int e = tid; e < k * k; e += FT) {
-    const int i = e / k, c = e % k;
-    Gs[i * jl + c] = G[min(i, c) * L.ld + max(i, c)];
   }
   __syncthreads();
-  const int j = tid >> 1, half = tid & 1;
-  const int hr = (k + 1) >> 1;
-  const int r0h = half * hr;
-  const int nh = max(0, min(hr, k - r0h));
-  float bc[HMAX];
+}
+
+// Partner of column j in round `round` (< mm) of the round-robin order on
+// kk = mm + 1 columns: the pairs are (round, mm) and (round + i, round - i)
+// mod mm, i = 1 .. kk/2 - 1.
+__device__ __forceinline__ int fin_partner(int round, int j, int mm) {
+  if (j == mm) return round;
+  if (j == round) return mm;
+  int x = 2 * round - j;
+  if (x < 0) x += mm;
+  if (x >= mm) x -= mm;
+  return x;
+}
+
+// The CholeskyQR2 correction applied in k x k space: R2 = chol(GQ) (GQ =
+// Q1^T Q1, upper, row stride gld, overwritten), G_M = R2^{-T} GM1 R2^{-1}
+// (upper, into GA; GM1 = M1^T M1, upper, row stride gld, may be GA) and
+// R_X^{-1} = R1^{-1} R2^{-1} (RI, in place).  Scratch: the area after GQ.
+__device__ void fin_refine(float* GQ, const float* GM1, float* GA, float* RI, float* area,
+                           float* DV, int k, int kc, int gld, int g4, int* status) {
+  const int tid = threadIdx.x;
+  float* RF = area + g4;     // R2^{-1}, row stride kc
+  float* TT = RF + kc * kc;  // row stride kc
+  float* RX = area;          // R1^{-1} R2^{-1}, row stride kc (GQ is dead by then)
+  fin_chol(GQ, gld, k, DV, true, status);
+  fin_rinv(GQ, gld, DV, k, kc, RF);
+  // TT = GM1 R2^{-1}, four columns per thread
+  for (int e = tid; e < k * 16; e += FT) {
+    const int a = e >> 4, c4 = e & 15;
+    if (4 * c4 < k) {
+      float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+      const int qm = min(k - 1, 4 * c4 + 3);
+      for (int q = 0; q <= qm; ++q) {
+        const float g = GM1[min(a, q) * gld + max(a, q)];
+        const float4 f = ld4(RF + q * kc + 4 * c4);
+        t0 = fmaf(g, f.x, t0);
+        t1 = fmaf(g, f.y, t1);
+        t2 = fmaf(g, f.z, t2);
+        t3 = fmaf(g, f.w, t3);
+      }
+      st4(TT + a * kc + 4 * c4, t0, t1, t2, t3);
+    }
+  }
+  __syncthreads();
+  // GA = R2^{-T} TT (upper); RX = R1^{-1} R2^{-1}
+  for (int e = tid; e < k * 16; e += FT) {
+    const int a = e >> 4, c4 = e & 15;
+    if (4 * c4 < k && 4 * c4 + 3 >= a) {
+      float t[4] = {0.f, 0.f, 0.f, 0.f}, w[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int q = 0; q <= a; ++q) {
+        const float f = RF[q * kc + a];
+        const float4 v = ld4(TT + q * kc + 4 * c4);
+        t[0] = fmaf(f, v.x, t[0]);
+        t[1] = fmaf(f, v.y, t[1]);
+        t[2] = fmaf(f, v.z, t[2]);
+        t[3] = fmaf(f, v.w, t[3]);
+      }
+      const int qm = min(k - 1, 4 * c4 + 3);
+      for (int q = a; q <= qm; ++q) {
+        const float f = RI[a * kc + q];
+        const float4 v = ld4(RF + q * kc + 4 * c4);
+        w[0] = fmaf(f, v.x, w[0]);
+        w[1] = fmaf(f, v.y, w[1]);
+        w[2] = fmaf(f, v.z, w[2]);
+        w[3] = fmaf(f, v.w, w[3]);
+      }
 #pragma unroll
-  for (int i = 0; i < HMAX; ++i) bc[i] = (j < k && i < nh) ? Gs[(r0h + i) * jl + j] : 0.f;
+      for (int z = 0; z < 4; ++z) {
+        const int c = 4 * c4 + z;
+        if (c >= a && c < k) GA[a * gld + c] = t[z];
+      }
+      st4(RX + a * kc + 4 * c4, w[0], w[1], w[2], w[3]);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < kc * kc; e += FT) {
+    const int a = e / kc, c = e - a * kc;
+    RI[e] = (a < k && c < k && c >= a) ? RX[e] : 0.f;
+  }
+  __syncthreads();
+}
+
+// Eigenpairs of G_M (upper in GA, row stride gld) and what follows from
+// them: sigma (md.sigma), V_r, W = R_X^{-1} V_r into WS (= the start of the
+// area, row stride kc), and in red[0] / red[1] (after the final barrier) the
+// captured energy tr(V_r^T G_M V_r) and the first-order bound
+//   est = u sum_{c<r} lambda_c (sum_i DX_i |W_ic|)^2
+// on its change from the rounding of X^T X (u = 2^-24): with
+// R^T R = X^T X + E, |E_ij| <~ u DX_i DX_j, lambda_c moves by about
+// lambda_c w_c^T E w_c, w_c = R^{-1} v_c, where ||X w_c|| = 1.
+//
+// G_M = R_M^T R_M (Cholesky), then one-sided Jacobi on L = R_M^T (column j
+// of L = row j of R_M).  Thread (j, qt) = (tid / 4, tid % 4) keeps rows
+// [qt QMAX, qt QMAX + QMAX) of column j in registers; each round of the
+// parallel round-robin order it stores them to one of two planes, reads its
+// part of the partner column after one barrier, sums the three partial dot
+// products over the column's four lanes, and all eight threads of a pair
+// compute the same rotation from the same sums.
+template <int QMAX>
+__device__ void fin_eigen(const MatDev& md, int k, int r, int kc, int gld, int g4,
+                          const float* GA, const float* RI, const float* DX, float* DV,
+                          float* area, double* red, int* status) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int jl = 4 * QMAX + 4;  // column stride of the planes
+  float* GC = area;                 // R_M, row stride gld; later E and WS
+  float* PL = area + g4;            // two planes
+  float* lam = PL + 2 * kc * jl;    // kc
+  int* order = (int*)(lam + kc);    // kc
+  for (int e = tid; e < k * 64; e += FT) {
+    const int a = e >> 6, c = e & 63;
+    if (c >= a && c < k) GC[a * gld + c] = GA[a * gld + c];
+  }
+  __syncthreads();
+  fin_chol(GC, gld, k, DV, false, status);
+  const int j = tid >> 2, qt = tid & 3;
+  const int i0 = qt * QMAX;
+  float bc[QMAX];
+#pragma unroll
+  for (int i = 0; i < QMAX; ++i) {
+    const int row = i0 + i;  // L[row][j] = R_M[j][row], zero below the diagonal of R_M
+    bc[i] = (j < k && row < k && row >= j) ? GC[j * gld + row] : 0.f;
+  }
+  const unsigned gmask = 0xFu << (lane & 28);  // the column's four lanes
   const int kk = k + (k & 1), mm = kk - 1;
   int t = 0;
-  for (int sweep = 0; sweep < 12 && mm > 0; ++sweep) {
+  for (int sweep = 0; sweep < 15 && mm > 0; ++sweep) {
     int rot = 0;
     for (int round = 0; round < mm; ++round, ++t) {
-      float* Bb = Bs + (t & 1) * k * jl;
+      float* Bb = PL + (t & 1) * kc * jl;
       if (j < k) {
 #pragma unroll
-        for (int i = 0; i < HMAX; ++i)
-          if (i < nh) Bb[j * jl + r0h + i] = bc[i];
+        for (int i = 0; i < QMAX; i += 4)
+          st4(Bb + j * jl + i0 + i, bc[i], bc[i + 1], bc[i + 2], bc[i + 3]);
       }
       __syncthreads();
       const int pj = (j < k) ? fin_partner(round, j, mm) : k;
-      if (pj < k) {  // both threads of the column take this branch together
-        const float* pb = Bb + pj * jl + r0h;
-        float y[HMAX];
+      if (pj < k) {  // the four threads of the column take this branch together
+        const float* pb = Bb + pj * jl + i0;
+        float y[QMAX];
         float aa = 0.f, pp = 0.f, ap = 0.f;
 #pragma unroll
-        for (int i = 0; i < HMAX; ++i) {
-          y[i] = (i < nh) ? pb[i] : 0.f;
+        for (int i = 0; i < QMAX; i += 4) {
+          const float4 v = ld4(pb + i);
+          y[i] = v.x;
+          y[i + 1] = v.y;
+          y[i + 2] = v.z;
+          y[i + 3] = v.w;
+        }
+#pragma unroll
+        for (int i = 0; i < QMAX; ++i) {
           aa = fmaf(bc[i], bc[i], aa);
           pp = fmaf(y[i], y[i], pp);
           ap = fmaf(bc[i], y[i], ap);
         }
-        const unsigned m2 = 3u << (threadIdx.x & 30);  // this column's two lanes
-        aa += __shfl_xor_sync(m2, aa, 1);
-        pp += __shfl_xor_sync(m2, pp, 1);
-        ap += __shfl_xor_sync(m2, ap, 1);
+        aa += __shfl_xor_sync(gmask, aa, 1);
+        pp += __shfl_xor_sync(gmask, pp, 1);
+        ap += __shfl_xor_sync(gmask, ap, 1);
+        aa += __shfl_xor_sync(gmask, aa, 2);
+        pp += __shfl_xor_sync(gmask, pp, 2);
+        ap += __shfl_xor_sync(gmask, ap, 2);
         const bool low = j < pj;  // the lower index is p of the pair (p, q)
         const float alpha = low ? aa : pp, beta = low ? pp : aa, gamma = ap;
-        if (fabsf(gamma) > 4.0e-6f * sqrtf(alpha * beta) && fabsf(gamma) > 1.0e-30f) {
-          const float zeta = (beta - alpha) / (2.f * gamma);
-          const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-          const float c = 1.f / sqrtf(1.f + tt * tt), sn = tt * c;
+        // rotate unless |gamma| <= 4e-6 sqrt(alpha beta) (a zero column
+        // gives rsqrt = inf: rotate if gamma != 0, skip if gamma == 0)
+        if (fabsf(gamma) * rsqrtf(alpha) * rsqrtf(beta) > 4.0e-6f) {
+          const float zeta = __fdividef(beta - alpha, 2.f * gamma);
+          const float az = fabsf(zeta), z2 = fmaf(zeta, zeta, 1.f);
+          const float hyp = az < 1.0e18f ? z2 * rsqrtf(z2) : az;  // sqrt(1 + zeta^2)
+          const float tt = copysignf(__fdividef(1.f, az + hyp), zeta);
+          const float cs = rsqrtf(fmaf(tt, tt, 1.f)), sn = tt * cs;
           // [b_p b_q] <- [c b_p - s b_q, s b_p + c b_q]
           const float cp = low ? -sn : sn;
 #pragma unroll
-          for (int i = 0; i < HMAX; ++i) bc[i] = fmaf(c, bc[i], cp * y[i]);
+          for (int i = 0; i < QMAX; ++i) bc[i] = fmaf(cs, bc[i], cp * y[i]);
           rot = 1;
         }
       }
     }
     if (!__syncthreads_or(rot)) break;
   }
-  // eigenvalues = column norms; normalised columns = eigenvectors (plane 0)
-  float* Vs = Bs;           // column j at Vs[j * jl + i]
-  float* Vc = Bs + k * jl;  // corrected V_r, column c at Vc[c * jl + i]
+  // sigma_j = column norm; the normalised column is an eigenvector (plane 0)
+  float* Vs = PL;            // column j at Vs[j * jl + i]
+  float* Vc = PL + kc * jl;  // corrected V_r, column c at Vc[c * jl + i]
   {
     float nn = 0.f;
 #pragma unroll
-    for (int i = 0; i < HMAX; ++i) nn = fmaf(bc[i], bc[i], nn);
+    for (int i = 0; i < QMAX; ++i) nn = fmaf(bc[i], bc[i], nn);
     nn += __shfl_xor_sync(0xffffffffu, nn, 1);
+    nn += __shfl_xor_sync(0xffffffffu, nn, 2);
     if (j < k) {
-      const float l = sqrtf(nn);
-      if (half == 0) lam[j] = l;
-      const float inv = l > 1.0e-30f ? 1.f / l : 0.f;
+      if (qt == 0) lam[j] = nn;
+      const float inv = nn > 1.0e-37f ? rsqrtf(nn) : 0.f;
 #pragma unroll
-      for (int i = 0; i < HMAX; ++i)
-        if (i < nh) Vs[j * jl + r0h + i] = (inv > 0.f) ? bc[i] * inv : (r0h + i == j ? 1.f : 0.f);
+      for (int i = 0; i < QMAX; i += 4) {
+        float v[4];
+#pragma unroll
+        for (int z = 0; z < 4; ++z)
+          v[z] = (inv > 0.f) ? bc[i + z] * inv : (i0 + i + z == j ? 1.f : 0.f);
+        st4(Vs + j * jl + i0 + i, v[0], v[1], v[2], v[3]);
+      }
     }
   }
   __syncthreads();
   for (int c = tid; c < k; c += FT) {  // descending eigenvalues
     int rank = 0;
-    for (int c2 = 0; c2 < k; ++c2) rank += (lam[c2] > lam[c]) || (lam[c2] == lam[c] && c2 < c);
+    const float lc = lam[c];
+    for (int c2 = 0; c2 < k; ++c2) rank += (lam[c2] > lc) || (lam[c2] == lc && c2 < c);
     order[rank] = c;
   }
   __syncthreads();
   if (md.sigma != nullptr)
     for (int c = tid; c < k; c += FT) ((float*)md.sigma)[c] = sqrtf(lam[order[c]]);
-  // column c < r of V_r (E = V_r^T V_r - I, then V_r <- V_r - V_r E / 2)
-  for (int c = tid; c < r; c += FT) {
-    const float* vc = Vs + order[c] * jl;
-    float e[TSK_MAX_K];
-#pragma unroll
-    for (int a = 0; a < TSK_MAX_K; ++a) {
-      float s2 = 0.f;
-      if (a < r) {
-        const float* va = Vs + order[a] * jl;
-        s2 = (a == c) ? -1.f : 0.f;
-        for (int i = 0; i < k; ++i) s2 = fmaf(va[i], vc[i], s2);
-      }
-      e[a] = s2;
-    }
-    for (int i = 0; i < k; ++i) {
-      float s2 = 0.f;
-#pragma unroll
-      for (int a = 0; a < TSK_MAX_K; ++a)
-        if (a < r) s2 = fmaf(Vs[order[a] * jl + i], e[a], s2);
-      Vc[c * jl + i] = fmaf(-0.5f, s2, vc[i]);
+  // V_r <- V_r - V_r E / 2, E = V_r^T V_r - I (E in GC, row stride kc)
+  float* E = GC;
+  for (int e = tid; e < r * 64; e += FT) {
+    const int a = e >> 6, c = e & 63;
+    if (c < r) {
+      const float* va = Vs + order[a] * jl;
+      const float* vc = Vs + order[c] * jl;
+      float s2 = (a == c) ? -1.f : 0.f;
+      for (int i = 0; i < k; ++i) s2 = fmaf(va[i], vc[i], s2);
+      E[a * kc + c] = s2;
     }
   }
   __syncthreads();
-  // row i of G V_r and of W = R_X^{-1} V_r; energy tr(V_r^T G V_r)
+  for (int e = tid; e < r * 64; e += FT) {
+    const int c = e >> 6, i = e & 63;
+    if (i < k) {
+      float s2 = 0.f;
+      for (int a = 0; a < r; ++a) s2 = fmaf(Vs[order[a] * jl + i], E[a * kc + c], s2);
+      Vc[c * jl + i] = fmaf(-0.5f, s2, Vs[order[c] * jl + i]);
+    }
+  }
+  __syncthreads();
+  // WS = R_X^{-1} V_r (row stride kc, E is dead); energy tr(V_r^T G_M V_r)
+  float* WS = GC;
   double part = 0.0;
+  for (int e = tid; e < k * 64; e += FT) {
+    const int i = e >> 6, c = e & 63;
+    if (c < r) {
+      const float* v = Vc + c * jl;
+      float gv = 0.f, w = 0.f;
+      for (int q = 0; q < k; ++q) gv = fmaf(GA[min(i, q) * gld + max(i, q)], v[q], gv);
+      part += (double)v[i] * (double)gv;
+      for (int q = i; q < k; ++q) w = fmaf(RI[i * kc + q], v[q], w);  // R_X^{-1} upper
+      WS[i * kc + c] = w;
+    }
+  }
+  __syncthreads();
+  double epart = 0.0;
+  if (tid < r) {
+    float sc = 0.f;
+    for (int i = 0; i < k; ++i) sc = fmaf(DX[i], fabsf(WS[i * kc + tid]), sc);
+    epart = 0x1p-24 * (double)lam[order[tid]] * (double)sc * (double)sc;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    part += __shfl_xor_sync(0xffffffffu, part, o);
+    epart += __shfl_xor_sync(0xffffffffu, epart, o);
+  }
+  if (lane == 0) {
+    red[2 + warp] = part;
+    red[2 + FW + warp] = epart;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double energy = 0.0, est = 0.0;
+    for (int w = 0; w < FW; ++w) {
+      energy += red[2 + w];
+      est += red[2 + FW + w];
+    }
+    red[0] = energy;
+    red[1] = est;
+  }
+  __syncthreads();
+}
+
+// One CTA per matrix; QMAX = fin_quarter(kcm).  refine: 0 never, 1 always,
+// 2 when est > 1e-3 (||A||^2 - energy) after the unrefined pass.
+template <int QMAX>
+__global__ void __launch_bounds__(FT, 4)
+finish_kernel(FinLay L, int kp, const MatDev* __restrict__ mats,
+              const PanelDev* __restrict__ xpanels, const PanelDev* __restrict__ ypanels,
+              float* __restrict__ Wm, const double* __restrict__ normA2,
+              double* __restrict__ err, int* __restrict__ flags, int err_mode, double tau,
+              int refine, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sm = (float*)smem_raw;
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const MatDev md = mats[b];
+  const int k = md.k, r = md.r;
+  const int kc = (k + 7) & ~7, gld = kc + 1, g4 = (kc * gld + 3) & ~3;
+  const PanelDev px = xpanels[b], py = ypanels[b];
+  float* RI = sm + L.ri;
+  float* GA = sm + L.ga;
+  float* DV = sm + L.dv;
+  float* DX = sm + L.dx;
+  double* red = (double*)(sm + L.red);
+  float* area = sm + L.area;
+  const double tot = normA2[b];
+  // ---- R1 = chol(X^T X), R1^{-1} into RI
+  FinPass ps;
+  ps.P0 = (const float*)px.P;
+  ps.rows0 = px.rows;
+  ps.out0 = GA;
+  ps.P1 = nullptr;
+  ps.rows1 = 0;
+  ps.out1 = nullptr;
+  ps.nseg = 1;
+  fin_stream(L, sm, kc, kp, ps, false);
+  for (int i = tid; i < k; i += FT) DX[i] = sqrtf(fmaxf(GA[i * gld + i], 0.f));
+  fin_chol(GA, gld, k, DV, true, status);
+  fin_rinv(GA, gld, DV, k, kc, RI);
+  // ---- G_M (upper) into GA, R_X^{-1} into RI
+  float* GB = area;  // a Gram target in the area, row stride gld
+  if (refine == 1) {
+    ps.P1 = (const float*)py.P;
+    ps.rows1 = py.rows;
+    ps.out1 = GB;
+    ps.nseg = 2;  // Q1 = X R1^{-1}: Gram into GA; M1 = Y R1^{-1}: Gram into GB
+    fin_stream(L, sm, kc, kp, ps, true);
+    fin_refine(GA, GB, GA, RI, area, DV, k, kc, gld, g4, status);
+  } else {
+    ps.P0 = (const float*)py.P;
+    ps.rows0 = py.rows;
+    ps.out0 = GA;  // M1 = Y R1^{-1}
+    fin_stream(L, sm, kc, kp, ps, true);
+  }
+  // ---- eigenpairs, W, energy; one refinement afterwards if the bound asks
+  for (int pass = 0;; ++pass) {
+    fin_eigen<QMAX>(md, k, r, kc, gld, g4, GA, RI, DX, DV, area, red, status);
+    const bool again = refine == 2 && pass == 0 && red[1] > 1e-3 * (tot - red[0]);
+    if (!again) break;  // uniform: every thread reads the same red[]
+    __syncthreads();    // red[] read before it is written again
+    ps.P0 = (const float*)px.P;
+    ps.rows0 = px.rows;
+    ps.out0 = GB;  // Q1 = X R1^{-1}
+    ps.nseg = 1;
+    fin_stream(L, sm, kc, kp, ps, true);
+    fin_refine(GB, GA, GA, RI, area, DV, k, kc, gld, g4, status);
+  }
+  // ---- outputs: W (kp x kp, zero outside k x r), err, flags
+  const float* WS = area;
   float* Wout = Wm + (long long)b * kp * kp;
   for (int e = tid; e < kp * kp; e += FT) {
     const int i = e / kp, c = e - i * kp;
-    float w = 0.f;
-    if (i < k && c < r) {
-      const float* v = Vc + c * jl;
-      float gv = 0.f;
-      for (int q = 0; q < k; ++q) gv = fmaf(Gs[i * jl + q], v[q], gv);
-      part += (double)v[i] * (double)gv;
-      for (int q = i; q < k; ++q) w = fmaf(RI[i * kp + q], v[q], w);  // R_X^{-1} upper
-    }
-    Wout[e] = w;
+    Wout[e] = (i < k && c < r) ? WS[i * kc + c] : 0.f;
   }
-  acc[tid] = part;
-  __syncthreads();
   if (tid == 0) {
-    double energy = 0.0;
-    for (int q = 0; q < FT; ++q) energy += acc[q];
-    const double tot = normA2[b];
-    const double e2 = tot - energy;
+    const double e2 = tot - red[0];
     err[b] = sqrt(e2 > 0.0 ? e2 : 0.0);
     flags[b] = (err_mode == 2) || (err_mode == 0 && e2 < tau * tot);
   }
 }
 
-template <int HMAX>
-cudaError_t launch_finish_t(int kp, const MatDev* mats, int count, const PanelDev* xpanels,
-                            const PanelDev* ypanels, float* Wm, double* normA2, double* err,
-                            int* flags, int err_mode, double tau, int refine, int* status,
-                            cudaStream_t s) {
-  const FinLay L = fin_layout(kp);
-  cudaError_t e = cudaFuncSetAttribute(finish_kernel<HMAX>,
+template <int QMAX>
+cudaError_t launch_finish_t(int kp, int kcm, const MatDev* mats, int count,
+                            const PanelDev* xpanels, const PanelDev* ypanels, float* Wm,
+                            double* normA2, double* err, int* flags, int err_mode, double tau,
+                            int refine, int* status, cudaStream_t s) {
+  const FinLay L = fin_layout(kcm);
+  cudaError_t e = cudaFuncSetAttribute(finish_kernel<QMAX>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
   if (e != cudaSuccess) return e;
-  finish_kernel<HMAX><<<count, FT, L.bytes, s>>>(kp, mats, xpanels, ypanels, Wm, normA2, err,
+  finish_kernel<QMAX><<<count, FT, L.bytes, s>>>(L, kp, mats, xpanels, ypanels, Wm, normA2, err,
                                                  flags, err_mode, tau, refine, status);
   return cudaGetLastError();
 }
@@ -515,22 +705,22 @@ cudaError_t launch_finish(int kp, int kmax, const MatDev* mats, int count,
                           double* normA2, double* err, int* flags, int err_mode, double tau,
                           int refine, int* status, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  if (kp % 16 != 0 || kp > TSK_MAX_K || kmax > kp) return cudaErrorInvalidValue;
-  const int hm = (kmax + 1) / 2;
-  if (hm <= 8)
-    return launch_finish_t<8>(kp, mats, count, xpanels, ypanels, Wm, normA2, err, flags,
-                              err_mode, tau, refine, status, s);
-  if (hm <= 16)
-    return launch_finish_t<16>(kp, mats, count, xpanels, ypanels, Wm, normA2, err, flags,
-                               err_mode, tau, refine, status, s);
-  if (hm <= 20)
-    return launch_finish_t<20>(kp, mats, count, xpanels, ypanels, Wm, normA2, err, flags,
-                               err_mode, tau, refine, status, s);
-  if (hm <= 24)
-    return launch_finish_t<24>(kp, mats, count, xpanels, ypanels, Wm, normA2, err, flags,
-                               err_mode, tau, refine, status, s);
-  return launch_finish_t<32>(kp, mats, count, xpanels, ypanels, Wm, normA2, err, flags,
-                             err_mode, tau, refine, status, s);
+  if (kp % 16 != 0 || kp > TSK_MAX_K || kmax > kp || kmax < 1) return cudaErrorInvalidValue;
+  const int kcm = (kmax + 7) & ~7;
+  switch (fin_quarter(kcm)) {
+    case 4:
+      return launch_finish_t<4>(kp, kcm, mats, count, xpanels, ypanels, Wm, normA2, err, flags,
+                                err_mode, tau, refine, status, s);
+    case 8:
+      return launch_finish_t<8>(kp, kcm, mats, count, xpanels, ypanels, Wm, normA2, err, flags,
+                                err_mode, tau, refine, status, s);
+    case 12:
+      return launch_finish_t<12>(kp, kcm, mats, count, xpanels, ypanels, Wm, normA2, err, flags,
+                                 err_mode, tau, refine, status, s);
+    default:
+      return launch_finish_t<16>(kp, kcm, mats, count, xpanels, ypanels, Wm, normA2, err, flags,
+                                 err_mode, tau, refine, status, s);
+  }
 }
 
 }  // namespace tsk

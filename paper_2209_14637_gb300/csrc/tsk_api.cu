@@ -87,7 +87,7 @@ extern "C" void tsk_default_options(tsk_options* o) {
   if (!o) return;
   memset(o, 0, sizeof(*o));
   o->kernel = TSK_KERNEL_AUTO;
-  o->refine_q = 1;
+  o->refine_q = 2;
   o->max_iter = 300;
   o->eig_tol = 0.0;
   o->err_mode = 0;
@@ -284,7 +284,7 @@ static cudaError_t capture_plan(tsk_plan p, cudaEvent_t evb, cudaEvent_t eve) {
     const PanelDev* pan = (const PanelDev*)(base + p->o_pan);
     ce = launch_finish(kp, p->kmax, d_mats, count, pan, pan + count, (float*)(base + p->o_W),
                        d_norm, d_err, (int*)(base + p->o_flag), h->opts.err_mode, tau,
-                       h->opts.refine_q ? 1 : 0, h->d_status, s);
+                       h->opts.refine_q, h->d_status, s);
     ++launches;
   }
   if (ce == cudaSuccess && h->opts.err_mode != 1) {

@@ -42,7 +42,7 @@ def test_null_arguments_are_rejected_without_a_device(lib):
 
 def test_default_options(lib):
     o = tsk.default_options()
-    assert o.kernel == tsk.KERNEL_AUTO and o.refine_q == 1
+    assert o.kernel == tsk.KERNEL_AUTO and o.refine_q == tsk.REFINE_AUTO
     assert o.max_iter == 300 and o.spin_limit == 1 << 24
 
 

@@ -138,3 +138,63 @@ def test_tc_repeated_plan_is_deterministic(tsk):
     assert torch.allclose(err, err[0].expand(9), rtol=1e-12, atol=0)
     plan.close()
     h.close()
+
+
+def _errs(tsk, refine, As, Ss, rs, kernel=None):
+    h = tsk.Handle(kernel=tsk.KERNEL_TC if kernel is None else kernel, refine_q=refine)
+    out = h.approx_batch(As, Ss, rs)
+    torch.cuda.synchronize()
+    st = h.sync_status()
+    h.close()
+    return _np(out["err"]), st
+
+
+def test_refinement_modes_on_a_stream_sample(tsk):
+    """C3-shaped stream (k = 40, r = 20; 1024 x 1024): every refinement mode
+    meets the gap; the automatic mode takes each matrix either unrefined or
+    refined, bit for bit like the fixed modes (the same arithmetic in the
+    same order), and on this well-conditioned stream leaves all unrefined."""
+    import synth
+    spec = synth.scaled(synth.C3, 1024, 1024, 24, 6)
+    tr = synth.stream(spec, "train")
+    S_o, _, _, _ = oracle.train_sketch(list(tr.double().numpy()), spec.k)
+    te = synth.stream(spec, "test", device="cuda")
+    S = torch.tensor(S_o, device="cuda", dtype=torch.float32)
+    As, Ss, rs = list(te), [S] * len(te), [spec.r] * len(te)
+    e0, s0 = _errs(tsk, tsk.REFINE_NEVER, As, Ss, rs)
+    e1, s1 = _errs(tsk, tsk.REFINE_ALWAYS, As, Ss, rs)
+    e2, s2 = _errs(tsk, tsk.REFINE_AUTO, As, Ss, rs)
+    assert s0 == s1 == s2 == 0
+    ref = np.array([oracle.scw(_np(A), S_o.astype(np.float32).astype(np.float64), spec.r,
+                               dense=False)["err"] for A in As])
+    for e in (e0, e1, e2):
+        assert np.max(np.abs(e - ref) / ref) <= GAP
+    assert np.array_equal(e2, e0)
+
+
+def test_automatic_refinement_where_the_bound_asks(tsk):
+    """Two nearly parallel sketch rows make X ill conditioned along one
+    direction: the first-order bound exceeds 1e-3 of the residual, so the
+    automatic mode refines every matrix (bit for bit the always-refine
+    result) and stays within the gap.  FP32 inputs (CUDA-core sketch): the
+    BF16 path rounds S to BF16, a relative perturbation of 2^-9 that such a
+    sketch amplifies past the gap by itself."""
+    g = torch.Generator(device="cuda").manual_seed(11)
+    m, n, k, r = 1024, 768, 40, 20
+    L = 2 * k
+    U = torch.linalg.qr(torch.randn(m, L, generator=g, device="cuda"))[0]
+    sv = torch.arange(1, L + 1, device="cuda", dtype=torch.float32) ** -1.2
+    As = [((U * sv) @ torch.randn(L, n, generator=g, device="cuda")
+           + 1e-3 * torch.randn(m, n, generator=g, device="cuda")).contiguous()
+          for _ in range(4)]
+    S = torch.linalg.qr(U[:, :k] + 0.1 * torch.randn(m, k, generator=g, device="cuda"))[0].T
+    S = S.contiguous()
+    S[5] = S[3] + 0.02 * torch.randn(m, generator=g, device="cuda") / m ** 0.5
+    Ss, rs = [S] * len(As), [r] * len(As)
+    e1, s1 = _errs(tsk, tsk.REFINE_ALWAYS, As, Ss, rs, kernel=tsk.KERNEL_AUTO)
+    e2, s2 = _errs(tsk, tsk.REFINE_AUTO, As, Ss, rs, kernel=tsk.KERNEL_AUTO)
+    assert s1 == s2 == 0
+    assert np.array_equal(e2, e1)
+    Sn = _np(S)
+    ref = np.array([oracle.scw(_np(A), Sn, r, dense=False)["err"] for A in As])
+    assert np.max(np.abs(e2 - ref) / ref) <= GAP
