@@ -139,17 +139,19 @@ __device__ __forceinline__ void fin_stream(const FinLay& L, float* sm, int kc, i
     r0 = (long long)(bi - (seg ? nb0 : 0)) * FSB;
     return (int)min((long long)FSB, (seg ? S.rows1 : S.rows0) - r0);
   };
-  auto issue = [&](int bi) {  // every thread: its 16-byte pieces of block bi
-    if (bi < nb) {
+  // Thread t copies the 16-byte pieces (row, quad) = (t / 16 + 16 i, t % 16),
+  // i = 0, 1, of every block.
+  static_assert(FSB * 16 == 2 * FT, "two pieces per thread and block");
+  auto issue = [&](int bi) {  // every thread: its pieces of block bi
+    const int crow = threadIdx.x >> 4, cq = threadIdx.x & 15;
+    if (bi < nb && cq < n4) {
       int seg;
       long long r0;
       const int nrows = block_rows(bi, seg, r0);
-      const float* P = (seg ? S.P1 : S.P0) + r0 * kp;
-      float* dst = area + (bi % NST) * L.stage;
-      for (int e = tid; e < FSB * 16; e += FT) {  // (row, quad) = (e / 16, e % 16)
-        const int row = e >> 4, c4 = e & 15;
-        if (row < nrows && c4 < n4) cp16(dst + row * srow + 4 * c4, P + row * kp + 4 * c4);
-      }
+      const float* P = (seg ? S.P1 : S.P0) + (r0 + crow) * kp + 4 * cq;
+      float* dst = area + (bi % NST) * L.stage + crow * srow + 4 * cq;
+      if (crow < nrows) cp16(dst, P);
+      if (crow + 16 < nrows) cp16(dst + 16 * srow, P + 16 * kp);
     }
     cp_commit();  // one group per block, empty ones included
   };
@@ -492,8 +494,12 @@ __device__ void fin_eigen(const MatDev& md, int k, int r, int kc, int gld, int g
         const bool low = j < pj;  // the lower index is p of the pair (p, q)
         const float alpha = low ? aa : pp, beta = low ? pp : aa, gamma = ap;
         // rotate unless |gamma| <= 4e-6 sqrt(alpha beta) (a zero column
-        // gives rsqrt = inf: rotate if gamma != 0, skip if gamma == 0)
-        if (fabsf(gamma) * rsqrtf(alpha) * rsqrtf(beta) > 4.0e-6f) {
+        // gives rsqrt = inf: rotate if gamma != 0, skip if gamma == 0).  The
+        // sweeps stop after one whose rotations all had |gamma| <=
+        // 2e-3 sqrt(alpha beta): convergence is quadratic by then, so what
+        // is left is of the order of the 4e-6 threshold.
+        const float meas = fabsf(gamma) * rsqrtf(alpha) * rsqrtf(beta);
+        if (meas > 4.0e-6f) {
           const float zeta = __fdividef(beta - alpha, 2.f * gamma);
           const float az = fabsf(zeta), z2 = fmaf(zeta, zeta, 1.f);
           const float hyp = az < 1.0e18f ? z2 * rsqrtf(z2) : az;  // sqrt(1 + zeta^2)
@@ -503,7 +509,7 @@ __device__ void fin_eigen(const MatDev& md, int k, int r, int kc, int gld, int g
           const float cp = low ? -sn : sn;
 #pragma unroll
           for (int i = 0; i < QMAX; ++i) bc[i] = fmaf(cs, bc[i], cp * y[i]);
-          rot = 1;
+          rot |= meas > 2.0e-3f;
         }
       }
     }
