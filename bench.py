@@ -218,6 +218,25 @@ def run_tsk(args):
     S, eig, st = h.sketch_from_gram(G, spec.k, prec=tsk.BF16)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    # the Gram (T1) once more, timed on the device: a tensor-bound SYRK of
+    # m^2 n multiply-adds' worth of flops per matrix (half of 2 m^2 n)
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record()
+    h.gram([tr[i] for i in range(tr.shape[0])], mode=1, out=G)
+    g1.record()
+    torch.cuda.synchronize()
+    gram_ms = g0.elapsed_time(g1)
+    gram_flops = float(spec.m) ** 2 * spec.n * (b - a)
+    gram_tf = gram_flops / (gram_ms / 1e3) / 1e12
+    gpeak = float(peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]))
+    train_info = {"matrices": b - a, "total_s": train_s, "gram_ms": gram_ms,
+                  "gram_kernel": "tcgen05" if args.kernel != tsk.KERNEL_SIMT else "simt",
+                  "roofline": {"bound": "tensor", "achieved": gram_tf, "peak": gpeak,
+                               "unit": "TFLOP/s", "frac": gram_tf / gpeak,
+                               "peak_source": "bf16_tflops of " + peak_src,
+                               "flops": gram_flops}}
+    stage(f"training Gram: {train_info}")
     del tr, G
     torch.cuda.empty_cache()
 
@@ -423,6 +442,7 @@ def run_tsk(args):
             "fp32_path": fp32,
             "rel_err_gap": gap,
             "train_s": train_s,
+            "train": train_info,
             "train_status": st,
         }
         print(json.dumps(line), flush=True)

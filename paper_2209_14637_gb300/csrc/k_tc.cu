@@ -326,8 +326,9 @@ struct Ctl {
 
 // Bounded wait.  Returns false on timeout (after raising the status bit and
 // the CTA-wide abort flag) or when the CTA is already aborting.
+template <class PP>
 __device__ __forceinline__ bool bwait(uint32_t bar, uint32_t parity, volatile Ctl* ctl,
-                                      const TcParams& P) {
+                                      const PP& P) {
   if (ctl->abort) return false;
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
@@ -345,16 +346,17 @@ __device__ __forceinline__ bool bwait(uint32_t bar, uint32_t parity, volatile Ct
 }
 // Warp-uniform bounded wait: lane 0 polls, the verdict is broadcast, and the
 // warp leaves converged (the tcgen05.ld that follows is .sync.aligned).
+template <class PP>
 __device__ __forceinline__ bool bwait_warp(uint32_t bar, uint32_t parity, volatile Ctl* ctl,
-                                           const TcParams& P) {
+                                           const PP& P) {
   int ok = 0;
   if ((threadIdx.x & 31) == 0) ok = bwait(bar, parity, ctl, P) ? 1 : 0;
   ok = __shfl_sync(0xffffffffu, ok, 0);
   return ok != 0;
 }
 // Bounded wait that ignores the abort flag (used to drain own copies).
-__device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity,
-                                           const TcParams& P) {
+template <class PP>
+__device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity, const PP& P) {
   const uint64_t t0 = globaltimer();
   while (!mbar_try_wait(bar, parity)) {
     if ((long long)(globaltimer() - t0) > P.timeout_ns) {
@@ -1057,6 +1059,211 @@ cudaError_t class_launch(int C, int MC, const TcParams& prm, int nclusters, cuda
   return cudaErrorInvalidValue;
 }
 
+
+// ---------------------------------------------------------------------------
+// T1 on the tensor cores: the mode-1 Gram matrix G = sum_d A_d A_d^T of BF16
+// training matrices (Eq. 3.2; the Gram route of Section 3.1), FP32
+// accumulation in TMEM, FP64 sums in G.
+//
+// One CTA per 128 x 128 tile (I, J), I <= J, of the upper block triangle
+// (blockIdx.y splits the matrices when there are few tiles).  Both operands
+// are K-major: rows I and rows J of A_d, 64 columns per stage, loaded by TMA
+// with the 128-byte swizzle (a diagonal tile loads its rows once and uses
+// them as both operands).  Warp 0 issues the loads into a ring of GSTG
+// stages, warp 1 the MMAs (M = N = 128, K = 16, four per stage) into one of
+// two TMEM accumulators of 128 columns; every GFL matrices the accumulator
+// is handed to warps 2-5, which add it to G in FP64 while the MMAs go on in
+// the other one.  The lower triangle is mirrored afterwards.
+// ---------------------------------------------------------------------------
+struct GramParams {
+  const CUtensorMap* tmaps;  // one per matrix: box 64 columns x 128 rows
+  long long D, m, n;
+  double* G;                 // m x m, row-major
+  int ntile;                 // ceil(m / 128)
+  int splits;                // CTAs per tile (contiguous ranges of matrices)
+  int* status;
+  long long timeout_ns;
+};
+
+constexpr int GNT = 192;              // 6 warps: TMA, MMA, four epilogue warps
+constexpr int GSTG = 6;               // stages in flight
+constexpr int GTILE = 128 * 128;      // 128 rows x 64 BF16 columns = 16 KB
+constexpr int GSTAGE = 2 * GTILE;
+constexpr int GFL = 8;                // matrices per TMEM flush
+constexpr int G_OFF_BAR = GSTG * GSTAGE;
+enum { GB_FULL = 0, GB_EMPTY = GSTG, GB_TFULL = 2 * GSTG, GB_TEMPTY = 2 * GSTG + 2,
+       GB_DRAIN = 2 * GSTG + 4, GB_COUNT = 2 * GSTG + 5 };
+constexpr int G_SMEM = G_OFF_BAR + 256;
+static_assert(GB_COUNT * 8 + 16 <= 256, "gram barrier area");
+static_assert(G_SMEM <= 227 * 1024, "gram shared memory");
+
+__global__ void __launch_bounds__(GNT, 1) gram_tc_kernel(const __grid_constant__ GramParams P) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = smem_raw;
+  const uint32_t sb = smem_u32(sm);
+  if (sb & 1023) {
+    if (threadIdx.x == 0) atomicOr(P.status, kStatusTimeout);
+    return;
+  }
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  auto bar = [&](int i) -> uint32_t { return sb + G_OFF_BAR + 8 * i; };
+  volatile Ctl* ctl = (volatile Ctl*)(sm + G_OFF_BAR + 8 * GB_COUNT);
+  uint32_t* tmem_slot = (uint32_t*)(sm + G_OFF_BAR + 8 * GB_COUNT + 8);
+  int t = blockIdx.x, ti = 0;  // tile (ti, tj), ti <= tj, from the linear index
+  while (t >= P.ntile - ti) {
+    t -= P.ntile - ti;
+    ++ti;
+  }
+  const int tj = ti + t;
+  const bool diag = ti == tj;
+  const long long d0 = P.D * (long long)blockIdx.y / P.splits;
+  const long long d1 = P.D * (long long)(blockIdx.y + 1) / P.splits;
+  const int nkb = (int)((P.n + 63) / 64);
+  const int ngroups = (int)((d1 - d0 + GFL - 1) / GFL);
+  if (tid == 0) {
+    for (int s = 0; s < GSTG; ++s) {
+      mbar_init(bar(GB_FULL + s), 1);
+      mbar_init(bar(GB_EMPTY + s), 1);  // MMA commit
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar(GB_TFULL + b), 1);   // MMA commit
+      mbar_init(bar(GB_TEMPTY + b), 4);  // four epilogue warps
+    }
+    mbar_init(bar(GB_DRAIN), 1);
+    ctl->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(256)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      long long q = 0;
+      bool stop = false;
+      for (long long d = d0; d < d1 && !stop; ++d) {
+        const CUtensorMap* map = P.tmaps + d;
+        for (int kb = 0; kb < nkb; ++kb, ++q) {
+          const int s = (int)(q % GSTG);
+          const uint32_t u = (uint32_t)(q / GSTG);
+          if (!bwait(bar(GB_EMPTY + s), (u & 1) ^ 1, ctl, P)) {
+            stop = true;
+            break;
+          }
+          mbar_expect_tx(bar(GB_FULL + s), diag ? GTILE : GSTAGE);
+          tma_load_2d(sb + s * GSTAGE, map, kb * 64, ti * 128, bar(GB_FULL + s));
+          if (!diag)
+            tma_load_2d(sb + s * GSTAGE + GTILE, map, kb * 64, tj * 128, bar(GB_FULL + s));
+        }
+      }
+      for (int s = 0; s < GSTG; ++s) {  // every load issued must land before exit
+        if (q > s) {
+          const long long last = ((q - 1 - s) / GSTG) * GSTG + s;
+          drain_wait(bar(GB_FULL + s), (uint32_t)((last / GSTG) & 1), P);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, 128, 0, 0);
+      long long q = 0;
+      bool ok = true;
+      for (int grp = 0; grp < ngroups && ok; ++grp) {
+        const int buf = grp & 1;
+        const uint32_t v = (uint32_t)(grp >> 1);
+        if (!bwait(bar(GB_TEMPTY + buf), (v & 1) ^ 1, ctl, P)) break;
+        tc_fence_after();
+        const long long dlo = d0 + (long long)grp * GFL;
+        const long long dhi = dlo + GFL < d1 ? dlo + GFL : d1;
+        bool first = true;
+        for (long long d = dlo; d < dhi && ok; ++d) {
+          for (int kb = 0; kb < nkb; ++kb, ++q) {
+            const int s = (int)(q % GSTG);
+            const uint32_t u = (uint32_t)(q / GSTG);
+            if (!bwait(bar(GB_FULL + s), u & 1, ctl, P)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = sb + s * GSTAGE, b0 = diag ? a0 : a0 + GTILE;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              tc_mma(tmem + buf * 128, sdesc(a0 + kk * 32, 16, 1024),
+                     sdesc(b0 + kk * 32, 16, 1024), idesc, (first && kk == 0) ? 0u : 1u);
+            first = false;
+            tc_commit(bar(GB_EMPTY + s));
+          }
+        }
+        if (ok) tc_commit(bar(GB_TFULL + buf));
+      }
+      tc_commit(bar(GB_DRAIN));
+      drain_wait(bar(GB_DRAIN), 0, P);
+    }
+  } else {
+    // ------------------------------------- epilogue (warps 2-5): TMEM -> G
+    const int lane_base = (warp & 3) * 32;  // the TMEM lanes this warp may read
+    const long long row = (long long)ti * 128 + lane_base + lane;
+    const bool atomic = P.splits > 1;
+    for (int grp = 0; grp < ngroups; ++grp) {
+      const int buf = grp & 1;
+      const uint32_t v = (uint32_t)(grp >> 1);
+      if (!bwait_warp(bar(GB_TFULL + buf), v & 1, ctl, P)) break;
+      tc_fence_after();
+#pragma unroll 1
+      for (int c0 = 0; c0 < 128; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)lane_base << 16) + buf * 128 + c0, r);
+        tmem_wait_ld();
+        tmem_regs8(r);
+        tmem_regs8(r + 8);
+        if (row < P.m) {
+          double* g = P.G + row * P.m + (long long)tj * 128 + c0;
+          const long long cmax = P.m - ((long long)tj * 128 + c0);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            if (i < cmax) {
+              const double x = (double)__uint_as_float(r[i]);
+              if (atomic)
+                atomicAdd(g + i, x);
+              else
+                g[i] += x;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(GB_TEMPTY + buf));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256)
+                 : "memory");
+  }
+}
+
+// G[a][b] = G[b][a] for a > b: the kernel above fills the upper block
+// triangle (diagonal blocks in full).
+__global__ void mirror_upper_kernel(double* __restrict__ G, long long m) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * m) return;
+  const long long a = e / m, b = e - a * m;
+  if (a > b) G[e] = G[b * m + a];
+}
+
 }  // namespace
 
 struct TcClass {
@@ -1084,6 +1291,74 @@ bool tc_supported() {
   cudaDeviceProp p;
   if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return false;
   return p.major == 10 && p.minor == 3 && get_encode() != nullptr;
+}
+
+bool gram_tc_eligible(int prec, int mode, const void* const* A, long long D, long long m,
+                      long long n, long long lda) {
+  if (prec != 2 || mode != 1 || D < 1 || m < 1 || n < 1) return false;
+  if ((lda * 2) % 16 != 0 || lda > (1ll << 31) || n > (1ll << 31) || m > (1ll << 31))
+    return false;
+  for (long long d = 0; d < D; ++d)
+    if (((uintptr_t)A[d]) % 16 != 0) return false;
+  return tc_supported();
+}
+
+cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long long n,
+                           long long lda, double* G, int* status, long long spin_limit,
+                           cudaStream_t s) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+  if (!enc) return cudaErrorNotSupported;
+  std::vector<CUtensorMap> maps((size_t)D);
+  for (long long d = 0; d < D; ++d) {
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
+    cuuint64_t strides[1] = {(cuuint64_t)lda * 2};
+    cuuint32_t box[2] = {64, 128};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(&maps[(size_t)d], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                     const_cast<void*>(A[d]), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  int dev = 0, nsm = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int ntile = (int)((m + 127) / 128);
+  const long long ntp = (long long)ntile * (ntile + 1) / 2;
+  if (ntp > 65535 * 8) return cudaErrorInvalidValue;
+  long long splits = nsm / ntp;
+  if (splits > D) splits = D;
+  if (splits < 1) splits = 1;
+  void* dmaps = nullptr;
+  cudaError_t e = cudaMallocAsync(&dmaps, sizeof(CUtensorMap) * (size_t)D, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(dmaps, maps.data(), sizeof(CUtensorMap) * (size_t)D,
+                      cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // maps (host) is freed on return
+  GramParams prm;
+  prm.tmaps = (const CUtensorMap*)dmaps;
+  prm.D = D;
+  prm.m = m;
+  prm.n = n;
+  prm.G = G;
+  prm.ntile = ntile;
+  prm.splits = (int)splits;
+  prm.status = status;
+  prm.timeout_ns = std::max<long long>(spin_limit, 1) * 120;
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             G_SMEM);
+  if (e == cudaSuccess) {
+    gram_tc_kernel<<<dim3((unsigned)ntp, (unsigned)splits), GNT, G_SMEM, s>>>(prm);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    const long long tot = m * m;
+    mirror_upper_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(G, m);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(dmaps, s);
+  return e;
 }
 
 cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int count,

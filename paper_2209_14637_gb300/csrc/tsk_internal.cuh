@@ -139,6 +139,14 @@ cudaError_t launch_batch_loss(int count, const double* err, const double* normA2
 // k_tc.cu (tcgen05 / TMA kernels; BF16)
 struct TcPlan;
 bool tc_supported();
+// Mode-1 Gram of BF16 matrices on the tensor cores (A: host array of D device
+// pointers, 16-byte aligned, lda * 2 a multiple of 16); adds into G (m x m,
+// double) and mirrors its upper triangle into the lower one.
+bool gram_tc_eligible(int prec, int mode, const void* const* A, long long D, long long m,
+                      long long n, long long lda);
+cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long long n,
+                           long long lda, double* G, int* status, long long spin_limit,
+                           cudaStream_t s);
 cudaError_t tc_prepare(TcPlan** out, const MatDev* host_mats,
                        const MatDev* dev_mats, int count, int kp, void* dev_X,
                        void* dev_Y, double* dev_normA2,

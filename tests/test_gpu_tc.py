@@ -198,3 +198,23 @@ def test_automatic_refinement_where_the_bound_asks(tsk):
     Sn = _np(S)
     ref = np.array([oracle.scw(_np(A), Sn, r, dense=False)["err"] for A in As])
     assert np.max(np.abs(e2 - ref) / ref) <= GAP
+
+
+@pytest.mark.parametrize("m,n,D", [(320, 200, 11), (2048, 256, 20), (128, 64, 3)])
+def test_tc_gram_mode1(tsk, m, n, D):
+    """T1 on the tensor cores (BF16, mode 1) against the FP64 oracle on the
+    same stored values: ragged m (a partial 128-row tile) and n (a partial
+    64-column block), matrices split over CTAs (FP64 atomics) or not, and
+    more than two TMEM flush groups of eight matrices."""
+    g = torch.Generator(device="cuda").manual_seed(m + n + D)
+    T = [torch.randn(m, n, generator=g, device="cuda").to(torch.bfloat16) for _ in range(D)]
+    h = tsk.Handle()
+    G = _np(h.gram(T, mode=1))
+    assert h.sync_status() == 0
+    R = oracle.gram_mode1([_np(t) for t in T])
+    assert np.linalg.norm(G - R) <= 1e-5 * np.linalg.norm(R)
+    assert np.array_equal(G, G.T)
+    Gs = h.gram(T[:2], mode=1)
+    h.gram(T[2:], mode=1, out=Gs, accumulate=True)
+    assert np.linalg.norm(_np(Gs) - R) <= 1e-5 * np.linalg.norm(R)
+    h.close()
