@@ -749,6 +749,84 @@ cudaError_t launch_apply_rinv(bool dbl, const void* P, const void* R, void* Q,
   return cudaGetLastError();
 }
 
+// R (upper, p x p, row stride p) with R^T R = Gm (p x p, row stride p):
+// right-looking Cholesky in shared memory, one CTA, thread c updating column
+// c of the trailing triangle (one barrier per step).  A pivot at or below
+// 1e-12 of the largest diagonal entry makes that row of R the unit row e_j
+// (the column then passes through unchanged).
+template <typename T>
+__global__ void chol_upper_kernel(const T* __restrict__ Gm, int p, T* __restrict__ R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = (T*)smem_raw;  // p x (p + 1)
+  const int ld = p + 1, tid = threadIdx.x;
+  for (int e = tid; e < p * p; e += blockDim.x) {
+    const int a = e / p, c = e - a * p;
+    A[a * ld + c] = Gm[e];
+  }
+  __syncthreads();
+  T mx = T(0);
+  for (int a = 0; a < p; ++a) mx = A[a * ld + a] > mx ? A[a * ld + a] : mx;
+  const T thr = T(1e-12) * mx;
+  __syncthreads();
+  for (int j = 0; j < p; ++j) {
+    const T d = A[j * ld + j];
+    for (int c = j + 1 + tid; c < p; c += blockDim.x) {
+      if (d > thr) {
+        const T f = A[j * ld + c] / d;
+        for (int a = j + 1; a <= c; ++a) A[a * ld + c] -= A[j * ld + a] * f;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < p * p; e += blockDim.x) {
+    const int a = e / p, c = e - a * p;
+    const T d = A[a * ld + a];
+    T v = T(0);
+    if (c >= a) v = (d > thr) ? A[a * ld + c] / sqrt(d) : (c == a ? T(1) : T(0));
+    R[e] = v;
+  }
+}
+
+cudaError_t launch_chol_upper(bool dbl, const void* Gm, int p, void* R, cudaStream_t s) {
+  const size_t sh = (size_t)p * (p + 1) * (dbl ? sizeof(double) : sizeof(float));
+  cudaError_t e;
+  if (dbl) {
+    e = cudaFuncSetAttribute(chol_upper_kernel<double>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e != cudaSuccess) return e;
+    chol_upper_kernel<double><<<1, 256, sh, s>>>((const double*)Gm, p, (double*)R);
+  } else {
+    e = cudaFuncSetAttribute(chol_upper_kernel<float>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e != cudaSuccess) return e;
+    chol_upper_kernel<float><<<1, 256, sh, s>>>((const float*)Gm, p, (float*)R);
+  }
+  return cudaGetLastError();
+}
+
+// P[:, c] /= |theta_c| (theta_c != 0): a subspace-iteration block G U whose
+// columns are close to theta_c u_c becomes close to orthonormal.
+template <typename T>
+__global__ void scale_cols_kernel(T* __restrict__ P, long long rows, int p,
+                                  const T* __restrict__ theta) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * p) return;
+  const T t = theta[e % p];
+  const T a = t < T(0) ? -t : t;
+  if (a > T(0)) P[e] /= a;
+}
+
+cudaError_t launch_scale_cols(bool dbl, void* P, long long rows, int p, const void* theta,
+                              cudaStream_t s) {
+  const unsigned blocks = (unsigned)((rows * p + 255) / 256);
+  if (dbl)
+    scale_cols_kernel<double><<<blocks, 256, 0, s>>>((double*)P, rows, p,
+                                                     (const double*)theta);
+  else
+    scale_cols_kernel<float><<<blocks, 256, 0, s>>>((float*)P, rows, p, (const float*)theta);
+  return cudaGetLastError();
+}
+
 // res[c] = ||GU[:, c] - theta_c U[:, c]||_2 for c < k (one CTA per column).
 template <typename T>
 __global__ void ritz_residual_kernel(const T* __restrict__ U,

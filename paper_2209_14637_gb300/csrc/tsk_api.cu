@@ -781,8 +781,22 @@ extern "C" tsk_status tsk_sketch_from_gram(tsk_handle h, const double* G,
     if (e == cudaSuccess) e = launch_apply_rinv(dbl, P, R, P, dim, p, s);
     return e;
   };
+  // FP32: CholeskyQR2 of the block (its Gram, Cholesky, Z <- Z R^{-1}, twice),
+  // after scaling column c of G U by 1/theta_c, which leaves it close to
+  // orthonormal (G u_c ~ theta_c u_c), so the Gram is well conditioned.  FP64
+  // keeps the blockwise Householder factorisation.
+  auto orth2 = [&](void* P, const void* theta) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    if (theta) e = launch_scale_cols(dbl, P, dim, p, theta, s);
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+      e = launch_gemm(dbl, 1, 0, p, p, dim, 1.0, P, p, P, p, 0.0, H, p, s);
+      if (e == cudaSuccess) e = launch_chol_upper(dbl, H, p, R, s);
+      if (e == cudaSuccess) e = launch_apply_rinv(dbl, P, R, P, dim, p, s);
+    }
+    return e;
+  };
   TSK_E(launch_random_fill(dbl, Z, dim * p, 0x5eed5eedull, s));
-  TSK_E(orth(Z));
+  TSK_E(dbl ? orth(Z) : orth2(Z, nullptr));
   std::vector<double> hres(k), hth(p);
   std::vector<float> hthf(p);
   double best = 1e300;
@@ -819,7 +833,7 @@ extern "C" tsk_status tsk_sketch_from_gram(tsk_handle h, const double* G,
       converged = true;
       break;
     }
-    TSK_E(orth(GU));
+    TSK_E(dbl ? orth(GU) : orth2(GU, th));
     std::swap(Z, GU);
   }
   TSK_E(launch_emit_sketch(dbl, U, dim, p, k, S, s));

@@ -98,6 +98,10 @@ cudaError_t launch_random_fill(bool dbl, void* Z, long long count,
                                unsigned long long seed, cudaStream_t s);
 cudaError_t launch_apply_rinv(bool dbl, const void* P, const void* R,
                               void* Q, long long rows, int p, cudaStream_t s);
+// R^T R = Gm (p x p), R upper (one CTA); P[:, c] /= |theta_c|.
+cudaError_t launch_chol_upper(bool dbl, const void* Gm, int p, void* R, cudaStream_t s);
+cudaError_t launch_scale_cols(bool dbl, void* P, long long rows, int p, const void* theta,
+                              cudaStream_t s);
 cudaError_t launch_ritz_residual(bool dbl, const void* U, const void* GU,
                                  const void* theta, double* res,
                                  long long rows, int p, int k, cudaStream_t s);
