@@ -1318,14 +1318,14 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
                      const_cast<void*>(A[d]), dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    if (r != CUDA_SUCCESS) return cudaErrorNotSupported;  // nothing launched yet
   }
   int dev = 0, nsm = 148;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int ntile = (int)((m + 127) / 128);
   const long long ntp = (long long)ntile * (ntile + 1) / 2;
-  if (ntp > 65535 * 8) return cudaErrorInvalidValue;
+  if (ntp > 65535 * 8) return cudaErrorNotSupported;
   long long splits = nsm / ntp;
   if (splits > D) splits = D;
   if (splits < 1) splits = 1;

@@ -702,10 +702,15 @@ extern "C" tsk_status tsk_gram(tsk_handle h, const void* const* A, int64_t D,
   const int64_t dim = (mode == 1) ? m : n;
   if (!accumulate) TSK_CUDA(h, cudaMemsetAsync(G, 0, sizeof(double) * dim * dim, s));
   if (h->opts.kernel != TSK_KERNEL_SIMT && gram_tc_eligible((int)prec, mode, A, D, m, n, lda)) {
-    // BF16 mode 1: tcgen05 SYRK (FP32 in TMEM, FP64 in G)
-    TSK_CUDA(h, launch_gram_tc(A, D, m, n, lda, G, h->d_status, h->opts.spin_limit, s));
-    TSK_CUDA(h, cudaStreamSynchronize(s));
-    return TSK_OK;
+    // BF16 mode 1: tcgen05 SYRK (FP32 in TMEM, FP64 in G); shapes whose
+    // tensor maps cannot be encoded go to the CUDA-core kernel below
+    const cudaError_t ge =
+        launch_gram_tc(A, D, m, n, lda, G, h->d_status, h->opts.spin_limit, s);
+    if (ge != cudaErrorNotSupported) {
+      TSK_CUDA(h, ge);
+      TSK_CUDA(h, cudaStreamSynchronize(s));
+      return TSK_OK;
+    }
   }
   void* dA = nullptr;
   TSK_CUDA(h, cudaMallocAsync(&dA, sizeof(void*) * D, s));

@@ -145,7 +145,9 @@ struct TcPlan;
 bool tc_supported();
 // Mode-1 Gram of BF16 matrices on the tensor cores (A: host array of D device
 // pointers, 16-byte aligned, lda * 2 a multiple of 16); adds into G (m x m,
-// double) and mirrors its upper triangle into the lower one.
+// double) and mirrors its upper triangle into the lower one.  Returns
+// cudaErrorNotSupported, having launched nothing, when a tensor map cannot be
+// encoded for these shapes.
 bool gram_tc_eligible(int prec, int mode, const void* const* A, long long D, long long m,
                       long long n, long long lda);
 cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long long n,
