@@ -152,7 +152,10 @@ tsk_status tsk_sync_status(tsk_handle h, tsk_stream stream);
    to G instead of overwriting it, so partial Gram matrices of disjoint
    training shards can be summed (the one exchange step of a multi-GPU
    training side).  Products are accumulated in the precision's compute type
-   (double for TSK_FP64, float otherwise) and summed into G in double. */
+   (double for TSK_FP64, float otherwise) and summed into G in double.
+   TSK_BF16 mode 1 with 16-byte aligned rows (lda * 2 a multiple of 16,
+   16-byte aligned A[d]) runs on the tensor cores (FP32 accumulation over
+   eight matrices at a time) and leaves G exactly symmetric. */
 tsk_status tsk_gram(tsk_handle h, const void* const* A, int64_t D, int64_t m,
                     int64_t n, int64_t lda, tsk_prec prec, int32_t mode,
                     double* G, int32_t accumulate, tsk_stream stream);

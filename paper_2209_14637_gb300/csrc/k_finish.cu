@@ -4,12 +4,14 @@
 // From the panels X (n x k) and Y = A X (m x k) written by the sketch pass:
 //
 //   R1   = chol(X^T X)                        (X = Q R_X)
-//   Q1   = X R1^{-1},  M1 = Y R1^{-1}         (one streaming pass over both)
-//   R2   = chol(Q1^T Q1)                      (one CholeskyQR2 step)
-//   G_M  = R2^{-T} (M1^T M1) R2^{-1} = M^T M,  M = Y R_X^{-1} = A Q,
-//          R_X = R2 R1
-//   sigma_i(AQ)^2 = lambda_i(G_M),  V = eigenvectors,  W = R_X^{-1} V_r
+//   M1   = Y R1^{-1},  G_M = M1^T M1          (streamed)
+//   sigma_i(AQ)^2 = lambda_i(G_M),  V = eigenvectors,  W = R1^{-1} V_r
 //   err^2 = ||A||^2 - sum_{i<=r} v_i^T G_M v_i (Eq. A.3; Ky Fan)
+//
+// and, where the first-order bound on the energy's change from the FP32
+// rounding of X^T X asks for it (or always, refine = 1), one CholeskyQR2
+// step: Q1 = X R1^{-1} streamed, R2 = chol(Q1^T Q1), G_M <- R2^{-T} G_M
+// R2^{-1}, R_X^{-1} = R1^{-1} R2^{-1}, and the eigenpairs again.
 //
 // Y itself is never factored: its columns scale like sigma_i^2 and Y^T Y
 // would lose everything in FP32.  M1 = A Q1 is as well conditioned as A Q,
