@@ -181,6 +181,74 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+def _timed_plan(plan, steps, ws, dist, probe=True):
+    """Executes a plan `steps` times between barriers; returns the total
+    device time (CUDA events on the launching stream) and the per-execution
+    sketch-pass times (event-record nodes inside the plan's graph)."""
+    import torch
+    evb = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    eve = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for e in evb + eve:
+        e.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record()
+    for i in range(steps):
+        if probe:
+            plan.set_probe(evb[i], eve[i])
+        plan.execute()
+    t_end.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    stage_ms = [b.elapsed_time(e) for b, e in zip(evb, eve)] if probe else []
+    if probe:
+        plan.set_probe(None, None)
+    return total_ms, stage_ms
+
+
+def _max_over_ranks(v, ws, dist):
+    import torch
+    t = torch.tensor([v], device="cuda", dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sgemm_peak():
+    """FP32 FMA peak of this GPU, measured: a CUDA-core SGEMM (cuBLAS,
+    TF32 off) of 8192^3, best of 5, as the BF16 denominator is measured
+    with a cuBLAS GEMM."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        n = 8192
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        c = torch.empty(n, n, device="cuda")
+        for _ in range(2):
+            torch.matmul(a, b, out=c)
+        best = 1e30
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b, c
+        return 2.0 * n ** 3 / (best / 1e3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def run_tsk(args):
     import numpy as np
     import torch
@@ -201,7 +269,9 @@ def run_tsk(args):
     peaks, peak_src = load_peaks()
     spec = synth.C3
     count = args.matrices if args.matrices > 0 else spec.n_test
-    h = tsk.Handle(kernel=args.kernel)
+    refine = {"always": tsk.REFINE_ALWAYS, "auto": tsk.REFINE_AUTO,
+              "never": tsk.REFINE_NEVER}[args.refine]
+    h = tsk.Handle(kernel=args.kernel, refine_q=refine)
 
     # ---- training side (timed separately, not part of the metric) --------
     from paper_2209_14637_gb300.dist import allreduce_gram, shard_range
@@ -218,8 +288,9 @@ def run_tsk(args):
     S, eig, st = h.sketch_from_gram(G, spec.k, prec=tsk.BF16)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    # the Gram (T1) once more, timed on the device: a tensor-bound SYRK of
-    # m^2 n multiply-adds' worth of flops per matrix (half of 2 m^2 n)
+    # the Gram (T1) once more, timed on the device (its tensor maps are
+    # cached by the handle, so this is the kernel's time): a tensor-bound
+    # SYRK of m^2 n multiply-adds' worth of flops per matrix (half of 2 m^2 n)
     g0 = torch.cuda.Event(enable_timing=True)
     g1 = torch.cuda.Event(enable_timing=True)
     g0.record()
@@ -234,7 +305,7 @@ def run_tsk(args):
                   "gram_kernel": "tcgen05" if args.kernel != tsk.KERNEL_SIMT else "simt",
                   "roofline": {"bound": "tensor", "achieved": gram_tf, "peak": gpeak,
                                "unit": "TFLOP/s", "frac": gram_tf / gpeak,
-                               "peak_source": "bf16_tflops of " + peak_src,
+                               "peak_source": "bf16_tflops (burst) of " + peak_src,
                                "flops": gram_flops}}
     stage(f"training Gram: {train_info}")
     del tr, G
@@ -249,45 +320,16 @@ def run_tsk(args):
     plan_kind = "tcgen05" if te.dtype == torch.bfloat16 and args.kernel != tsk.KERNEL_SIMT else "simt"
     stage(f"plan ready: {info}")
 
-    def timed(plan_, steps, probe=True):
-        evb = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        eve = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        for e in evb + eve:
-            e.record()
-        torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_start.record()
-        for i in range(steps):
-            if probe:
-                plan_.set_probe(evb[i], eve[i])
-            plan_.execute()
-        t_end.record()
-        torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
-        total_ms = t_start.elapsed_time(t_end)
-        stage_ms = [b.elapsed_time(e) for b, e in zip(evb, eve)] if probe else []
-        if probe:
-            plan_.set_probe(None, None)
-        return total_ms, stage_ms
-
     for _ in range(args.warmup):
         plan.execute()
     torch.cuda.synchronize()
-    stage("timing the BF16 path")
+    stage(f"timing the BF16 path (refine {args.refine})")
     clocks = ClockSampler(local)
     clocks.start()
-    total_ms, stage_ms = timed(plan, args.steps)
+    total_ms, stage_ms = _timed_plan(plan, args.steps, ws, dist)
     clk = clocks.stop()
     assert h.sync_status() == 0
-    t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
+    max_ms = _max_over_ranks(total_ms, ws, dist)
     value = count * ws * args.steps / (max_ms / 1e3)
     ms_per_step = max_ms / args.steps
     stage_avg = statistics.mean(stage_ms)
@@ -297,25 +339,56 @@ def run_tsk(args):
     achieved = alg_bytes / (stage_avg / 1e3) / 1e9
     peak = float(peaks["hbm_gbs"])
 
+    def side_variant(hv, steps):
+        """Matrices/s of the same workload through another handle setting."""
+        pv = hv.plan(te, S, spec.r, torch.empty(count, dtype=torch.float64, device="cuda"))
+        for _ in range(max(1, args.warmup)):
+            pv.execute()
+        ms, _ = _timed_plan(pv, steps, ws, dist, probe=False)
+        ms = _max_over_ranks(ms, ws, dist)
+        pv.close()
+        return {"value": count * ws * steps / (ms / 1e3), "unit": "matrices/s",
+                "ms_per_step": ms / steps, "steps": steps}
+
+    variants = {}
+    if not args.no_variants:
+        # the adaptive refinement (only matrices whose rounding bound asks)
+        ha = tsk.Handle(kernel=args.kernel, refine_q=tsk.REFINE_AUTO)
+        variants["refine_auto"] = side_variant(ha, args.steps)
+        ha.close()
+        # the k x k steps in FP64 (Householder R factors + Jacobi SVD in double)
+        hd = tsk.Handle(kernel=args.kernel, refine_q=refine, small_fp64=True)
+        variants["small_fp64"] = side_variant(hd, max(1, min(args.steps, 5)))
+        hd.close()
+        stage(f"variants: {variants}")
+
     # ---- plain FP32 path on the same matrices ----------------------------
     fp32 = None
+    sgemm = None
     if not args.no_fp32:
         stage("timing the FP32 path")
         te32 = te.float()
         err32 = torch.empty(count, dtype=torch.float64, device="cuda")
-        h32 = tsk.Handle()
+        h32 = tsk.Handle(refine_q=refine)
         plan32 = h32.plan(te32, S, spec.r, err32)
         for _ in range(max(1, args.warmup)):
             plan32.execute()
         steps32 = max(1, min(args.steps, 10))
-        ms32, st32 = timed(plan32, steps32)
-        t = torch.tensor([ms32], device="cuda", dtype=torch.float64)
-        if ws > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms32 = float(t.item())
+        ms32, st32 = _timed_plan(plan32, steps32, ws, dist)
+        ms32 = _max_over_ranks(ms32, ws, dist)
+        sgemm = _sgemm_peak()
+        sk32 = statistics.mean(st32)
+        flops32 = 4.0 * spec.m * spec.n * spec.k * count
         fp32 = {"value": count * ws * steps32 / (ms32 / 1e3), "unit": "matrices/s",
                 "ms_per_step": ms32 / steps32, "steps": steps32,
-                "sketch_pass_ms": statistics.mean(st32)}
+                "sketch_pass_ms": sk32,
+                "roofline": {"bound": "alu", "achieved": flops32 / (sk32 / 1e3) / 1e12,
+                             "peak": sgemm, "unit": "TFLOP/s",
+                             "frac": flops32 / (sk32 / 1e3) / 1e12 / sgemm,
+                             "peak_source": "FP32 SGEMM (cuBLAS, TF32 off) 8192^3 "
+                                            "measured in this run",
+                             "kernel": "CUDA-core sketch pass (X = A^T S^T, Y = A X)",
+                             "flops": flops32}}
         stage(f"fp32: {fp32}")
 
     # ---- end to end through the public API with host buffers -------------
@@ -335,11 +408,11 @@ def run_tsk(args):
         cplans = [h.plan(te[bnd[i]:bnd[i + 1]], S, spec.r, err[bnd[i]:bnd[i + 1]])
                   for i in range(nch)]
         cs = torch.cuda.Stream()
-        main = torch.cuda.current_stream()
+        main_s = torch.cuda.current_stream()
         copied = [torch.cuda.Event() for _ in range(nch)]
         consumed = [torch.cuda.Event() for _ in range(nch)]
         for ev in consumed:
-            ev.record(main)
+            ev.record(main_s)
 
         def e2e_step():
             for i in range(nch):
@@ -348,9 +421,9 @@ def run_tsk(args):
                     te[bnd[i]:bnd[i + 1]].copy_(host[bnd[i]:bnd[i + 1]], non_blocking=True)
                 copied[i].record(cs)
             for i in range(nch):
-                main.wait_event(copied[i])
+                main_s.wait_event(copied[i])
                 cplans[i].execute()
-                consumed[i].record(main)
+                consumed[i].record(main_s)
             err_host.copy_(err, non_blocking=True)
 
         steps_e = max(1, min(args.steps, 5))
@@ -366,11 +439,7 @@ def run_tsk(args):
             e2e_step()
         b_ev.record()
         torch.cuda.synchronize()
-        ms_e = a_ev.elapsed_time(b_ev)
-        t = torch.tensor([ms_e], device="cuda", dtype=torch.float64)
-        if ws > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e = float(t.item())
+        ms_e = _max_over_ranks(a_ev.elapsed_time(b_ev), ws, dist)
         e2e = {"value": count * ws * steps_e / (ms_e / 1e3), "unit": "matrices/s",
                "h2d_bytes_per_step": int(alg_bytes), "d2h_bytes_per_step": 8 * count,
                "steps": steps_e, "host_buffer": "page-locked (cudaHostAlloc)",
@@ -382,33 +451,59 @@ def run_tsk(args):
         del host
 
     # ---- oracle on a bounded sample: CPU baseline and the error gap ------
+    # The oracle trains its own sketch (16 training matrices) and runs SCW
+    # on a sample of the test matrices; the GPU paths run the same sample
+    # with that sketch (rounded to float32, the sketch type of the BF16 and
+    # FP32 paths), so no oracle input comes from the GPU.
     cpu = None
     gap = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         stage("oracle sample on the host cores")
         import oracle
-        Sn = S.double().cpu().numpy()
+        tr_o = synth.stream(spec, "train", device="cuda", count=16)
+        S_o, _, _, _ = oracle.train_sketch(list(tr_o.double().cpu().numpy()), spec.k)
+        del tr_o
+        S_o32 = torch.tensor(S_o, device="cuda", dtype=torch.float32)
+        Sn = S_o32.double().cpu().numpy()
         idx = list(range(0, count, max(1, count // args.cpu_sample)))[:args.cpu_sample]
         mats = [te[i].double().cpu().numpy() for i in idx]
         t0 = time.perf_counter()
-        ref = [oracle.scw(A, Sn, spec.r, dense=False)["err"] for A in mats]
+        ref = np.array([oracle.scw(A, Sn, spec.r, dense=False)["err"] for A in mats])
         dt = time.perf_counter() - t0
         cpu = {"value": len(mats) / dt, "unit": "matrices/s", "cores": cpu_threads(),
                "kind": "oracle",
                "sample": f"{len(mats)} of the {count} test matrices, FP64 numpy SCW"}
-        plan.execute()
-        torch.cuda.synchronize()
-        g = err.cpu().numpy()[idx]
-        gap = {"bf16": float(np.max(np.abs(g - ref) / np.asarray(ref)))}
-        if fp32 is not None:
-            plan32.execute()
+        sub = te[idx]
+        gap = {}
+        runs = [("bf16", dict(refine_q=refine), sub),
+                ("bf16_small_fp64", dict(refine_q=refine, small_fp64=True), sub),
+                ("bf16_refine_auto", dict(refine_q=tsk.REFINE_AUTO), sub),
+                ("fp32", dict(refine_q=refine), sub.float())]
+        got = {}
+        for name, kw, A in runs:
+            hv = tsk.Handle(kernel=args.kernel, **kw)
+            o = hv.approx_batch(A, S_o32, spec.r)
             torch.cuda.synchronize()
-            g32 = err32.cpu().numpy()[idx]
-            gap["fp32"] = float(np.max(np.abs(g32 - ref) / np.asarray(ref)))
+            assert hv.sync_status() == 0
+            got[name] = o["err"].cpu().numpy()
+            gap[name] = float(np.max(np.abs(got[name] - ref) / ref))
+            hv.close()
+        # the k x k steps in FP32 against the same steps in FP64, on the
+        # same BF16 panels
+        gap["fp32_vs_fp64_kxk"] = float(np.max(np.abs(got["bf16"] - got["bf16_small_fp64"])
+                                               / got["bf16_small_fp64"]))
         gap["checked"] = len(mats)
+        gap["sketch"] = "oracle's, from 16 training matrices (FP64 Gram + eigh)"
         stage(f"oracle: {cpu}; gap {gap}")
 
+    extra = {}
+    if not args.no_extra:
+        extra = run_extra_workloads(args, tsk, h, sgemm, peaks, ws, dist, rank)
+
     if rank == 0:
+        traffic = None
+        if plan_kind == "tcgen05" and (spec.m, spec.n, spec.k) == (2048, 2048, 40):
+            traffic = SKETCH_TRAFFIC_PER_MATRIX * count
         line = {
             "metric": "stream matrices/s, rank-r SCW (BF16 vs FP32 path) at rel-err gap <=1e-3",
             "value": value, "unit": "matrices/s", "n_gpus": ws,
@@ -416,9 +511,12 @@ def run_tsk(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16", "data": "synthetic",
             "config": {"workload": f"C3 test pass: {count} stream matrices 2048x2048 BF16 "
-                                   "per GPU, k=40, r=20, sketch trained on "
+                                   "per GPU, k=40, r=20, one refinement step on Q per "
+                                   f"matrix (refine={args.refine}), sketch trained on "
                                    f"{args.train} matrices of the stream",
                        "m": spec.m, "n": spec.n, "k": spec.k, "r": spec.r,
+                       "refine": args.refine,
+                       "small_factors": "fp32 (Gram route); fp64 timed in small_fp64",
                        "matrices_per_step_per_gpu": count,
                        "l2": f"inputs ({alg_bytes / 1e9:.2f} GB per step) larger than "
                              "L2 (129 MB); no flush",
@@ -429,22 +527,23 @@ def run_tsk(args):
                          "kernel": "sketch pass (X = A^T S^T, Y = A X)",
                          "kernel_ms": stage_avg,
                          "algorithmic_bytes": alg_bytes,
-                         "traffic": (SKETCH_TRAFFIC_PER_MATRIX * count
-                                     if plan_kind == "tcgen05" else None),
+                         "traffic": traffic,
                          "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum "
-                                            "of one 64-matrix launch, scaled to this launch "
-                                            "by the number of matrices"
-                                            if plan_kind == "tcgen05" else None)},
+                                            "of one 64-matrix launch of this shape, scaled to "
+                                            "this launch by the number of matrices"
+                                            if traffic is not None else None)},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,
             "gpu_launches": info["launches"] * args.steps,
             "fp32_path": fp32,
+            "variants": variants,
             "rel_err_gap": gap,
             "train_s": train_s,
             "train": train_info,
             "train_status": st,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if fp32 is not None:
         plan32.close()
@@ -454,6 +553,175 @@ def run_tsk(args):
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def _optimal_errors(As, r):
+    """||A - A_r||_F of the best rank-r approximation (Eckart-Young): the
+    reference the test error (Eq. 4.1) is measured against.  A plain
+    singular-value routine in float64 (reporting, not part of the path)."""
+    import torch
+    out = []
+    for A in As:
+        A64 = A.detach().to(torch.float64)
+        try:
+            s = torch.linalg.svdvals(A64)
+        except Exception:  # no device linear-algebra library: use the host
+            s = torch.linalg.svdvals(A64.cpu())
+        out.append(float(torch.sqrt(torch.sum(s[r:] ** 2))))
+    return out
+
+
+def _test_error(errs, opt):
+    """Eq. 4.1: the mean over the test set of (err - opt) / opt."""
+    return float(sum((e - o) / o for e, o in zip(errs, opt)) / len(opt))
+
+
+def run_extra_workloads(args, tsk, h, sgemm, peaks, ws, dist, rank):
+    """The other workloads of the method, each under its own key: C2 (FP32,
+    1024 x 768), C4 (512 ragged BF16 matrices in one plan), C5 (the learned
+    refiner), the classical random sketches (Gaussian, sign) against the
+    tensor sketch, and the training-fraction sweep."""
+    import dataclasses
+
+    import torch
+
+    import synth
+    out = {}
+    peak_hbm = float(peaks["hbm_gbs"])
+
+    def timed_value(plan, n, steps, probe=True):
+        for _ in range(max(1, args.warmup)):
+            plan.execute()
+        ms, st = _timed_plan(plan, steps, ws, dist, probe=probe)
+        ms = _max_over_ranks(ms, ws, dist)
+        return n * ws * steps / (ms / 1e3), ms / steps, (statistics.mean(st) if st else None)
+
+    # ---- C2: plain FP32 path, HSI shape --------------------------------
+    spec2 = synth.C2
+    stage("C2: training on 400 FP32 matrices")
+    tr2 = synth.stream(spec2, "train", device="cuda")
+    h2 = tsk.Handle(refine_q=tsk.REFINE_ALWAYS)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S2, _, _, st2 = h2.train_sketch(tr2, spec2.k)
+    torch.cuda.synchronize()
+    train2_s = time.perf_counter() - t0
+    te2 = synth.stream(spec2, "test", device="cuda")
+    err2 = torch.empty(spec2.n_test, dtype=torch.float64, device="cuda")
+    p2 = h2.plan(te2, S2, spec2.r, err2)
+    v2, ms2, sk2 = timed_value(p2, spec2.n_test, args.steps)
+    flops2 = 4.0 * spec2.m * spec2.n * spec2.k * spec2.n_test
+    opt2 = _optimal_errors(te2[:50], spec2.r)
+    c2 = {"value": v2, "unit": "matrices/s", "ms_per_step": ms2, "dtype": "f32",
+          "workload": "C2: 200 FP32 1024x768 matrices per step, k=20, r=10, sketch from "
+                      "400 training matrices, one refinement step per matrix",
+          "train_s": train2_s, "train_status": st2,
+          "test_error_4_1": _test_error(err2[:50].tolist(), opt2),
+          "roofline": ({"bound": "alu", "achieved": flops2 / (sk2 / 1e3) / 1e12,
+                        "peak": sgemm, "unit": "TFLOP/s",
+                        "frac": flops2 / (sk2 / 1e3) / 1e12 / sgemm,
+                        "peak_source": "FP32 SGEMM (cuBLAS, TF32 off) measured in this run",
+                        "kernel": "CUDA-core sketch pass", "flops": flops2}
+                       if sgemm else None)}
+    # NEXT-4: the data-oblivious sketches of classical SCW on the same matrices
+    rnd = {"tensor": c2["test_error_4_1"]}
+    for kind in ("gauss", "sign"):
+        Sr = synth.random_sketch(kind, spec2.k, spec2.m, spec2.seed, device="cuda")
+        e = h2.approx_batch(te2[:50], Sr, spec2.r)["err"]
+        rnd[kind] = _test_error(e.tolist(), opt2)
+    out["c2"] = c2
+    out["random_sketch_test_error"] = dict(rnd, matrices=50, workload="C2")
+    stage(f"C2: {c2}; random sketches {rnd}")
+    p2.close()
+    del tr2
+
+    # NEXT-3: training fraction (2 %, 20 %, 80 % of a 600-matrix C2 stream),
+    # the Gram accumulated chunk by chunk as the stream arrives
+    pool = dataclasses.replace(spec2, n_train=500, n_test=100)
+    teP = synth.stream(pool, "test", device="cuda", count=50)
+    optP = _optimal_errors(teP, pool.r)
+    sweep = {}
+    G = None
+    done = 0
+    for frac in (0.02, 0.2, 0.8):
+        want = int(round(frac * 600))
+        while done < want:
+            c = min(want - done, 60)
+            chunk = synth.stream(pool, "train", device="cuda", start=done, count=c)
+            G = h2.gram([chunk[i] for i in range(c)], mode=1, out=G, accumulate=G is not None)
+            done += c
+        Sf, _, _ = h2.sketch_from_gram(G, pool.k, prec=tsk.FP32)
+        e = h2.approx_batch(teP, Sf, pool.r)["err"]
+        sweep[f"{int(frac * 100)}%"] = {"train_matrices": want,
+                                        "test_error_4_1": _test_error(e.tolist(), optP)}
+    out["sample_ratio"] = dict(sweep, test_matrices=50, stream=600, workload="C2 stream")
+    stage(f"sample ratio: {out['sample_ratio']}")
+    h2.close()
+    del te2, teP
+    torch.cuda.empty_cache()
+
+    # ---- C4: 512 ragged BF16 matrices in one plan -----------------------
+    stage("C4: generating 512 ragged matrices")
+    items = synth.ragged_sizes(512)
+    S4 = [synth.item_sketch(it, device="cuda") for it in items]
+    r4 = [it.r for it in items]
+    c4 = {"workload": "C4: 512 BF16 matrices per step, m in [256, 4096], n in [256, 2048] "
+                      "log-uniform, k in {10, 20, 40}, r = k/2, one refinement step each",
+          "unit": "matrices/s"}
+    for pad in (True, False):
+        A4 = synth.ragged_batch(items, device="cuda", pad_rows=pad)
+        alg4 = float(sum(it.m * it.n * 2 for it in items))
+        h4 = tsk.Handle(refine_q=tsk.REFINE_ALWAYS)
+        e4 = torch.empty(len(items), dtype=torch.float64, device="cuda")
+        p4 = h4.plan(A4, S4, r4, e4)
+        inf4 = p4.info()
+        v4, ms4, sk4 = timed_value(p4, len(items), args.steps)
+        key = "padded_rows" if pad else "contiguous_rows"
+        c4[key] = {"value": v4, "ms_per_step": ms4, "sketch_pass_ms": sk4,
+                   "launches": inf4["launches"],
+                   "tensor_core_matrices": sum((A.stride(0) * 2) % 16 == 0 for A in A4),
+                   "roofline": {"bound": "hbm", "achieved": alg4 / (sk4 / 1e3) / 1e9,
+                                "peak": peak_hbm, "unit": "GB/s",
+                                "frac": alg4 / (sk4 / 1e3) / 1e9 / peak_hbm,
+                                "algorithmic_bytes": alg4,
+                                "kernel": "sketch pass"}}
+        p4.close()
+        h4.close()
+        del A4
+    out["c4"] = c4
+    stage(f"C4: {c4}")
+    del S4
+    torch.cuda.empty_cache()
+
+    # ---- C5: the learned refiner ------------------------------------------
+    spec5 = synth.C5
+    stage("C5: refiner")
+    tr5 = synth.stream(spec5, "train", device="cuda")
+    te5 = synth.stream(spec5, "test", device="cuda")
+    h5 = tsk.Handle()
+    S5, _, _, _ = h5.train_sketch(tr5, spec5.k)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dS, hist = h5.refine_sketch(tr5[:350], tr5[350:], S5, spec5.r, steps=args.c5_steps,
+                                batch=16, lr=1e-3, eval_every=100)
+    torch.cuda.synchronize()
+    dt5 = time.perf_counter() - t0
+    opt5 = _optimal_errors(te5[:50], spec5.r)
+    plain = h5.approx_batch(te5[:50], S5, spec5.r)["err"].tolist()
+    refined = h5.approx_batch(te5[:50], S5 + dS, spec5.r)["err"].tolist()
+    out["c5"] = {"workload": "C5: refiner S_theta = S_tensor + dS, 1024x768 FP32, k=20, "
+                             f"r=10, SGD batch 16, lr 1e-3, {args.c5_steps} steps on 350 "
+                             "training matrices, validation on 50",
+                 "steps_per_s": args.c5_steps / dt5, "train_s": dt5,
+                 "val_loss_first_best": [hist[0], min(hist)],
+                 "held_out_test_error_4_1": {"tensor": _test_error(plain, opt5),
+                                             "refined": _test_error(refined, opt5),
+                                             "matrices": 50},
+                 "held_out_mean_err": {"tensor": sum(plain) / 50, "refined": sum(refined) / 50,
+                                       "optimal": sum(opt5) / 50}}
+    stage(f"C5: {out['c5']}")
+    h5.close()
+    return out
 
 
 def main():
@@ -476,6 +744,14 @@ def main():
     ap.add_argument("--e2e-chunks", type=int, default=4,
                     help="chunks the end-to-end leg streams and computes in overlap")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the refine_auto and small_fp64 timings")
+    ap.add_argument("--c5-steps", type=int, default=2000)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the C2, C4 and C5 workloads")
+    ap.add_argument("--refine", default="always", choices=["always", "auto", "never"],
+                    help="refinement of Q on the headline path (the workload states one "
+                         "step per matrix)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

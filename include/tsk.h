@@ -35,10 +35,13 @@
  *     two host threads at the same time.
  *   - Requirements on sizes: 1 <= r <= k <= min(m, n) (thin QR of the n x k
  *     matrix (SA)^T needs k <= n; Theorem 1 needs k > r for its bound but
- *     r = k is accepted) and k <= TSK_MAX_K.  The tensor-core path also
- *     needs k <= 48, m <= 4096, A and S 16-byte aligned and lda * element
- *     size a multiple of 16 bytes; the SIMT paths need only natural
- *     alignment.
+ *     r = k is accepted) and k <= TSK_MAX_K.  The tensor-core sketch of a
+ *     BF16 matrix also needs k <= 48, m <= 4096, a 16-byte aligned A and
+ *     lda * 2 a multiple of 16 bytes (TMA moves rows that start on 16-byte
+ *     boundaries); with TSK_KERNEL_AUTO the BF16 matrices of a batch that
+ *     miss one of these go to the CUDA-core sketch kernels, in the same
+ *     plan and concurrently with the rest.  The CUDA-core paths need only
+ *     natural alignment.
  */
 #ifndef TSK_H_
 #define TSK_H_
@@ -99,6 +102,17 @@ typedef struct {
   double eig_tol;     /* eigensolver residual tolerance relative to lambda_1;
                          0 selects 1e-13 (FP64) or 2e-6 (FP32/BF16)           */
   int64_t spin_limit; /* iteration bound of every device spin-wait (1<<24)    */
+  int32_t small_fp64; /* FP32 / BF16 paths only: 0 (default) takes the small
+                         factors by the FP32 Gram route (Cholesky of X^T X,
+                         one-sided Jacobi on the Cholesky factor of M^T M, M =
+                         A Q; only the energy and the error in double); 1
+                         takes them in double: blockwise Householder QR of the
+                         X and Y panels (read from the FP32 panels, one
+                         refinement pass) and one-sided Jacobi SVD of the k x k
+                         R_Y R_X^{-1}, as on the TSK_FP64 path.  Slower (the
+                         Householder steps are serial); it exists to run the
+                         k x k steps in FP64 where a configuration asks.     */
+  int32_t reserved;   /* must be 0                                            */
 } tsk_options;
 
 /* One test-side matrix.  A: device, m x n, leading dimension lda >= n.
@@ -283,21 +297,33 @@ tsk_status tsk_refine_sketch(tsk_handle h, const tsk_mat_desc* train,
    advance.  No handle is needed and nothing is allocated: every intermediate
    lives in a file-scope __device__ array of TSK_NOALLOC_SCRATCH_BYTES (8 MiB)
    that each GPU which loads the library holds until the process exits.
-   Matrices needing more than that ((m + n) * k_pad * element size plus a few
-   KB of descriptors, k_pad = k rounded up to 16) are rejected with
-   TSK_EINVAL and a message in tsk_last_error(NULL).
+   Matrices needing more than that (2 (m + n) * k_pad * element size plus a
+   few KB of descriptors, k_pad = k rounded up to 16, element size 8 for
+   TSK_FP64 and 4 otherwise: the X and Y panels and the factors of the
+   direct-error pass; for example m + n up to 21,800 at k = 48 in FP32) are
+   rejected with TSK_EINVAL and a message in tsk_last_error(NULL).
    mat: host pointer to the descriptor (device A and S as for
    tsk_approx_batch; any of the three precisions, always the CUDA-core
    kernels).  err: device, one double; normA2: device, one double, nullable.
+   status: device, one int32, nullable; when given it receives, once the
+   work has run, the device status of this call: 0, or TSK_ERANKDEF when S A
+   had rank < k (the error is then that of Householder's completion of the
+   basis), or TSK_ETIMEOUT.  Errors follow the default err_mode of
+   tsk_approx_batch: the projection identity, then a direct pass over A
+   when the identity cancels (err^2 < tau ||A||^2, tau = 1e-6 for TSK_FP64,
+   1e-4 otherwise).
    The first call on each device looks up the array's device address with
    cudaGetSymbolAddress while that device is current, so make that first call
-   before any stream capture.  All calls share the one array and it keeps the
+   before any stream capture; later calls outside a capture look it up again
+   (cheap once the module is loaded), so the address stays valid after the
+   device's context has been reset and the module reloaded.  All calls share the one array and it keeps the
    previous call's contents (the call clears what it accumulates into): calls
    that overlap on the GPU -- on two streams, or from two host threads --
    race and corrupt each other's results.  Asynchronous on stream; other
    errors as in the rest of this header (tsk_last_error(NULL) has the text). */
 tsk_status tsk_approx_noalloc(const tsk_mat_desc* mat, tsk_prec prec,
-                              double* err, double* normA2, tsk_stream stream);
+                              double* err, double* normA2, int32_t* status,
+                              tsk_stream stream);
 
 #ifdef __cplusplus
 }

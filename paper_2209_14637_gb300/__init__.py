@@ -45,7 +45,8 @@ class TskError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("refine_q", C.c_int32),
                 ("max_iter", C.c_int32), ("err_mode", C.c_int32),
-                ("eig_tol", C.c_double), ("spin_limit", C.c_int64)]
+                ("eig_tol", C.c_double), ("spin_limit", C.c_int64),
+                ("small_fp64", C.c_int32), ("reserved", C.c_int32)]
 
 
 class MatDesc(C.Structure):
@@ -98,7 +99,7 @@ def load_library(path: str = LIB_PATH):
         "tsk_plan_set_probe": ([P, P, P], I32),
         "tsk_error": ([P, I64, C.POINTER(MatDesc), I32, C.POINTER(MatOut), P, P], I32),
         "tsk_ivy_grad": ([P, I64, C.POINTER(MatDesc), I32, P, P, P, P], I32),
-        "tsk_approx_noalloc": ([C.POINTER(MatDesc), I32, P, P, P], I32),
+        "tsk_approx_noalloc": ([C.POINTER(MatDesc), I32, P, P, P, P], I32),
         "tsk_default_refine_options": ([C.POINTER(RefineOpts)], None),
         "tsk_refine_sketch": ([P, C.POINTER(MatDesc), I64, C.POINTER(MatDesc), I64, I32,
                                C.POINTER(RefineOpts), P, P, C.POINTER(D), P], I32),
@@ -137,13 +138,15 @@ class Handle:
 
     def __init__(self, kernel: int = KERNEL_AUTO, refine_q: int = REFINE_AUTO,
                  max_iter: int = 300, eig_tol: float = 0.0,
-                 spin_limit: int = 1 << 24, err_mode: int = 0):
+                 spin_limit: int = 1 << 24, err_mode: int = 0,
+                 small_fp64: bool = False):
         lib = load_library()
         if not torch.cuda.is_available():
             raise RuntimeError("libtsk needs a CUDA device; none is available")
         o = default_options()
         o.kernel, o.refine_q, o.max_iter = kernel, int(refine_q), max_iter
         o.eig_tol, o.spin_limit, o.err_mode = eig_tol, spin_limit, err_mode
+        o.small_fp64 = int(bool(small_fp64))
         h = C.c_void_p()
         st = lib.tsk_create(C.byref(h), C.byref(o))
         if st != 0:

@@ -12,9 +12,13 @@
 // That array is part of the loaded module: every GPU that loads libtsk.so
 // holds kNoAllocScratchBytes of it until the process exits, whether or not
 // the entry point is ever called.  Host code cannot use the array's name as
-// a device address (it names a host-side shadow), so the first call on each
-// device looks the address up with cudaGetSymbolAddress while that device
-// is current, and caches it.
+// a device address (it names a host-side shadow), so each call looks the
+// address up with cudaGetSymbolAddress while the caller's device is current
+// (cheap once the module is loaded, and right again after a context reset
+// reloads the module elsewhere); inside a stream capture, where that lookup
+// may not be made, the address cached by an earlier call on the device is
+// used.  The errors follow the allocating entry point's default: the
+// projection identity, and a direct pass over A where it cancels.
 #include <stdio.h>
 #include <string.h>
 
@@ -36,7 +40,8 @@ void* g_addr[kMaxDevices] = {nullptr};
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct Layout {
-  size_t mats, items_x, items_y, panels, X, Y, RX, RY, W, norm, flags, status, total;
+  size_t mats, items_x, items_y, panels, X, Y, RX, RY, W, norm, flags, status, U2, V2, e2,
+      total;
 };
 
 Layout layout_for(long long m, long long n, int kp, size_t cs) {
@@ -66,6 +71,13 @@ Layout layout_for(long long m, long long n, int kp, size_t cs) {
   o = up256(o + sizeof(int));
   L.status = o;
   o = up256(o + sizeof(int));
+  // direct-residual fallback: U_r Sigma_r (m x kp), (Q V_r)^T panel (n x kp)
+  L.U2 = o;
+  o = up256(o + cs * (size_t)m * kp);
+  L.V2 = o;
+  o = up256(o + cs * (size_t)n * kp);
+  L.e2 = o;
+  o = up256(o + sizeof(double));
   L.total = o;
   return L;
 }
@@ -93,9 +105,17 @@ __global__ void noalloc_setup_kernel(unsigned char* base, Layout L, MatDev md, i
     p[1].ld = kp;
     p[1].R = base + L.RY;
     *(double*)(base + L.norm) = 0.0;
+    *(double*)(base + L.e2) = 0.0;
     *(int*)(base + L.flags) = 0;
     *(int*)(base + L.status) = 0;
   }
+}
+
+// The call's status bits as a tsk_status value for the caller.
+__global__ void noalloc_status_kernel(const int* bits, int32_t* out) {
+  const int b = *bits;
+  *out = (b & kStatusTimeout) ? (int32_t)TSK_ETIMEOUT
+                              : ((b & kStatusRankDef) ? (int32_t)TSK_ERANKDEF : (int32_t)TSK_OK);
 }
 
 tsk_status fail(const char* msg) {
@@ -109,7 +129,8 @@ tsk_status fail(const char* msg) {
 using namespace tsk;
 
 extern "C" tsk_status tsk_approx_noalloc(const tsk_mat_desc* mat, tsk_prec prec,
-                                         double* err, double* normA2, tsk_stream stream) {
+                                         double* err, double* normA2, int32_t* status_out,
+                                         tsk_stream stream) {
   if (!mat || !err) return fail("tsk_approx_noalloc: mat and err must be non-NULL");
   const tsk_mat_desc d = *mat;
   if (!d.A || !d.S) return fail("tsk_approx_noalloc: A or S is NULL");
@@ -128,17 +149,21 @@ extern "C" tsk_status tsk_approx_noalloc(const tsk_mat_desc* mat, tsk_prec prec,
   if (L.total > kNoAllocScratchBytes) {
     set_thread_error(
         "tsk_approx_noalloc: this matrix needs %zu bytes of scratch, more than the "
-        "%zu-byte static array ((m + n) * k_padded * %zu bytes plus descriptors)",
+        "%zu-byte static array (2 (m + n) * k_padded * %zu bytes plus descriptors)",
         L.total, kNoAllocScratchBytes, cs);
     return TSK_EINVAL;
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail("tsk_approx_noalloc: no usable current device");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess)
+    return fail("tsk_approx_noalloc: invalid stream");
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
       void* p = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || !p) {
@@ -147,10 +172,13 @@ extern "C" tsk_status tsk_approx_noalloc(const tsk_mat_desc* mat, tsk_prec prec,
         return TSK_ECUDA;
       }
       g_addr[dev] = p;
+    } else if (!g_addr[dev]) {
+      set_thread_error("tsk_approx_noalloc: the first call on a device must not be made "
+                       "during a stream capture");
+      return TSK_EINVAL;
     }
     base = (unsigned char*)g_addr[dev];
   }
-  cudaStream_t s = (cudaStream_t)stream;
   MatDev md;
   memset(&md, 0, sizeof(md));
   md.A = d.A;
@@ -177,11 +205,22 @@ extern "C" tsk_status tsk_approx_noalloc(const tsk_mat_desc* mat, tsk_prec prec,
                         (int)((d.m + 63) / 64), base + L.X, base + L.Y, s);
   if (e == cudaSuccess)
     e = launch_tsqr(dbl, kp, (const PanelDev*)(base + L.panels), 2, 1, status, s);
+  const double tau = dbl ? 1e-6 : 1e-4;
   if (e == cudaSuccess)
     e = launch_small_svd(dbl, kp, dm, 1, base + L.RX, base + L.RY, base + L.W, nrm, err,
-                         (int*)(base + L.flags), 1, 0.0, status, s);
+                         (int*)(base + L.flags), 0, tau, status, s);
+  // where the identity cancels (err^2 < tau ||A||^2) the flag is set and the
+  // error is recomputed by a direct pass over A; otherwise this does nothing
+  if (e == cudaSuccess)
+    e = launch_direct_fallback(in_type, kp, dm, 1, (const int*)(base + L.flags), base + L.X,
+                               base + L.Y, base + L.W, base + L.U2, base + L.V2,
+                               (double*)(base + L.e2), err, s);
   if (e == cudaSuccess && normA2)
     e = cudaMemcpyAsync(normA2, nrm, sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && status_out) {
+    noalloc_status_kernel<<<1, 1, 0, s>>>(status, status_out);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) {
     set_thread_error("tsk_approx_noalloc: %s", cudaGetErrorString(e));
     return TSK_ECUDA;

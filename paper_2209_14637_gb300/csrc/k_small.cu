@@ -133,7 +133,7 @@ __device__ void column_norms_sorted(const T* M, int nrow, int ncol, int ld,
 // triangular.  With refine = 1 the panel is passed again as Q1 = P R0^{-1}
 // (computed row by row on load), and the result is R = R2 R0.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, typename Tin>
 __global__ void __launch_bounds__(256)
 tsqr_kernel(int kp, const PanelDev* __restrict__ panels, int refine) {
   constexpr int B = 64;
@@ -146,7 +146,7 @@ tsqr_kernel(int kp, const PanelDev* __restrict__ panels, int refine) {
   const PanelDev pd = panels[blockIdx.x];
   const int k = pd.k, pld = pd.ld;
   const long long rows = pd.rows;
-  const T* __restrict__ P = (const T*)pd.P;
+  const Tin* __restrict__ P = (const Tin*)pd.P;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int e = tid; e < kp * ld; e += blockDim.x) {
     Rs[e] = T(0);
@@ -165,7 +165,7 @@ tsqr_kernel(int kp, const PanelDev* __restrict__ panels, int refine) {
       for (int e = tid; e < B * kp; e += blockDim.x) {
         const int ii = e / kp, c = e % kp;
         const long long gi = r0 + ii;
-        Bs[ii * ld + c] = (gi < rows && c < k) ? P[gi * pld + c] : T(0);
+        Bs[ii * ld + c] = (gi < rows && c < k) ? (T)P[gi * pld + c] : T(0);
       }
       __syncthreads();
       if (pass == 1) {
@@ -237,23 +237,28 @@ static size_t tsqr_smem(int kp, size_t elt) {
   return (size_t)(64 + 2 * kp) * (kp + 1) * elt;
 }
 
+template <typename T, typename Tin>
+static cudaError_t tsqr_t(int kp, const PanelDev* panels, int count, int refine,
+                          cudaStream_t s) {
+  const size_t sm = tsqr_smem(kp, sizeof(T));
+  cudaError_t e = cudaFuncSetAttribute(tsqr_kernel<T, Tin>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  tsqr_kernel<T, Tin><<<count, 256, sm, s>>>(kp, panels, refine);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tsqr(bool dbl, int kp, const PanelDev* panels, int count,
                         int refine, int* /*status*/, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  if (dbl) {
-    const size_t sm = tsqr_smem(kp, sizeof(double));
-    cudaError_t e = cudaFuncSetAttribute(
-        tsqr_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    tsqr_kernel<double><<<count, 256, sm, s>>>(kp, panels, refine);
-  } else {
-    const size_t sm = tsqr_smem(kp, sizeof(float));
-    cudaError_t e = cudaFuncSetAttribute(
-        tsqr_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    tsqr_kernel<float><<<count, 256, sm, s>>>(kp, panels, refine);
-  }
-  return cudaGetLastError();
+  return dbl ? tsqr_t<double, double>(kp, panels, count, refine, s)
+             : tsqr_t<float, float>(kp, panels, count, refine, s);
+}
+
+cudaError_t launch_tsqr_f32_in_f64(int kp, const PanelDev* panels, int count, int refine,
+                                   cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  return tsqr_t<double, float>(kp, panels, count, refine, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -266,7 +271,7 @@ small_svd_kernel(int kp, const MatDev* __restrict__ mats,
                  const T* __restrict__ RX, const T* __restrict__ RY,
                  T* __restrict__ Wm, const double* __restrict__ normA2,
                  double* __restrict__ err, int* __restrict__ flags, int err_mode,
-                 double tau, int* __restrict__ status) {
+                 double tau, int sigma_f32, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ld = kp + 1;
   T* Rx = (T*)smem_raw;
@@ -310,8 +315,12 @@ small_svd_kernel(int kp, const MatDev* __restrict__ mats,
   __syncthreads();
   column_norms_sorted<T>(Tm, k, k, ld, sig, order);
   if (md.sigma != nullptr)
-    for (int c = tid; c < k; c += blockDim.x)
-      ((T*)md.sigma)[c] = sig[order[c]];
+    for (int c = tid; c < k; c += blockDim.x) {
+      if (sigma_f32)
+        ((float*)md.sigma)[c] = (float)sig[order[c]];
+      else
+        ((T*)md.sigma)[c] = sig[order[c]];
+    }
   if (tid == 0) {
     double cap = 0.0;
     for (int c = 0; c < r; ++c) {
@@ -346,7 +355,7 @@ static size_t small_svd_smem(int kp, size_t elt) {
 cudaError_t launch_small_svd(bool dbl, int kp, const MatDev* mats, int count,
                              const void* RX, const void* RY, void* Wm,
                              double* normA2, double* err, int* flags, int err_mode,
-                             double tau, int* status, cudaStream_t s) {
+                             double tau, int* status, cudaStream_t s, int sigma_f32) {
   if (count <= 0) return cudaSuccess;
   if (dbl) {
     const size_t sm = small_svd_smem(kp, sizeof(double));
@@ -356,7 +365,7 @@ cudaError_t launch_small_svd(bool dbl, int kp, const MatDev* mats, int count,
     if (e != cudaSuccess) return e;
     small_svd_kernel<double><<<count, 256, sm, s>>>(
         kp, mats, (const double*)RX, (const double*)RY, (double*)Wm, normA2,
-        err, flags, err_mode, tau, status);
+        err, flags, err_mode, tau, sigma_f32, status);
   } else {
     const size_t sm = small_svd_smem(kp, sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(small_svd_kernel<float>,
@@ -365,7 +374,7 @@ cudaError_t launch_small_svd(bool dbl, int kp, const MatDev* mats, int count,
     if (e != cudaSuccess) return e;
     small_svd_kernel<float><<<count, 256, sm, s>>>(
         kp, mats, (const float*)RX, (const float*)RY, (float*)Wm, normA2, err,
-        flags, err_mode, tau, status);
+        flags, err_mode, tau, 0, status);
   }
   return cudaGetLastError();
 }

@@ -354,9 +354,29 @@ __device__ __forceinline__ bool bwait_warp(uint32_t bar, uint32_t parity, volati
   ok = __shfl_sync(0xffffffffu, ok, 0);
   return ok != 0;
 }
-// Bounded wait that ignores the abort flag (used to drain own copies).
+// Bounded wait that ignores the abort flag, used to drain the CTA's own TMA
+// loads and tensor-core operations before it leaves.  Its bound is fixed
+// (two seconds, far beyond any copy or MMA that was actually issued) and
+// independent of the caller's spin limit: a short spin limit may cut the
+// ordinary waits short, but never lets a CTA exit with its own operations
+// still in flight.
+constexpr long long kDrainTimeoutNs = 2000000000ll;
 template <class PP>
 __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity, const PP& P) {
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if ((long long)(globaltimer() - t0) > kDrainTimeoutNs) {
+      atomicOr(P.status, kStatusTimeout);
+      return;
+    }
+  }
+}
+
+// Bounded wait for arrives that peers of the cluster send (bounded by the
+// spin limit like every wait on another CTA; a peer that aborted may never
+// send them, and the teardown's cluster barrier covers what is in flight).
+template <class PP>
+__device__ __forceinline__ void peer_wait(uint32_t bar, uint32_t parity, const PP& P) {
   const uint64_t t0 = globaltimer();
   while (!mbar_try_wait(bar, parity)) {
     if ((long long)(globaltimer() - t0) > P.timeout_ns) {
@@ -791,8 +811,8 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
       for (int h = 0; h < 2; ++h) {
         if (g > h) {
           const long long last = ((g - 1 - h) / 2) * 2 + h;
-          drain_wait(bar(B_PEMPTY + h), (uint32_t)((last >> 1) & 1), P);
-          drain_wait(bar(B_XBEMPTY + h), (uint32_t)((last >> 1) & 1), P);
+          peer_wait(bar(B_PEMPTY + h), (uint32_t)((last >> 1) & 1), P);
+          peer_wait(bar(B_XBEMPTY + h), (uint32_t)((last >> 1) & 1), P);
         }
       }
     }
@@ -1293,6 +1313,11 @@ bool tc_supported() {
   return p.major == 10 && p.minor == 3 && get_encode() != nullptr;
 }
 
+bool tc_matrix_eligible(const void* A, long long m, long long lda, int k) {
+  return k >= 1 && k <= KPAD_MAX && m >= 1 && m <= 4096 && ((uintptr_t)A) % 16 == 0 &&
+         (lda * 2) % 16 == 0 && lda <= (1ll << 36);
+}
+
 bool gram_tc_eligible(int prec, int mode, const void* const* A, long long D, long long m,
                       long long n, long long lda) {
   if (prec != 2 || mode != 1 || D < 1 || m < 1 || n < 1) return false;
@@ -1303,22 +1328,63 @@ bool gram_tc_eligible(int prec, int mode, const void* const* A, long long D, lon
   return tc_supported();
 }
 
+// The tensor maps of the last training set a handle's Gram saw, kept on the
+// device: a repeated Gram over the same matrices (a timed re-run, the sweeps
+// of an iterative method) skips the host encoding and the upload.
+struct GramCache {
+  std::vector<const void*> key;
+  long long m = 0, n = 0, lda = 0;
+  CUtensorMap* dmaps = nullptr;
+  size_t cap = 0;
+};
+
+GramCache* gram_cache_create() { return new GramCache(); }
+void gram_cache_destroy(GramCache* c) {
+  if (!c) return;
+  if (c->dmaps) cudaFree(c->dmaps);
+  delete c;
+}
+
 cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long long n,
                            long long lda, double* G, int* status, long long spin_limit,
-                           cudaStream_t s) {
+                           GramCache* cache, cudaStream_t s) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
-  if (!enc) return cudaErrorNotSupported;
-  std::vector<CUtensorMap> maps((size_t)D);
-  for (long long d = 0; d < D; ++d) {
-    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
-    cuuint64_t strides[1] = {(cuuint64_t)lda * 2};
-    cuuint32_t box[2] = {64, 128};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(&maps[(size_t)d], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                     const_cast<void*>(A[d]), dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorNotSupported;  // nothing launched yet
+  if (!enc || !cache) return cudaErrorNotSupported;
+  const bool hit = cache->dmaps && cache->m == m && cache->n == n && cache->lda == lda &&
+                   (long long)cache->key.size() == D &&
+                   std::equal(cache->key.begin(), cache->key.end(), A);
+  if (!hit) {
+    std::vector<CUtensorMap> maps((size_t)D);
+    for (long long d = 0; d < D; ++d) {
+      cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
+      cuuint64_t strides[1] = {(cuuint64_t)lda * 2};
+      cuuint32_t box[2] = {64, 128};
+      cuuint32_t es[2] = {1, 1};
+      CUresult r = enc(&maps[(size_t)d], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                       const_cast<void*>(A[d]), dims, strides, box, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return cudaErrorNotSupported;  // nothing launched yet
+    }
+    // the previous maps may still be read by a Gram in flight on this stream
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (cache->cap < (size_t)D) {
+      if (cache->dmaps) cudaFree(cache->dmaps);
+      cache->dmaps = nullptr;
+      cache->cap = 0;
+      e = cudaMalloc((void**)&cache->dmaps, sizeof(CUtensorMap) * (size_t)D);
+      if (e != cudaSuccess) return e;
+      cache->cap = (size_t)D;
+    }
+    cache->key.clear();
+    e = cudaMemcpy(cache->dmaps, maps.data(), sizeof(CUtensorMap) * (size_t)D,
+                   cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    cache->key.assign(A, A + D);
+    cache->m = m;
+    cache->n = n;
+    cache->lda = lda;
   }
   int dev = 0, nsm = 148;
   if (cudaGetDevice(&dev) == cudaSuccess)
@@ -1329,14 +1395,9 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
   long long splits = nsm / ntp;
   if (splits > D) splits = D;
   if (splits < 1) splits = 1;
-  void* dmaps = nullptr;
-  cudaError_t e = cudaMallocAsync(&dmaps, sizeof(CUtensorMap) * (size_t)D, s);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(dmaps, maps.data(), sizeof(CUtensorMap) * (size_t)D,
-                      cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // maps (host) is freed on return
+  cudaError_t e = cudaSuccess;
   GramParams prm;
-  prm.tmaps = (const CUtensorMap*)dmaps;
+  prm.tmaps = cache->dmaps;
   prm.D = D;
   prm.m = m;
   prm.n = n;
@@ -1357,13 +1418,13 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
     mirror_upper_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(G, m);
     e = cudaGetLastError();
   }
-  cudaFreeAsync(dmaps, s);
   return e;
 }
 
 cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int count,
-                       int kp, void* dev_X, void* dev_Y, double* dev_normA2,
-                       int* status, long long spin_limit, char* msg, int msglen) {
+                       const int* ids, int nids, int kp, void* dev_X, void* dev_Y,
+                       double* dev_normA2, int* status, long long spin_limit, char* msg,
+                       int msglen) {
   *out = nullptr;
   auto fail = [&](const char* why) {
     if (msg && msglen > 0) snprintf(msg, msglen, "%s", why);
@@ -1371,8 +1432,11 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
   };
   PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
   if (!enc) return fail("cuTensorMapEncodeTiled is unavailable");
+  if (nids < 1) return fail("no matrix for the tensor-core kernel");
   int kmax = 1;
-  for (int i = 0; i < count; ++i) {
+  for (int t = 0; t < nids; ++t) {
+    const int i = ids[t];
+    if (i < 0 || i >= count) return fail("matrix index out of range");
     if (hm[i].k > KPAD_MAX) return fail("k > 48 is not supported by the tensor-core kernel");
     if (hm[i].m > 4096) return fail("m > 4096 is not supported by the tensor-core kernel");
     kmax = std::max(kmax, hm[i].k);
@@ -1382,7 +1446,8 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
   p->kq = ((kmax + 7) / 8) * 8;
   // classes by cluster shape (C, MC)
   std::map<std::pair<int, int>, std::vector<int>> byC;
-  for (int i = 0; i < count; ++i) {
+  for (int t = 0; t < nids; ++t) {
+    const int i = ids[t];
     int C, mc;
     cluster_shape(hm[i].m, &C, &mc);
     byC[std::make_pair(C, mc)].push_back(i);
@@ -1390,9 +1455,10 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
   // distinct sketch images
   std::map<std::tuple<const void*, long long, int>, long long> img_of;
   std::vector<SImgDesc> sdesc;
-  std::vector<long long> simg_off(count);
+  std::vector<long long> simg_off(count, 0);
   long long img_total = 0;
-  for (int i = 0; i < count; ++i) {
+  for (int t = 0; t < nids; ++t) {
+    const int i = ids[t];
     auto key = std::make_tuple(hm[i].S, hm[i].m, hm[i].k);
     auto it = img_of.find(key);
     if (it == img_of.end()) {
@@ -1484,7 +1550,8 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
     return e;
   }
   std::vector<unsigned char> host(o_img, 0);
-  for (int i = 0; i < count; ++i) {
+  for (int t = 0; t < nids; ++t) {  // maps of the other matrices stay zero (unused)
+    const int i = ids[t];
     CUtensorMap* map = reinterpret_cast<CUtensorMap*>(host.data() + o_map) + i;
     cuuint64_t dims[2] = {(cuuint64_t)hm[i].n, (cuuint64_t)hm[i].m};
     cuuint64_t strides[1] = {(cuuint64_t)hm[i].lda * 2};

@@ -22,7 +22,9 @@ struct tsk_plan_s {
   int kp = 16;
   int kmax = 1;
   bool dbl = false;
-  bool use_tc = false;
+  bool use_tc = false;   // some matrices take the tensor-core sketch
+  bool use_simt = true;  // some matrices take the CUDA-core sketch
+  bool small64 = false;  // FP32 / BF16 plan with the FP64 small-factor route
   void* ws = nullptr;
   size_t ws_bytes = 0;
   cudaGraph_t graph = nullptr;
@@ -35,7 +37,8 @@ struct tsk_plan_s {
   int nx = 0, ny = 0, nio = 0;
   unsigned char* base = nullptr;
   size_t o_mats = 0, o_ix = 0, o_iy = 0, o_io = 0, o_pan = 0, o_X = 0, o_Y = 0,
-         o_RX = 0, o_RY = 0, o_W = 0, o_flag = 0, o_U2 = 0, o_V2 = 0, o_e2 = 0;
+         o_RX = 0, o_RY = 0, o_W = 0, o_flag = 0, o_U2 = 0, o_V2 = 0, o_e2 = 0,
+         o_pan64 = 0, o_RX64 = 0, o_RY64 = 0, o_W64 = 0;
   // Gram route (FP32 / BF16)
   double* d_norm = nullptr;
   double* d_err = nullptr;
@@ -48,7 +51,10 @@ struct tsk_handle_s {
   char last_error[512] = {0};
   int* d_status = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_stream2 = nullptr;  // second branch of a captured plan
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<tsk_plan> cache;
+  GramCache* gram_cache = nullptr;  // tensor maps of the last BF16 training set
 };
 
 static thread_local char g_create_error[512] = "no error";
@@ -92,6 +98,8 @@ extern "C" void tsk_default_options(tsk_options* o) {
   o->eig_tol = 0.0;
   o->err_mode = 0;
   o->spin_limit = 1ll << 24;
+  o->small_fp64 = 0;
+  o->reserved = 0;
 }
 
 extern "C" tsk_status tsk_create(tsk_handle* out, const tsk_options* opts) {
@@ -120,8 +128,15 @@ extern "C" tsk_status tsk_create(tsk_handle* out, const tsk_options* opts) {
   e = cudaMalloc(&h->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     set_err(nullptr, "tsk_create: %s", cudaGetErrorString(e));
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->d_status) cudaFree(h->d_status);
     delete h;
     return TSK_ECUDA;
@@ -144,6 +159,10 @@ extern "C" tsk_status tsk_destroy(tsk_handle h) {
   cudaDeviceSynchronize();
   for (tsk_plan p : h->cache) plan_free(p);
   h->cache.clear();
+  gram_cache_destroy(h->gram_cache);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->d_status) cudaFree(h->d_status);
   delete h;
@@ -201,16 +220,10 @@ static tsk_status check_desc(tsk_handle h, const tsk_mat_desc& d, int64_t i,
 }
 
 // The tensor-core kernel takes k <= 48 and m <= 4096 (clusters of at most 8
-// CTAs of 512 rows) and needs 16-byte aligned rows for TMA.
-static bool tc_eligible(const tsk_mat_desc* mats, int64_t count) {
-  for (int64_t i = 0; i < count; ++i) {
-    if (mats[i].k > 48 || mats[i].m > 4096) return false;
-    if (((uintptr_t)mats[i].A) % 16 != 0) return false;
-    if ((mats[i].lda * 2) % 16 != 0) return false;
-    if (((uintptr_t)mats[i].S) % 16 != 0) return false;
-    if ((mats[i].m * 4) % 16 != 0) return false;
-  }
-  return true;
+// CTAs of 512 rows) and needs 16-byte aligned rows for TMA; S is read
+// through a pre-swizzled image the plan builds, so it needs no alignment.
+static bool tc_eligible_one(const tsk_mat_desc& d) {
+  return tc_matrix_eligible(d.A, d.m, d.lda, d.k);
 }
 
 // ---------------------------------------------------------------------------
@@ -252,18 +265,31 @@ static cudaError_t capture_plan(tsk_plan p, cudaEvent_t evb, cudaEvent_t eve) {
   int launches = 0;
   ce = cudaMemsetAsync(d_norm, 0, sizeof(double) * count, s);
   if (ce == cudaSuccess && evb) ce = cudaEventRecordWithFlags(evb, s, cudaEventRecordExternal);
-  if (ce == cudaSuccess) {
-    if (p->use_tc) {
-      ce = tc_launch(p->tc, s);
-      launches += tc_launches(p->tc);
-    } else {
-      ce = launch_sketch_x(in_type, kp, d_mats, (const int2*)(base + p->o_ix),
-                           p->nx, base + p->o_X, d_norm, s);
-      if (ce == cudaSuccess)
-        ce = launch_sketch_y(in_type, kp, d_mats, (const int2*)(base + p->o_iy),
-                             p->ny, base + p->o_X, base + p->o_Y, s);
-      launches += 2;
-    }
+  // The sketch pass: the tensor-core kernel on the eligible matrices and the
+  // CUDA-core kernels on the rest, on two branches of the graph that run
+  // concurrently and join before the small factors.
+  const bool both = p->use_tc && p->use_simt;
+  cudaStream_t s2 = both ? h->cap_stream2 : s;
+  if (ce == cudaSuccess && both) {
+    ce = cudaEventRecord(h->ev_fork, s);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s2, h->ev_fork, 0);
+  }
+  if (ce == cudaSuccess && p->use_tc) {
+    ce = tc_launch(p->tc, s);
+    launches += tc_launches(p->tc);
+  }
+  if (ce == cudaSuccess && p->use_simt) {
+    ce = launch_sketch_x(in_type, kp, d_mats, (const int2*)(base + p->o_ix),
+                         p->nx, base + p->o_X, d_norm, s2);
+    if (ce == cudaSuccess)
+      ce = launch_sketch_y(in_type, kp, d_mats, (const int2*)(base + p->o_iy),
+                           p->ny, base + p->o_X, base + p->o_Y, s2);
+    launches += 2;
+  }
+  if (both) {  // join the branch even after an error, so the capture can end
+    cudaError_t je = cudaEventRecord(h->ev_join, s2);
+    if (je == cudaSuccess) je = cudaStreamWaitEvent(s, h->ev_join, 0);
+    if (ce == cudaSuccess) ce = je;
   }
   if (ce == cudaSuccess && eve) ce = cudaEventRecordWithFlags(eve, s, cudaEventRecordExternal);
   const double tau = p->dbl ? 1e-6 : 1e-4;
@@ -277,6 +303,22 @@ static cudaError_t capture_plan(tsk_plan p, cudaEvent_t evb, cudaEvent_t eve) {
                             base + p->o_RY, base + p->o_W, d_norm, d_err,
                             (int*)(base + p->o_flag), h->opts.err_mode, tau,
                             h->d_status, s);
+    ++launches;
+  } else if (ce == cudaSuccess && p->small64) {
+    // FP32 / BF16 panels, small factors in double: Householder R factors of
+    // X and Y (with one refinement pass on X when refine_q != 0), the SVD of
+    // R_Y R_X^{-1}, then W back to float for the outputs and the fallback.
+    ce = launch_tsqr_f32_in_f64(kp, (const PanelDev*)(base + p->o_pan64), 2 * count,
+                                h->opts.refine_q ? 1 : 0, s);
+    ++launches;
+    if (ce == cudaSuccess)
+      ce = launch_small_svd(true, kp, d_mats, count, base + p->o_RX64, base + p->o_RY64,
+                            base + p->o_W64, d_norm, d_err, (int*)(base + p->o_flag),
+                            h->opts.err_mode, tau, h->d_status, s, 1);
+    ++launches;
+    if (ce == cudaSuccess)
+      ce = launch_convert_gram(false, (const double*)(base + p->o_W64), base + p->o_W,
+                               (long long)count * kp * kp, s);
     ++launches;
   } else if (ce == cudaSuccess) {
     // FP32 / BF16: Cholesky of X^T X (+ one refinement), eigenpairs of M^T M,
@@ -350,20 +392,30 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
     kmax = std::max(kmax, mats[i].k);
   }
   const int req = h->opts.kernel;
-  bool use_tc = false;
-  if (prec == TSK_BF16 && req != TSK_KERNEL_SIMT) {
-    const bool ok = tc_supported() && tc_eligible(mats, count);
-    if (req == TSK_KERNEL_TC && !ok) {
-      set_err(h, "tensor-core kernel requested but unavailable for these "
-                 "arguments (needs a GB300, k <= 48, m <= 4096 and 16-byte aligned A, S, "
-                 "lda)");
+  // per matrix: tensor-core sketch (1) or CUDA-core sketch (0)
+  std::vector<char> on_tc((size_t)count, 0);
+  std::vector<int> tc_ids;
+  if (prec == TSK_BF16 && req != TSK_KERNEL_SIMT && tc_supported()) {
+    for (int64_t i = 0; i < count; ++i)
+      if (tc_eligible_one(mats[i])) {
+        on_tc[(size_t)i] = 1;
+        tc_ids.push_back((int)i);
+      }
+  }
+  if (req == TSK_KERNEL_TC) {
+    if (prec != TSK_BF16) {
+      set_err(h, "the tensor-core kernel runs the TSK_BF16 path only");
       return TSK_EUNSUPPORTED;
     }
-    use_tc = ok;
-  } else if (req == TSK_KERNEL_TC) {
-    set_err(h, "the tensor-core kernel runs the TSK_BF16 path only");
-    return TSK_EUNSUPPORTED;
+    if ((int64_t)tc_ids.size() != count) {
+      set_err(h, "tensor-core kernel requested but unavailable for these "
+                 "arguments (needs a GB300, k <= 48, m <= 4096, a 16-byte aligned A and "
+                 "lda * 2 a multiple of 16)");
+      return TSK_EUNSUPPORTED;
+    }
   }
+  const bool use_tc = !tc_ids.empty();
+  const bool use_simt = (int64_t)tc_ids.size() < count;
 
   tsk_plan p = new (std::nothrow) tsk_plan_s();
   if (!p) return TSK_ENOMEM;
@@ -374,6 +426,8 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   p->kp = ((kmax + 15) / 16) * 16;
   p->kmax = kmax;
   p->use_tc = use_tc;
+  p->use_simt = use_simt;
+  p->small64 = (prec != TSK_FP64) && h->opts.small_fp64 != 0;
   const int kp = p->kp;
   const size_t cs = compute_size(prec);
 
@@ -398,8 +452,10 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
     d.sigma = outs ? outs[i].sigma : nullptr;
     offX += d.n * kp;
     offY += d.m * kp;
-    for (long long t = 0; t < (d.n + 63) / 64; ++t) ix.push_back(make_int2((int)i, (int)t));
-    for (long long t = 0; t < (d.m + 63) / 64; ++t) iy.push_back(make_int2((int)i, (int)t));
+    if (!on_tc[(size_t)i]) {  // CUDA-core sketch items: 64 columns (X) or rows (Y)
+      for (long long t = 0; t < (d.n + 63) / 64; ++t) ix.push_back(make_int2((int)i, (int)t));
+      for (long long t = 0; t < (d.m + 63) / 64; ++t) iy.push_back(make_int2((int)i, (int)t));
+    }
     if (d.US)
       for (long long t = 0; t < (d.m + 255) / 256; ++t)
         io.push_back(make_int4((int)i, (int)t, 0, 0));
@@ -410,8 +466,8 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   }
   Carve cv;
   const size_t o_mats = cv.take(sizeof(MatDev) * count);
-  const size_t o_ix = cv.take(sizeof(int2) * ix.size());
-  const size_t o_iy = cv.take(sizeof(int2) * iy.size());
+  const size_t o_ix = cv.take(sizeof(int2) * std::max<size_t>(1, ix.size()));
+  const size_t o_iy = cv.take(sizeof(int2) * std::max<size_t>(1, iy.size()));
   const size_t o_io = cv.take(sizeof(int4) * std::max<size_t>(1, io.size()));
   const size_t o_pan = cv.take(sizeof(PanelDev) * 2 * count);
   const size_t o_X = cv.take(cs * offX);
@@ -426,6 +482,12 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   const size_t o_U2 = cv.take(fallback ? cs * offY : 0);
   const size_t o_V2 = cv.take(fallback ? cs * offX : 0);
   const size_t o_e2 = cv.take(sizeof(double) * count);
+  // FP64 small-factor route: panel descriptors and double R_X, R_Y, W
+  const bool s64 = p->small64;
+  const size_t o_pan64 = cv.take(s64 ? sizeof(PanelDev) * 2 * count : 0);
+  const size_t o_RX64 = cv.take(s64 ? 8 * (size_t)count * kp * kp : 0);
+  const size_t o_RY64 = cv.take(s64 ? 8 * (size_t)count * kp * kp : 0);
+  const size_t o_W64 = cv.take(s64 ? 8 * (size_t)count * kp * kp : 0);
   const size_t host_part = o_X;  // descriptors live before X
   p->ws_bytes = cv.off;
   cudaError_t ce = cudaMalloc(&p->ws, p->ws_bytes);
@@ -454,11 +516,21 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   }
   std::vector<unsigned char> staging(host_part, 0);
   memcpy(staging.data() + o_mats, hm.data(), sizeof(MatDev) * count);
-  memcpy(staging.data() + o_ix, ix.data(), sizeof(int2) * ix.size());
-  memcpy(staging.data() + o_iy, iy.data(), sizeof(int2) * iy.size());
+  if (!ix.empty()) memcpy(staging.data() + o_ix, ix.data(), sizeof(int2) * ix.size());
+  if (!iy.empty()) memcpy(staging.data() + o_iy, iy.data(), sizeof(int2) * iy.size());
   if (!io.empty()) memcpy(staging.data() + o_io, io.data(), sizeof(int4) * io.size());
   memcpy(staging.data() + o_pan, hp.data(), sizeof(PanelDev) * 2 * count);
   ce = cudaMemcpy(p->ws, staging.data(), host_part, cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess && s64) {
+    // the same float panels, with double R factors
+    std::vector<PanelDev> hp64(hp);
+    for (int64_t i = 0; i < count; ++i) {
+      hp64[i].R = base + o_RX64 + 8 * i * kp * kp;
+      hp64[count + i].R = base + o_RY64 + 8 * i * kp * kp;
+    }
+    ce = cudaMemcpy(base + o_pan64, hp64.data(), sizeof(PanelDev) * 2 * count,
+                    cudaMemcpyHostToDevice);
+  }
   // The X and Y panels start zeroed: the kernels write columns < k (the
   // tensor-core kernel: < k rounded up to 8) and never the rest, which the
   // Gram kernel reads as zeros.
@@ -472,8 +544,9 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   const MatDev* d_mats = (const MatDev*)(base + o_mats);
   if (use_tc) {
     char msg[256] = {0};
-    ce = tc_prepare(&p->tc, hm.data(), d_mats, (int)count, kp, base + o_X, base + o_Y,
-                    d_norm, h->d_status, h->opts.spin_limit, msg, sizeof(msg));
+    ce = tc_prepare(&p->tc, hm.data(), d_mats, (int)count, tc_ids.data(), (int)tc_ids.size(),
+                    kp, base + o_X, base + o_Y, d_norm, h->d_status, h->opts.spin_limit, msg,
+                    sizeof(msg));
     if (ce != cudaSuccess) {
       set_err(h, "tensor-core plan: %s (%s)", msg, cudaGetErrorString(ce));
       plan_free(p);
@@ -500,6 +573,10 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   p->o_U2 = o_U2;
   p->o_V2 = o_V2;
   p->o_e2 = o_e2;
+  p->o_pan64 = o_pan64;
+  p->o_RX64 = o_RX64;
+  p->o_RY64 = o_RY64;
+  p->o_W64 = o_W64;
   p->d_norm = d_norm;
   p->d_err = d_err;
   ce = capture_plan(p, nullptr, nullptr);
@@ -583,6 +660,7 @@ static std::vector<unsigned char> plan_key(tsk_handle h, int64_t count,
   put(&h->opts.kernel, sizeof(h->opts.kernel));
   put(&h->opts.refine_q, sizeof(h->opts.refine_q));
   put(&h->opts.err_mode, sizeof(h->opts.err_mode));
+  put(&h->opts.small_fp64, sizeof(h->opts.small_fp64));
   put(mats, sizeof(tsk_mat_desc) * count);
   const unsigned char has = outs ? 1 : 0;
   put(&has, 1);
@@ -705,7 +783,8 @@ extern "C" tsk_status tsk_gram(tsk_handle h, const void* const* A, int64_t D,
     // BF16 mode 1: tcgen05 SYRK (FP32 in TMEM, FP64 in G); shapes whose
     // tensor maps cannot be encoded go to the CUDA-core kernel below
     const cudaError_t ge =
-        launch_gram_tc(A, D, m, n, lda, G, h->d_status, h->opts.spin_limit, s);
+        launch_gram_tc(A, D, m, n, lda, G, h->d_status, h->opts.spin_limit,
+                       h->gram_cache ? h->gram_cache : (h->gram_cache = gram_cache_create()), s);
     if (ge != cudaErrorNotSupported) {
       TSK_CUDA(h, ge);
       TSK_CUDA(h, cudaStreamSynchronize(s));

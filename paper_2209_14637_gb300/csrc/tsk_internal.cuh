@@ -111,11 +111,17 @@ cudaError_t launch_emit_sketch(bool dbl, const void* U, long long rows, int p,
 // k_small.cu
 cudaError_t launch_tsqr(bool dbl, int kp, const PanelDev* panels, int count,
                         int refine, int* status, cudaStream_t s);
+// sigma_f32 != 0 writes the singular values as float (the FP32 / BF16
+// outputs) from the double kernel.
 cudaError_t launch_small_svd(bool dbl, int kp, const MatDev* mats, int count,
                              const void* RX, const void* RY, void* Wm,
                              double* normA2, double* err, int* flags,
                              int err_mode, double tau, int* status,
-                             cudaStream_t s);
+                             cudaStream_t s, int sigma_f32 = 0);
+// R factors in double of float panels (the FP64 small-factor route of the
+// FP32 / BF16 paths); the panel descriptors point at float data.
+cudaError_t launch_tsqr_f32_in_f64(int kp, const PanelDev* panels, int count, int refine,
+                                   cudaStream_t s);
 cudaError_t launch_sym_eig(bool dbl, const void* H, int p, void* theta,
                            void* V, cudaStream_t s);
 // Fused small factors of the FP32 / BF16 paths (k_finish.cu): one CTA per
@@ -150,14 +156,22 @@ bool tc_supported();
 // encoded for these shapes.
 bool gram_tc_eligible(int prec, int mode, const void* const* A, long long D, long long m,
                       long long n, long long lda);
+struct GramCache;
+GramCache* gram_cache_create();
+void gram_cache_destroy(GramCache* c);
 cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long long n,
                            long long lda, double* G, int* status, long long spin_limit,
-                           cudaStream_t s);
+                           GramCache* cache, cudaStream_t s);
+// Builds the tensor-core part of a plan for the matrices ids[0..nids) of
+// the plan's count matrices (tensor maps, S images, per-class schedules).
 cudaError_t tc_prepare(TcPlan** out, const MatDev* host_mats,
-                       const MatDev* dev_mats, int count, int kp, void* dev_X,
-                       void* dev_Y, double* dev_normA2,
+                       const MatDev* dev_mats, int count, const int* ids, int nids,
+                       int kp, void* dev_X, void* dev_Y, double* dev_normA2,
                        int* status, long long spin_limit, char* msg,
                        int msglen);
+// Whether one BF16 matrix can take the tensor-core sketch: k <= 48,
+// m <= 4096, A 16-byte aligned, lda * 2 a multiple of 16.
+bool tc_matrix_eligible(const void* A, long long m, long long lda, int k);
 cudaError_t tc_launch(TcPlan* p, cudaStream_t s);
 int tc_launches(const TcPlan* p);
 long long tc_workspace_bytes(const TcPlan* p);

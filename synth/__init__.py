@@ -100,11 +100,17 @@ def _gen(seed: int, device) -> torch.Generator:
 
 
 def orth(M: torch.Tensor) -> torch.Tensor:
-    """Orthonormal basis of the columns of M, signs fixed so diag(R) >= 0."""
-    Q, R = torch.linalg.qr(M)
+    """Orthonormal basis of the columns of M, signs fixed so diag(R) >= 0.
+
+    The QR runs on the host (LAPACK) whatever M's device, and the result
+    goes back to M's device: the tall m x L factors are small, and the
+    device QR would need torch's separate CUDA linear-algebra library, which
+    some profiling set-ups cannot load.
+    """
+    Q, R = torch.linalg.qr(M.detach().to("cpu", torch.float64))
     s = torch.sign(torch.diagonal(R, dim1=-2, dim2=-1))
     s = torch.where(s == 0, torch.ones_like(s), s)
-    return Q * s.unsqueeze(-2)
+    return (Q * s.unsqueeze(-2)).to(M.device, M.dtype)
 
 
 def shared_basis(spec: StreamSpec, device="cpu", stream_id: int = 0
@@ -164,7 +170,9 @@ def ragged_sizes(count: int = 512, seed: int = BASE_SEED + 4,
     """Sizes of the ragged batch: m, n log-uniform, k uniform over ks, r=k/2.
 
     Each item is its own small stream (latent rank 2k, sigma_i = i^-1.2,
-    drift 0.05, noise 1e-3) whose sketch is trained on 8 draws.
+    drift 0.05, noise 1e-3, 8 training draws); item_sketch() draws the
+    sketch it is approximated with.  Sizes are not rounded: most rows of a
+    contiguous BF16 item do not start on a 16-byte boundary.
     """
     rng = np.random.default_rng(seed)
     items = []
@@ -174,10 +182,6 @@ def ragged_sizes(count: int = 512, seed: int = BASE_SEED + 4,
         n = int(round(math.exp(rng.uniform(math.log(n_range[0]),
                                            math.log(n_range[1])))))
         k = int(ks[rng.integers(0, len(ks))])
-        # Rows and columns of every item are kept multiples of 8 so that
-        # BF16 rows start on 16-byte boundaries.
-        m = max(8, (m // 8) * 8)
-        n = max(8, (n // 8) * 8)
         k = min(k, m, n)
         L = min(2 * k, m, n)
         spec = StreamSpec(f"ragged_{i}", m, n, 8, 1, k, max(1, k // 2), L,
@@ -185,3 +189,53 @@ def ragged_sizes(count: int = 512, seed: int = BASE_SEED + 4,
                           seed * 1009 + i)
         items.append(RaggedItem(m, n, k, max(1, k // 2), spec))
     return items
+
+
+def item_sketch(item: RaggedItem, device="cpu", spread: float = 0.1,
+                dtype=torch.float32) -> torch.Tensor:
+    """A k x m row-orthonormal sketch for one ragged item: the first k
+    directions of the item's shared basis U0, each perturbed by a Gaussian
+    vector of norm about `spread`, orthonormalised.  It stands in for a
+    sketch trained on the item's own stream (a trained sketch lies near the
+    same leading subspace) and is an input to both the oracle and the GPU."""
+    spec = item.spec
+    U0 = shared_basis(spec, "cpu")
+    g = _gen(spec.seed * 6151 + 3, "cpu")
+    E = torch.randn(spec.m, item.k, generator=g, dtype=torch.float64)
+    Sm = orth(U0[:, :item.k] + (spread / math.sqrt(spec.m)) * E)
+    return Sm.T.contiguous().to(device, dtype)
+
+
+def random_sketch(kind: str, k: int, m: int, seed: int, device="cpu",
+                  dtype=torch.float32) -> torch.Tensor:
+    """The data-oblivious sketches of classical SCW (Section 1): a k x m
+    Gaussian matrix with N(0, 1/k) entries, or a sign (Rademacher) matrix
+    with entries +-1/sqrt(k)."""
+    g = _gen(seed * 7 + (1 if kind == "gauss" else 2), "cpu")
+    if kind == "gauss":
+        S = torch.randn(k, m, generator=g, dtype=torch.float64) / math.sqrt(k)
+    elif kind == "sign":
+        b = torch.randint(0, 2, (k, m), generator=g, dtype=torch.int64)
+        S = (2.0 * b.to(torch.float64) - 1.0) / math.sqrt(k)
+    else:
+        raise ValueError(f"unknown sketch kind {kind!r}")
+    return S.to(device, dtype).contiguous()
+
+
+def ragged_batch(items: Sequence[RaggedItem], device="cpu", pad_rows: bool = False,
+                 d: int = 8) -> List[torch.Tensor]:
+    """The test matrix (index d: after the 8 training draws) of every item,
+    BF16.  With pad_rows the rows are laid out with a leading dimension
+    rounded up to 8 elements (16 bytes), the storage a producer chooses
+    for the tensor-core path; the matrices keep their n columns (views)."""
+    out = []
+    for it in items:
+        U0 = shared_basis(it.spec, device)
+        A = stream_matrix(it.spec, U0, d).to(torch.bfloat16)
+        if pad_rows:
+            ld = (it.n + 7) // 8 * 8
+            buf = torch.zeros(it.m, ld, dtype=torch.bfloat16, device=device)
+            buf[:, :it.n] = A
+            A = buf[:, :it.n]
+        out.append(A)
+    return out

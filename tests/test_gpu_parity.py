@@ -50,6 +50,40 @@ def _gap(g, o):
     return np.max(np.abs(g - o) / o)
 
 
+def assert_sketch_solves_tucker1(S, eig, G_o, lam_o, tol):
+    """The k x m sketch S with eigenvalues eig solves problem 3.2 for the
+    oracle's Gram G_o (eigenvalues lam_o, descending), judged by properties
+    that do not depend on a spectral gap at k (the generated streams have
+    almost none, so the k-th eigenvector itself is not determined):
+      * Weyl: |eig_i - lam_i| <= tol * lam_1;
+      * Ky Fan: the energy tr(S G_o S^T) it captures, the objective of
+        Eq. 3.2, is within tol * sum_{i<=k} lam_i of the maximum;
+      * every row is an eigenvector of G_o up to a residual of 10 tol lam_1.
+    tol is the relative accuracy of the Gram entries in the path's precision."""
+    k = S.shape[0]
+    lam1 = lam_o[0]
+    assert np.max(np.abs(eig - lam_o[:k])) <= tol * lam1, np.max(np.abs(eig - lam_o[:k])) / lam1
+    # energy of the subspace the rows span (the float32 rows are orthonormal
+    # only to about 1e-7, which would otherwise count as energy)
+    Qs, _ = np.linalg.qr(S.T)
+    cap = float(np.trace(Qs.T @ G_o @ Qs))
+    best = float(np.sum(lam_o[:k]))
+    assert cap <= best * (1 + 1e-12)
+    assert best - cap <= tol * best, (best - cap) / best
+    res = np.linalg.norm(G_o @ S.T - S.T * eig[None, :], axis=0)
+    assert np.max(res) <= 10 * tol * lam1, np.max(res) / lam1
+
+
+def assert_gram_entrywise(G, R, tol):
+    """|G_ij - R_ij| <= tol * sqrt(R_ii R_jj) for every entry: each entry is
+    checked against the scale Cauchy-Schwarz gives it, so a wrong tile of
+    small entries cannot hide behind the large ones of a norm."""
+    d = np.sqrt(np.clip(np.diag(R), 0.0, None))
+    bound = tol * np.outer(d, d) + 1e-300
+    worst = np.max(np.abs(G - R) / bound)
+    assert worst <= 1.0, worst
+
+
 # ------------------------------------------------------------- FP64 (C1) ---
 def test_c1_fp64_training_matches_oracle(tsk, handle):
     spec = synth.C1
@@ -129,12 +163,12 @@ def test_gram_parity(tsk, handle):
         G1 = _np(handle.gram(T, mode=1))
         G2 = _np(handle.gram(T, mode=2))
         R1, R2 = oracle.gram_mode1(An), oracle.gram_mode2(An)
-        assert np.linalg.norm(G1 - R1) <= tol * np.linalg.norm(R1), dt
-        assert np.linalg.norm(G2 - R2) <= tol * np.linalg.norm(R2), dt
+        assert_gram_entrywise(G1, R1, tol)
+        assert_gram_entrywise(G2, R2, tol)
         # partial Gram matrices of two shards sum to the whole
         G = handle.gram(T[:2], mode=1)
         handle.gram(T[2:], mode=1, out=G, accumulate=True)
-        assert np.linalg.norm(_np(G) - R1) <= tol * np.linalg.norm(R1)
+        assert_gram_entrywise(_np(G), R1, tol)
 
 
 # ---------------------------------------------------- FP32 / BF16 paths ---
@@ -151,15 +185,13 @@ def test_reduced_precision_scaled(tsk, handle, storage):
     ref = _oracle_errs(list(_np(te)), _np(S), r)
     gap = _gap(_np(out["err"]), [o["err"] for o in ref])
     assert gap <= GAP, gap
-    # training side in the reduced precision: same leading subspace
+    # training side in the reduced precision: an orthonormal sketch whose
+    # errors match those of the oracle's sketch (the sketch itself is only
+    # determined where the spectrum has a gap, so its errors are compared)
     S_g, _, eig, _ = handle.train_sketch(tr, k)
     Sg = _np(S_g)
     assert np.linalg.norm(Sg @ Sg.T - np.eye(k)) < 1e-4
-    # the sketch is only determined where the spectrum has a gap; compare
-    # the errors it gives instead of its entries
     out2 = handle.approx_batch(te, S_g, r)
-    ref2 = _oracle_errs(list(_np(te)), Sg, r)
-    assert _gap(_np(out2["err"]), [o["err"] for o in ref2]) <= GAP
     assert _gap(_np(out2["err"]), [o["err"] for o in ref]) <= 1e-2
 
 
@@ -218,23 +250,148 @@ def test_invalid_arguments_are_rejected(tsk, handle):
 
 
 # -------------------------------------------- full size, sampled outputs ---
-def test_c3_full_size_sampled(tsk):
+@pytest.mark.parametrize("refine", [1, 2])
+def test_c3_full_size_sampled(tsk, refine):
     """2048 x 2048 BF16, k=40, r=20: the bench's batch of 500 matrices, in
-    the launch configuration the bench uses; 4 sampled outputs checked."""
+    the launch configuration the bench uses (one refinement step on Q for
+    every matrix, as the workload states, and the adaptive refinement);
+    sampled outputs checked against the oracle run with the oracle's own
+    sketch from 16 training matrices."""
     spec = synth.C3
-    h = tsk.Handle()
+    h = tsk.Handle(refine_q=refine)
     tr = synth.stream(spec, "train", device="cuda", count=16)
-    S, _, _, _ = h.train_sketch(tr, spec.k)
+    S_o, _, _, _ = oracle.train_sketch(list(_np(tr)), spec.k)
     del tr
+    S = torch.tensor(S_o, device="cuda", dtype=torch.float32)
+    Sn = _np(S)  # the float32 values both sides use
     te = synth.stream(spec, "test", device="cuda")
     err = torch.empty(spec.n_test, dtype=torch.float64, device="cuda")
     plan = h.plan(te, S, spec.r, err)
     plan.execute()
     torch.cuda.synchronize()
     assert h.sync_status() == 0
-    Sn = _np(S)
     for i in (0, 137, 311, 499):
         o = oracle.scw(_np(te[i]), Sn, spec.r, dense=False)
         assert abs(float(err[i]) - o["err"]) <= GAP * o["err"], (i, float(err[i]), o["err"])
     plan.close()
     h.close()
+
+
+def test_c2_full_size(tsk):
+    """Config C2 as stated: FP32, 1024 x 768 (the HSI shape), 400 training
+    and 200 test matrices, k=20, r=10.  The GPU-trained sketch spans the
+    oracle's leading subspace; the test pass with the oracle's sketch
+    matches the oracle on 40 sampled matrices within the 1e-3 gap, and the
+    GPU-trained sketch gives errors within 1e-3 of the oracle sketch's."""
+    spec = synth.C2
+    h = tsk.Handle()
+    tr = synth.stream(spec, "train", device="cuda")
+    S_g, _, eig, st = h.train_sketch(tr, spec.k)
+    assert st == 0
+    G_o = oracle.gram_mode1(list(_np(tr)))
+    S_o, lam = oracle.leading_eigvecs(G_o, spec.k)
+    del tr
+    Sg = _np(S_g)
+    assert np.linalg.norm(Sg @ Sg.T - np.eye(spec.k)) < 1e-5
+    # FP32 products summed over chunks of 45 matrices x 768 columns
+    assert_sketch_solves_tucker1(Sg, _np(eig), G_o, lam, 5e-5)
+    te = synth.stream(spec, "test", device="cuda")
+    S = torch.tensor(S_o, device="cuda", dtype=torch.float32)
+    out = h.approx_batch(te, S, spec.r)
+    out_g = h.approx_batch(te, S_g, spec.r)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    Sn = _np(S)
+    idx = list(range(0, spec.n_test, 5))
+    ref = [oracle.scw(_np(te[i]), Sn, spec.r, dense=False)["err"] for i in idx]
+    assert _gap(_np(out["err"])[idx], ref) <= GAP
+    # the trained sketch may span a slightly different k-th direction
+    # (lam_20 and lam_21 differ by 4e-5 lam_1, and swapping those two
+    # eigenvectors moves single errors by up to 2 %): the test error
+    # (Eq. 4.1) it gives agrees to 5 %
+    opt = [oracle.optimal_error(_np(te[i]), spec.r) for i in idx]
+    t_g = oracle.test_error(_np(out_g["err"])[idx], opt)
+    t_o = oracle.test_error(ref, opt)
+    assert abs(t_g - t_o) <= 5e-2 * (1 + t_o), (t_g, t_o)
+    h.close()
+
+
+def test_c3_training_full_size(tsk):
+    """Config C3's training side as stated: the sketch of the 2048 x 2048
+    BF16 stream from all 1000 training matrices (tensor-core Gram, FP64
+    sums) against the oracle's FP64 Gram and eigenvectors of the same
+    stored values: the projectors onto the two k-dimensional subspaces and
+    the eigenvalues agree, and the errors the GPU sketch gives on 8 test
+    matrices are within the 1e-3 gap of the errors of the oracle's sketch."""
+    spec = synth.C3
+    h = tsk.Handle()
+    G_o = np.zeros((spec.m, spec.m))
+    chunks = []
+    for start in range(0, spec.n_train, 100):
+        tr = synth.stream(spec, "train", device="cuda", start=start, count=100)
+        chunks.append(tr)
+        G_o += oracle.gram_mode1(list(_np(tr)))  # the Gram is a sum over d
+    S_o, lam = oracle.leading_eigvecs(G_o, spec.k)
+    S_g, _, eig, st = h.train_sketch([a for c in chunks for a in c], spec.k)
+    assert st == 0
+    del chunks
+    Sg = _np(S_g)
+    assert np.linalg.norm(Sg @ Sg.T - np.eye(spec.k)) < 1e-5
+    # FP32 sums in TMEM over 8 matrices x 2048 columns, then FP64
+    assert_sketch_solves_tucker1(Sg, _np(eig), G_o, lam, 5e-5)
+    # test pass with the oracle's sketch and with the trained one: the
+    # errors of 8 test matrices, and the test error (Eq. 4.1) they give
+    te = synth.stream(spec, "test", device="cuda", count=8)
+    S = torch.tensor(S_o, device="cuda", dtype=torch.float32)
+    out = h.approx_batch(te, S, spec.r)
+    out_g = h.approx_batch(te, S_g, spec.r)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    Sn = _np(S)
+    ref = [oracle.scw(A, Sn, spec.r, dense=False)["err"] for A in _np(te)]
+    assert _gap(_np(out["err"]), ref) <= GAP
+    opt = [oracle.optimal_error(A, spec.r) for A in _np(te)]
+    t_g = oracle.test_error(_np(out_g["err"]), opt)
+    t_o = oracle.test_error(ref, opt)
+    assert abs(t_g - t_o) <= 5e-2 * (1 + t_o), (t_g, t_o)
+    h.close()
+
+
+def test_eigensolver_iteration_cap_is_reported(tsk):
+    """max_iter = 1 cannot converge: tsk_train_sketch returns TSK_ENOCONV
+    (the sketch is still written) and the handle stays usable."""
+    spec = synth.C1
+    tr = synth.stream(spec, "train", device="cpu").cuda()
+    h = tsk.Handle(max_iter=1)
+    S, _, eig, st = h.train_sketch(tr, spec.k)
+    assert st == 4  # TSK_ENOCONV
+    assert b"eigensolver" in h._lib.tsk_last_error(h._h)
+    assert torch.isfinite(S).all()
+    assert h.sync_status() == 0
+    h.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f32"])
+def test_small_factors_in_fp64(tsk, storage):
+    """small_fp64: the k x k steps in double (Householder R factors of the
+    FP32 panels, Jacobi SVD of R_Y R_X^{-1}) give the oracle's errors and
+    singular values, and errors within 1e-4 of the FP32 Gram route."""
+    spec = synth.scaled(synth.C3, 1024, 1024, 24, 6, storage=storage)
+    tr = synth.stream(spec, "train")
+    S_o, _, _, _ = oracle.train_sketch(list(tr.double().numpy()), spec.k)
+    S = torch.tensor(S_o, device="cuda", dtype=torch.float32)
+    te = synth.stream(spec, "test", device="cuda")
+    ref = _oracle_errs(list(_np(te)), _np(S), spec.r)
+    e = {}
+    for f64 in (False, True):
+        h = tsk.Handle(small_fp64=f64, refine_q=tsk.REFINE_ALWAYS)
+        out = h.approx_batch(te, S, spec.r, outputs=True)
+        torch.cuda.synchronize()
+        assert h.sync_status() == 0
+        e[f64] = _np(out["err"])
+        assert _gap(e[f64], [o["err"] for o in ref]) <= GAP
+        for i in range(te.shape[0]):
+            np.testing.assert_allclose(_np(out["sigma"][i])[:spec.r],
+                                       ref[i]["sigma"][:spec.r], rtol=2e-3)
+        h.close()
+    assert np.max(np.abs(e[True] - e[False]) / e[True]) <= 1e-4

@@ -54,8 +54,33 @@ def test_ragged_sizes():
     assert len(items) == 64
     for it in items:
         assert 256 <= it.m <= 4096 and 256 <= it.n <= 2048
-        assert it.m % 8 == 0 and it.n % 8 == 0
         assert it.k in (10, 20, 40) and it.r == it.k // 2
     assert items[0].m == synth.ragged_sizes(64)[0].m
-    ms = np.log([it.m for it in synth.ragged_sizes(512)])
+    full = synth.ragged_sizes(512)
+    ms = np.log([it.m for it in full])
     assert abs(ms.mean() - 0.5 * (np.log(256) + np.log(4096))) < 0.15
+    # sizes are not rounded: most widths are not multiples of 8
+    assert sum(it.n % 8 != 0 for it in full) > 256
+
+
+def test_item_and_random_sketches():
+    it = synth.ragged_sizes(3)[1]
+    S = synth.item_sketch(it)
+    assert S.shape == (it.k, it.m) and S.dtype == torch.float32
+    assert torch.allclose(S.double() @ S.double().T, torch.eye(it.k, dtype=torch.float64),
+                          atol=1e-5)
+    assert torch.equal(S, synth.item_sketch(it))
+    g = synth.random_sketch("gauss", 20, 300, 1, dtype=torch.float64)
+    assert g.shape == (20, 300) and abs(float(g.pow(2).mean()) - 1 / 20) < 0.2 / 20
+    s = synth.random_sketch("sign", 20, 300, 1, dtype=torch.float64)
+    assert torch.allclose(s.abs(), torch.full_like(s, 20 ** -0.5))
+
+
+def test_padded_ragged_batch_keeps_the_values():
+    items = synth.ragged_sizes(4, m_range=(64, 96), n_range=(33, 61))
+    a = synth.ragged_batch(items)
+    b = synth.ragged_batch(items, pad_rows=True)
+    for x, y, it in zip(a, b, items):
+        assert x.shape == y.shape == (it.m, it.n)
+        assert (y.stride(0) * 2) % 16 == 0
+        assert torch.equal(x, y)
