@@ -112,7 +112,10 @@ typedef struct {
                          R_Y R_X^{-1}, as on the TSK_FP64 path.  Slower (the
                          Householder steps are serial); it exists to run the
                          k x k steps in FP64 where a configuration asks.     */
-  int32_t reserved;   /* must be 0                                            */
+  int32_t gram_tile;  /* tiles of the BF16 mode-1 Gram on the tensor cores:
+                         0 (default) 256 x 256 tiles, each on a pair of CTAs
+                         whose tensor cores work as one (M = N = 256 MMAs);
+                         1: 128 x 128 tiles on single CTAs                 */
 } tsk_options;
 
 /* One test-side matrix.  A: device, m x n, leading dimension lda >= n.
@@ -233,12 +236,78 @@ tsk_status tsk_plan_set_probe(tsk_plan plan, void* ev_begin, void* ev_end);
 tsk_status tsk_plan_info(tsk_plan plan, int64_t* workspace_bytes,
                          int32_t* launches_per_execute);
 
+/* Autotuner of the tensor-core sketch pass (BF16).  For every size class of
+   the batch where the kernel has two shapes -- 256 < m <= 2048, where a
+   matrix can be split over CTAs of 256 or of 512 rows -- it builds a plan
+   of up to 16 of the class's matrices for each shape, times the sketch pass
+   (CUDA events around it inside the plan's graph; best of reps executions
+   after one warm-up) and keeps the faster shape in the handle.  A size
+   class is (the cluster size at 512 rows per CTA, k rounded up to 8).  Plans
+   built afterwards take the tuned shapes.  Runs the work on stream and
+   synchronises it; the matrices are read, not changed. */
+tsk_status tsk_autotune(tsk_handle h, int64_t count, const tsk_mat_desc* mats, tsk_prec prec,
+                        int32_t reps, tsk_stream stream);
+/* Writes the handle's tuned shapes to a JSON file (one object per size
+   class with the times measured), or reads such a file back into the
+   handle (replacing its table). */
+tsk_status tsk_autotune_save(tsk_handle h, const char* path);
+tsk_status tsk_autotune_load(tsk_handle h, const char* path);
+
 /* Direct error ||A_d - US_d Vt_d||_F of factored approximations (problem
    1.1), one more pass over every A_d.  outs[i].US (m x r) and outs[i].Vt
    (r x n) must be non-NULL; err: device, count doubles. */
 tsk_status tsk_error(tsk_handle h, int64_t count, const tsk_mat_desc* mats,
                      tsk_prec prec, const tsk_mat_out* outs, double* err,
                      tsk_stream stream);
+
+/* ---- two-sided sketching (Section 3.2, Algorithms 3 and 5) ------------- */
+
+/* One test-side matrix for two-sided SCW.  A: device, m x n (lda >= n).
+   S: device, k x m row-major (leading dimension m); W: device, l x n
+   row-major (leading dimension n); double for TSK_FP64, float otherwise.
+   r: target rank. */
+typedef struct {
+  const void* A;
+  const void* S;
+  const void* W;
+  int64_t m, n, lda;
+  int32_t k, l, r, reserved;
+} tsk_mat2_desc;
+
+/* Algorithm 3 (two-sided SCW) for a batch: Q = qr((S A)^T) (n x k),
+   P = qr(A W^T) (m x l), the l x k core P^T A Q, its rank-r truncation and
+   B = P [P^T A Q]_r Q^T.  One pass over each A gives X = (S A)^T,
+   Y = A X and Z = A W^T; the core is R_Z^{-T} (Z^T Y) R_X^{-1} with R_X, R_Z
+   the R factors (blockwise Householder) of X and Z, its SVD is one-sided
+   Jacobi in double, and err (device, count doubles, nullable) receives
+   ||A - B||_F = sqrt(||A||^2 - sum_{i<=r} sigma_i(core)^2) (P and Q are
+   orthonormal).  normA2 (device, nullable): ||A||_F^2.  outs (host array,
+   nullable): US = P U_r Sigma_r (m x r), Vt = (Q V_r)^T (r x n), sigma
+   (k values: the min(k, l) singular values of the core, then zeros).
+   Needs 1 <= r <= min(k, l), k <= n, l <= m, k, l <= TSK_MAX_K.  Rank
+   deficiency of S A or A W^T raises TSK_ERANKDEF in the status word.
+   Blocks until the work is done (the descriptors are staged from the
+   host). */
+tsk_status tsk_approx_two_sided(tsk_handle h, int64_t count, const tsk_mat2_desc* mats,
+                                tsk_prec prec, const tsk_mat_out* outs, double* err,
+                                double* normA2, tsk_stream stream);
+
+/* Training side of the two-sided sketch: the Tucker2 problem (Eq. 3.6) of
+   the D training matrices A (host array of device pointers, m x n, lda >=
+   n) by HOOI (Algorithm 5 with the mode-3 factor the identity), started
+   from the HOSVD pair (leading eigenvectors of the mode-1 and mode-2 Gram
+   matrices).  A sweep replaces S by the top k eigenvectors of
+   sum_d (A_d W^T)(A_d W^T)^T and then W by the top l eigenvectors of
+   sum_d (S A_d)^T (S A_d); it stops when the core energy
+   sum_d ||S A_d W^T||_F^2 changed by less than tol * sum_d ||A_d||_F^2
+   (tol <= 0 selects 1e-12 for TSK_FP64, 1e-7 otherwise) or after
+   max_sweeps sweeps.  S (k x m) and W (l x n): device, double for TSK_FP64,
+   float otherwise.  core_energy (host, nullable) receives the final core
+   energy, sweeps (host, nullable) the number of sweeps made.  Blocks. */
+tsk_status tsk_train_two_sided(tsk_handle h, const void* const* A, int64_t D, int64_t m,
+                               int64_t n, int64_t lda, tsk_prec prec, int32_t k, int32_t l,
+                               int32_t max_sweeps, double tol, void* S, void* W,
+                               double* core_energy, int32_t* sweeps, tsk_stream stream);
 
 /* ---- learned sketch refiner (IVY loss, Eq. 2.1) ------------------------ */
 

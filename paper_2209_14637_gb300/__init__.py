@@ -46,7 +46,7 @@ class Options(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("refine_q", C.c_int32),
                 ("max_iter", C.c_int32), ("err_mode", C.c_int32),
                 ("eig_tol", C.c_double), ("spin_limit", C.c_int64),
-                ("small_fp64", C.c_int32), ("reserved", C.c_int32)]
+                ("small_fp64", C.c_int32), ("gram_tile", C.c_int32)]
 
 
 class MatDesc(C.Structure):
@@ -57,6 +57,13 @@ class MatDesc(C.Structure):
 
 class MatOut(C.Structure):
     _fields_ = [("US", C.c_void_p), ("Vt", C.c_void_p), ("sigma", C.c_void_p)]
+
+
+class Mat2Desc(C.Structure):
+    _fields_ = [("A", C.c_void_p), ("S", C.c_void_p), ("W", C.c_void_p),
+                ("m", C.c_int64), ("n", C.c_int64), ("lda", C.c_int64),
+                ("k", C.c_int32), ("l", C.c_int32), ("r", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class RefineOpts(C.Structure):
@@ -100,6 +107,13 @@ def load_library(path: str = LIB_PATH):
         "tsk_error": ([P, I64, C.POINTER(MatDesc), I32, C.POINTER(MatOut), P, P], I32),
         "tsk_ivy_grad": ([P, I64, C.POINTER(MatDesc), I32, P, P, P, P], I32),
         "tsk_approx_noalloc": ([C.POINTER(MatDesc), I32, P, P, P, P], I32),
+        "tsk_autotune": ([P, I64, C.POINTER(MatDesc), I32, I32, P], I32),
+        "tsk_autotune_save": ([P, C.c_char_p], I32),
+        "tsk_autotune_load": ([P, C.c_char_p], I32),
+        "tsk_approx_two_sided": ([P, I64, C.POINTER(Mat2Desc), I32, C.POINTER(MatOut),
+                                  P, P, P], I32),
+        "tsk_train_two_sided": ([P, C.POINTER(P), I64, I64, I64, I64, I32, I32, I32, I32,
+                                 D, P, P, C.POINTER(D), C.POINTER(I32), P], I32),
         "tsk_default_refine_options": ([C.POINTER(RefineOpts)], None),
         "tsk_refine_sketch": ([P, C.POINTER(MatDesc), I64, C.POINTER(MatDesc), I64, I32,
                                C.POINTER(RefineOpts), P, P, C.POINTER(D), P], I32),
@@ -139,7 +153,7 @@ class Handle:
     def __init__(self, kernel: int = KERNEL_AUTO, refine_q: int = REFINE_AUTO,
                  max_iter: int = 300, eig_tol: float = 0.0,
                  spin_limit: int = 1 << 24, err_mode: int = 0,
-                 small_fp64: bool = False):
+                 small_fp64: bool = False, gram_tile: int = 0):
         lib = load_library()
         if not torch.cuda.is_available():
             raise RuntimeError("libtsk needs a CUDA device; none is available")
@@ -147,6 +161,7 @@ class Handle:
         o.kernel, o.refine_q, o.max_iter = kernel, int(refine_q), max_iter
         o.eig_tol, o.spin_limit, o.err_mode = eig_tol, spin_limit, err_mode
         o.small_fp64 = int(bool(small_fp64))
+        o.gram_tile = int(gram_tile)
         h = C.c_void_p()
         st = lib.tsk_create(C.byref(h), C.byref(o))
         if st != 0:
@@ -304,6 +319,75 @@ class Handle:
                                         _stream(stream)))
         return err
 
+
+    def autotune(self, As, Ss, r, reps: int = 5, stream=None):
+        """Times the tensor-core sketch pass's two cluster shapes per size
+        class of this batch and keeps the faster in the handle."""
+        As = [As[i] for i in range(As.shape[0])] if isinstance(As, torch.Tensor) else list(As)
+        count = len(As)
+        Ss = [Ss] * count if isinstance(Ss, torch.Tensor) else list(Ss)
+        rs = [r] * count if isinstance(r, int) else list(r)
+        _require_cuda(*As, *Ss)
+        descs = self._descs(As, Ss, [S.shape[0] for S in Ss], rs)
+        self._check(self._lib.tsk_autotune(self._h, count, descs, _DTYPE_PREC[As[0].dtype],
+                                           reps, _stream(stream)))
+
+    def autotune_save(self, path: str):
+        self._check(self._lib.tsk_autotune_save(self._h, os.fsencode(path)))
+
+    def autotune_load(self, path: str):
+        self._check(self._lib.tsk_autotune_load(self._h, os.fsencode(path)))
+
+    # ---- two-sided sketching (Algorithms 3 and 5) -----------------------
+    def train_two_sided(self, As, k: int, l: int, max_sweeps: int = 50, tol: float = 0.0,
+                        stream=None):
+        """Tucker2 sketches (S k x m, W l x n) of the training matrices by
+        HOOI from the HOSVD start; returns (S, W, core_energy, sweeps, status)."""
+        mats = [As[i] for i in range(As.shape[0])] if isinstance(As, torch.Tensor) else list(As)
+        _require_cuda(*mats)
+        m, n = mats[0].shape
+        prec = _DTYPE_PREC[mats[0].dtype]
+        dev = mats[0].device
+        S = torch.empty(k, m, dtype=_PREC_COMPUTE[prec], device=dev)
+        W = torch.empty(l, n, dtype=_PREC_COMPUTE[prec], device=dev)
+        energy, sweeps = C.c_double(), C.c_int32()
+        ptrs = (C.c_void_p * len(mats))(*[a.data_ptr() for a in mats])
+        st = self._check(self._lib.tsk_train_two_sided(
+            self._h, ptrs, len(mats), m, n, mats[0].stride(0), prec, k, l, max_sweeps, tol,
+            _ptr(S), _ptr(W), C.byref(energy), C.byref(sweeps), _stream(stream)), allow=(4,))
+        return S, W, energy.value, sweeps.value, st
+
+    def approx_two_sided(self, As, Ss, Ws, r, outputs: bool = False, stream=None):
+        """Two-sided SCW (Algorithm 3) for every matrix; returns
+        dict(err, normA2[, US, Vt, sigma])."""
+        As = [As[i] for i in range(As.shape[0])] if isinstance(As, torch.Tensor) else list(As)
+        count = len(As)
+        Ss = [Ss] * count if isinstance(Ss, torch.Tensor) else list(Ss)
+        Ws = [Ws] * count if isinstance(Ws, torch.Tensor) else list(Ws)
+        rs = [r] * count if isinstance(r, int) else list(r)
+        _require_cuda(*As, *Ss, *Ws)
+        prec = _DTYPE_PREC[As[0].dtype]
+        dev = As[0].device
+        err = torch.empty(count, dtype=torch.float64, device=dev)
+        normA2 = torch.empty(count, dtype=torch.float64, device=dev)
+        res = {"err": err, "normA2": normA2}
+        outs = None
+        if outputs:
+            cd = _PREC_COMPUTE[prec]
+            US = [torch.empty(A.shape[0], rr, dtype=cd, device=dev) for A, rr in zip(As, rs)]
+            Vt = [torch.empty(rr, A.shape[1], dtype=cd, device=dev) for A, rr in zip(As, rs)]
+            sg = [torch.empty(S.shape[0], dtype=cd, device=dev) for S in Ss]
+            outs = (MatOut * count)(*[MatOut(u.data_ptr(), v.data_ptr(), g.data_ptr())
+                                      for u, v, g in zip(US, Vt, sg)])
+            res.update(US=US, Vt=Vt, sigma=sg)
+        descs = (Mat2Desc * count)()
+        for i in range(count):
+            A, S, W = As[i], Ss[i], Ws[i]
+            descs[i] = Mat2Desc(A.data_ptr(), S.data_ptr(), W.data_ptr(), A.shape[0],
+                                A.shape[1], A.stride(0), S.shape[0], W.shape[0], int(rs[i]), 0)
+        self._check(self._lib.tsk_approx_two_sided(self._h, count, descs, prec, outs,
+                                                   _ptr(err), _ptr(normA2), _stream(stream)))
+        return res
 
     # ---- learned refiner ------------------------------------------------
     def ivy_grad(self, As, S, r: int, stream=None):

@@ -541,9 +541,14 @@ __device__ void fin_eigen(const MatDev& md, int k, int r, int kc, int gld, int g
   }
   __syncthreads();
   for (int c = tid; c < k; c += FT) {  // descending eigenvalues
+    // NaN ranks below everything (a total order), so `order` is a
+    // permutation whatever the values: it indexes shared memory below
     int rank = 0;
-    const float lc = lam[c];
-    for (int c2 = 0; c2 < k; ++c2) rank += (lam[c2] > lc) || (lam[c2] == lc && c2 < c);
+    const float lc = lam[c] == lam[c] ? lam[c] : -INFINITY;
+    for (int c2 = 0; c2 < k; ++c2) {
+      const float l2 = lam[c2] == lam[c2] ? lam[c2] : -INFINITY;
+      rank += (l2 > lc) || (l2 == lc && c2 < c);
+    }
     order[rank] = c;
   }
   __syncthreads();

@@ -154,12 +154,215 @@ sketch_y_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ items,
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same two kernels for float compute (FP32 and BF16 inputs): 128 threads
+// per 64-wide item, each thread an 8 x KP/16 register tile fed by two float4
+// shared loads and KP/16 broadcast loads per step (24 FMAs per 5 loads at
+// KP = 48, against 12 per 7 above), and float4 / 8-byte global loads of A
+// where its rows allow them.
+// ---------------------------------------------------------------------------
+template <typename Tin>
+__device__ __forceinline__ bool rows_vec_ok(const Tin* A, long long lda) {
+  // a 4-element vector at any multiple of 4 columns stays aligned
+  return (((uintptr_t)A) % (4 * sizeof(Tin)) == 0) && (lda % 4 == 0);
+}
+__device__ __forceinline__ void load4(const float* p, float* v) {
+  const float4 w = *reinterpret_cast<const float4*>(p);
+  v[0] = w.x;
+  v[1] = w.y;
+  v[2] = w.z;
+  v[3] = w.w;
+}
+__device__ __forceinline__ void load4(const __nv_bfloat16* p, float* v) {
+  const uint2 w = *reinterpret_cast<const uint2*>(p);
+  v[0] = __uint_as_float(w.x << 16);
+  v[1] = __uint_as_float(w.x & 0xFFFF0000u);
+  v[2] = __uint_as_float(w.y << 16);
+  v[3] = __uint_as_float(w.y & 0xFFFF0000u);
+}
+
+template <typename Tin, int KP>
+__global__ void __launch_bounds__(128)
+sketch_x_f32_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ items,
+                    float* __restrict__ X, double* __restrict__ normA2) {
+  constexpr int BJ = 64, BI = 32, CPT = KP / 16;
+  __shared__ __align__(16) float As[BI][BJ];
+  __shared__ __align__(16) float Ss[BI][KP];
+  __shared__ double red[4];
+  const int2 it = items[blockIdx.x];
+  const MatDev md = mats[it.x];
+  const Tin* __restrict__ A = (const Tin*)md.A;
+  const float* __restrict__ S = (const float*)md.S;
+  const long long m = md.m, n = md.n, lda = md.lda;
+  const int k = md.k;
+  const int tid = threadIdx.x, jg = tid & 7, cg = tid >> 3;
+  const long long j0 = (long long)it.y * BJ;
+  const bool vec = rows_vec_ok(A, lda);
+  float acc[8][CPT];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int p = 0; p < CPT; ++p) acc[q][p] = 0.f;
+  double sq = 0.0;
+  for (long long i0 = 0; i0 < m; i0 += BI) {
+    float part = 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {  // 512 quads of the 32 x 64 chunk
+      const int e4 = tid + 128 * t, ii = e4 >> 4, c4 = (e4 & 15) * 4;
+      const long long i = i0 + ii, j = j0 + c4;
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      if (i < m) {
+        if (vec && j + 3 < n) {
+          load4(A + i * lda + j, v);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (j + u < n) v[u] = to_float(A[i * lda + j + u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) part = fmaf(v[u], v[u], part);
+      *reinterpret_cast<float4*>(&As[ii][c4]) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    sq += (double)part;
+    for (int e = tid; e < BI * KP; e += 128) {
+      const int c = e / BI, ii = e % BI;
+      const long long i = i0 + ii;
+      Ss[ii][c] = (c < k && i < m) ? S[(long long)c * m + i] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ii = 0; ii < BI; ++ii) {
+      float a[8], sv[CPT];
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[ii][jg * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[ii][jg * 8 + 4]);
+      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
+      a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+#pragma unroll
+      for (int p = 0; p < CPT; ++p) sv[p] = Ss[ii][cg * CPT + p];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int p = 0; p < CPT; ++p) acc[q][p] = fmaf(a[q], sv[p], acc[q][p]);
+    }
+    __syncthreads();
+  }
+  float* __restrict__ Xm = X + md.offX;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const long long j = j0 + jg * 8 + q;
+    if (j < n) {
+#pragma unroll
+      for (int p = 0; p < CPT; ++p) Xm[j * KP + cg * CPT + p] = acc[q][p];
+    }
+  }
+  sq = warp_sum(sq);
+  if ((tid & 31) == 0) red[tid >> 5] = sq;
+  __syncthreads();
+  if (tid == 0) atomicAdd(normA2 + it.x, (red[0] + red[1]) + (red[2] + red[3]));
+}
+
+template <typename Tin, int KP>
+__global__ void __launch_bounds__(128)
+sketch_y_f32_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ items,
+                    const float* __restrict__ X, float* __restrict__ Y) {
+  constexpr int BI = 64, BJ = 32, CPT = KP / 16, LDT = BI + 4;
+  __shared__ __align__(16) float AsT[BJ][LDT];
+  __shared__ __align__(16) float Xs[BJ][KP];
+  const int2 it = items[blockIdx.x];
+  const MatDev md = mats[it.x];
+  const Tin* __restrict__ A = (const Tin*)md.A;
+  const long long m = md.m, n = md.n, lda = md.lda;
+  const float* __restrict__ Xm = X + md.offX;
+  const int tid = threadIdx.x, ig = tid & 7, cg = tid >> 3;
+  const long long i0 = (long long)it.y * BI;
+  const bool vec = rows_vec_ok(A, lda);
+  float acc[8][CPT];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int p = 0; p < CPT; ++p) acc[q][p] = 0.f;
+  for (long long j0 = 0; j0 < n; j0 += BJ) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {  // 512 quads of the 64 x 32 chunk, stored transposed
+      const int e4 = tid + 128 * t, ii = e4 >> 3, c4 = (e4 & 7) * 4;
+      const long long i = i0 + ii, j = j0 + c4;
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      if (i < m) {
+        if (vec && j + 3 < n) {
+          load4(A + i * lda + j, v);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (j + u < n) v[u] = to_float(A[i * lda + j + u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) AsT[c4 + u][ii] = v[u];
+    }
+    for (int e = tid; e < BJ * KP / 4; e += 128) {  // X rows are KP floats, 16-byte aligned
+      const int jj = e / (KP / 4), c4 = (e % (KP / 4)) * 4;
+      const long long j = j0 + jj;
+      float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j < n) w = *reinterpret_cast<const float4*>(Xm + j * KP + c4);
+      *reinterpret_cast<float4*>(&Xs[jj][c4]) = w;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < BJ; ++jj) {
+      float a[8], xv[CPT];
+      const float4 a0 = *reinterpret_cast<const float4*>(&AsT[jj][ig * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&AsT[jj][ig * 8 + 4]);
+      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
+      a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+#pragma unroll
+      for (int p = 0; p < CPT; ++p) xv[p] = Xs[jj][cg * CPT + p];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int p = 0; p < CPT; ++p) acc[q][p] = fmaf(a[q], xv[p], acc[q][p]);
+    }
+    __syncthreads();
+  }
+  float* __restrict__ Ym = Y + md.offY;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const long long i = i0 + ig * 8 + q;
+    if (i < m) {
+#pragma unroll
+      for (int p = 0; p < CPT; ++p) Ym[i * KP + cg * CPT + p] = acc[q][p];
+    }
+  }
+}
+
 template <typename Tin, typename Tc>
 static cudaError_t sketch_dispatch_kp(int kp, const MatDev* mats,
                                       const int2* items, int nitems, void* X,
                                       double* normA2, const void* Xin, void* Y,
                                       bool is_x, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
+  if constexpr (sizeof(Tc) == 4) {  // float compute: the 8 x KP/16 register-tile kernels
+#define TSK_SK4(KPV)                                                                   \
+  case KPV:                                                                            \
+    if (is_x)                                                                          \
+      sketch_x_f32_kernel<Tin, KPV><<<nitems, 128, 0, s>>>(mats, items, (float*)X,     \
+                                                            normA2);                   \
+    else                                                                               \
+      sketch_y_f32_kernel<Tin, KPV><<<nitems, 128, 0, s>>>(mats, items,               \
+                                                            (const float*)Xin,         \
+                                                            (float*)Y);                \
+    break;
+    switch (kp) {
+      TSK_SK4(16)
+      TSK_SK4(32)
+      TSK_SK4(48)
+      TSK_SK4(64)
+      default:
+        return cudaErrorInvalidValue;
+    }
+#undef TSK_SK4
+    return cudaGetLastError();
+  }
 #define TSK_SK(KPV)                                                        \
   case KPV:                                                                \
     if (is_x)                                                              \

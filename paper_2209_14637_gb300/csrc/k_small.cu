@@ -104,7 +104,15 @@ __device__ void jacobi_columns(T* M, T* V, int nrow, int ncol, int ld,
   }
 }
 
-// sig[c] = ||M[:, c]||, order[rank] = c with descending sig (stable).
+// NaN ordered below every number (-inf included: ties go by index), so a
+// ranking by it is a permutation whatever the values.
+template <typename T>
+__device__ __forceinline__ T nan_low(T x) {
+  return x == x ? x : -INFINITY;
+}
+
+// sig[c] = ||M[:, c]||, order[rank] = c with descending sig (stable; a
+// permutation even when some norms are NaN).
 template <typename T>
 __device__ void column_norms_sorted(const T* M, int nrow, int ncol, int ld,
                                     T* sig, int* order) {
@@ -117,7 +125,8 @@ __device__ void column_norms_sorted(const T* M, int nrow, int ncol, int ld,
   for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
     int rank = 0;
     for (int c2 = 0; c2 < ncol; ++c2)
-      rank += (sig[c2] > sig[c]) || (sig[c2] == sig[c] && c2 < c);
+      rank += (nan_low(sig[c2]) > nan_low(sig[c])) ||
+              (nan_low(sig[c2]) == nan_low(sig[c]) && c2 < c);
     order[rank] = c;
   }
   __syncthreads();

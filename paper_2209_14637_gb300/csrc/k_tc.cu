@@ -324,23 +324,39 @@ struct Ctl {
   int abort;
 };
 
+// try_wait whose suspension is capped at `hint_ns` nanoseconds (it returns
+// at the phase change or when the cap runs out, whichever comes first).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity,
+                                                   uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait.  Returns false on timeout (after raising the status bit and
-// the CTA-wide abort flag) or when the CTA is already aborting.
+// the CTA-wide abort flag) or when the CTA is already aborting.  Each poll
+// suspends for at most the time left (at most 100 us), and the clock is read
+// after every poll, so the bound holds for any spin limit: a limit shorter
+// than the work in flight makes the wait run out.
 template <class PP>
 __device__ __forceinline__ bool bwait(uint32_t bar, uint32_t parity, volatile Ctl* ctl,
                                       const PP& P) {
   if (ctl->abort) return false;
-  if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
-  for (uint32_t i = 1;; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63) == 0) {
-      if (ctl->abort) return false;
-      if ((long long)(globaltimer() - t0) > P.timeout_ns) {
-        atomicOr(P.status, kStatusTimeout);
-        ctl->abort = 1;
-        return false;
-      }
+  const uint32_t hint = (uint32_t)(P.timeout_ns < 100000 ? P.timeout_ns : 100000);
+  for (;;) {
+    if (mbar_try_wait_hint(bar, parity, hint)) return true;
+    if (ctl->abort) return false;
+    if ((long long)(globaltimer() - t0) > P.timeout_ns) {
+      atomicOr(P.status, kStatusTimeout);
+      ctl->abort = 1;
+      return false;
     }
   }
 }
@@ -712,13 +728,15 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
         // significant bits of X instead of 8.  The rows are written only
         // when every CTA's MMA-Y and this CTA's X writer are done with the
         // previous contents of buffer h.
-        bwait_warp(bar(B_XBEMPTY + h), (v & 1) ^ 1, ctl, P);
-        bwait_warp(bar(B_XWDONE + h), (v & 1) ^ 1, ctl, P);
-        bwait_warp(bar(B_RFULL + h), v & 1, ctl, P);
+        // (after a timeout the buffers hold nothing valid: skip the reduce,
+        // but keep arriving so that no local wait is left hanging)
+        const bool got = bwait_warp(bar(B_XBEMPTY + h), (v & 1) ^ 1, ctl, P) &&
+                         bwait_warp(bar(B_XWDONE + h), (v & 1) ^ 1, ctl, P) &&
+                         bwait_warp(bar(B_RFULL + h), v & 1, ctl, P);
         const unsigned char* rb = sm + OFF_RECV + h * RECV_BYTES;
         unsigned char* xb = sm + OFF_XB + h * XB_BYTES;
 #pragma unroll 1
-        for (int it = xt; it < R * 8; it += 64) {
+        for (int it = xt; got && it < R * 8; it += 64) {
           const int ri = it % R, ob = it / R;  // row, octet of columns
           const int cr = (int)rank * R + ri;
           float acc[8];
@@ -838,7 +856,9 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
       for (int q = 0; q < nblk; ++q, ++g) {
         const int h = (int)(g & 1);
         const uint32_t v = (uint32_t)(g >> 1);
-        if (bwait_warp(bar(B_XREADY + h), v & 1, ctl, P)) {
+        // the abort flag is read again after the wait: rows written by an
+        // exchange that ran out are not valid
+        if (bwait_warp(bar(B_XREADY + h), v & 1, ctl, P) && !ctl->abort) {
           const unsigned char* xb = sm + OFF_XB + h * XB_BYTES;
           const long long jb = (long long)q * NB;
           const int jmax = (int)min((long long)NB, n - jb);
@@ -1046,8 +1066,10 @@ cudaError_t launch_class(const TcParams& prm, int nclusters, cudaStream_t s) {
 // same per column block whatever MC is, so 512 rows per CTA (two 64 KB
 // stages) beat 256 rows (four 32 KB stages) once a cluster is needed; a
 // matrix of at most 256 rows takes one CTA with four stages.
-void cluster_shape(long long m, int* C, int* MC) {
+void cluster_shape(long long m, int* C, int* MC, int mc_pref = 0) {
   *MC = m <= 256 ? 256 : 512;
+  if (mc_pref == 256 && m <= 8 * 256) *MC = 256;  // up to clusters of 8
+  if (mc_pref == 512) *MC = 512;
   int c = 1;
   while ((long long)c * *MC < m) c *= 2;
   *C = c;
@@ -1062,6 +1084,9 @@ cudaError_t class_attrs(int C, int MC, int* ncl) {
     if (e == cudaSuccess) *ncl = max_clusters<c_, mc_>(); \
   }
   TSK_TC_CASE(1, 256)
+  TSK_TC_CASE(2, 256)
+  TSK_TC_CASE(4, 256)
+  TSK_TC_CASE(8, 256)
   TSK_TC_CASE(1, 512)
   TSK_TC_CASE(2, 512)
   TSK_TC_CASE(4, 512)
@@ -1072,6 +1097,9 @@ cudaError_t class_attrs(int C, int MC, int* ncl) {
 
 cudaError_t class_launch(int C, int MC, const TcParams& prm, int nclusters, cudaStream_t s) {
   if (C == 1 && MC == 256) return launch_class<1, 256>(prm, nclusters, s);
+  if (C == 2 && MC == 256) return launch_class<2, 256>(prm, nclusters, s);
+  if (C == 4 && MC == 256) return launch_class<4, 256>(prm, nclusters, s);
+  if (C == 8 && MC == 256) return launch_class<8, 256>(prm, nclusters, s);
   if (C == 1 && MC == 512) return launch_class<1, 512>(prm, nclusters, s);
   if (C == 2 && MC == 512) return launch_class<2, 512>(prm, nclusters, s);
   if (C == 4 && MC == 512) return launch_class<4, 512>(prm, nclusters, s);
@@ -1275,7 +1303,284 @@ __global__ void __launch_bounds__(GNT, 1) gram_tc_kernel(const __grid_constant__
   }
 }
 
-// G[a][b] = G[b][a] for a > b: the kernel above fills the upper block
+// ---------------------------------------------------------------------------
+// T1 on CTA pairs: the same Gram with 256 x 256 tiles of G, each computed by
+// a cluster of two CTAs whose tensor cores work as one (tcgen05 .cta_group::2,
+// M = N = 256, K = 16 per MMA).  CTA rank rho of the pair holds rows
+// [rho * 128, rho * 128 + 128) of the tile's row block (the M half of the A
+// operand) and the same rows of its column block (the N half of the B
+// operand), and its TMEM receives those 128 rows of the 256 x 256 tile.
+// Per 64-column stage a CTA loads 32 KB and its tensor core does half of a
+// 256 x 256 x 64 product: twice the flops per loaded byte of the 128 x 128
+// single-CTA tile, which is what bounds that kernel (its operand rows come
+// from L2 faster than HBM, but not fast enough to keep the MMAs busy).
+//
+// Roles: in both CTAs warp 0 issues the TMA loads of its own halves, which
+// count their bytes on the even CTA's FULL barrier (.cta_group::2 loads);
+// warp 1 of the even CTA issues the MMAs and commits them to the EMPTY and
+// TFULL barriers of both CTAs; warps 2-5 of each CTA add its 128 TMEM lanes
+// to G and arrive on the even CTA's TEMPTY barrier.
+// ---------------------------------------------------------------------------
+struct Gram2Params {
+  const CUtensorMap* tmaps;  // one per matrix: box 64 columns x 128 rows
+  long long D, m, n;
+  double* G;
+  int ntile;   // ceil(m / 256)
+  int splits;  // pairs per tile (contiguous ranges of matrices)
+  int* status;
+  long long timeout_ns;
+};
+
+constexpr int G2STG = 6;
+constexpr int G2HALF = 128 * 128;       // 128 rows x 64 BF16 columns = 16 KB
+constexpr int G2STAGE = 2 * G2HALF;     // A half, B half
+constexpr int G2_OFF_BAR = G2STG * G2STAGE;
+enum { G2_FULL = 0, G2_EMPTY = G2STG, G2_TFULL = 2 * G2STG, G2_TEMPTY = 2 * G2STG + 2,
+       G2_DRAIN = 2 * G2STG + 4, G2_COUNT = 2 * G2STG + 5 };
+constexpr int G2_SMEM = G2_OFF_BAR + 256;
+static_assert(G2_COUNT * 8 + 16 <= 256, "gram2 barrier area");
+static_assert(G2_SMEM <= 227 * 1024, "gram2 shared memory");
+
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int x,
+                                                 int y, uint32_t bar_cluster) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::"
+      "bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar_cluster)
+      : "memory");
+}
+__device__ __forceinline__ void tc_mma_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit_pair_mc(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster."
+      "b64 [%0], %1;" ::"r"(bar),
+      "h"((uint16_t)3)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit_pair(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(
+                   cluster_addr)
+               : "memory");
+}
+// try_wait with cluster-scope acquire: the barrier is arrived on from the
+// peer CTA after it has read its TMEM.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+template <class PP>
+__device__ __forceinline__ bool bwait_cluster(uint32_t bar, uint32_t parity, volatile Ctl* ctl,
+                                              const PP& P) {
+  if (ctl->abort) return false;
+  const uint64_t t0 = globaltimer();
+  for (;;) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    if (ctl->abort) return false;
+    if ((long long)(globaltimer() - t0) > P.timeout_ns) {
+      atomicOr(P.status, kStatusTimeout);
+      ctl->abort = 1;
+      return false;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant__ Gram2Params P) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = smem_raw;
+  const uint32_t sb = smem_u32(sm);
+  // every CTA of the launch sees the same layout, so both CTAs of a pair
+  // leave here together
+  if (sb & 1023) {
+    if (threadIdx.x == 0) atomicOr(P.status, kStatusTimeout);
+    return;
+  }
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t rank = cluster_rank();  // 0: issues the MMAs; 1: its peer
+  const bool lead = rank == 0;
+  auto bar = [&](int i) -> uint32_t { return sb + G2_OFF_BAR + 8 * i; };
+  volatile Ctl* ctl = (volatile Ctl*)(sm + G2_OFF_BAR + 8 * G2_COUNT);
+  uint32_t* tmem_slot = (uint32_t*)(sm + G2_OFF_BAR + 8 * G2_COUNT + 8);
+  int t = (int)(blockIdx.x >> 1), ti = 0;  // tile (ti, tj), ti <= tj
+  while (t >= P.ntile - ti) {
+    t -= P.ntile - ti;
+    ++ti;
+  }
+  const int tj = ti + t;
+  const bool diag = ti == tj;
+  const long long d0 = P.D * (long long)blockIdx.y / P.splits;
+  const long long d1 = P.D * (long long)(blockIdx.y + 1) / P.splits;
+  const int nkb = (int)((P.n + 63) / 64);
+  const int ngroups = (int)((d1 - d0 + GFL - 1) / GFL);
+  if (tid == 0) {
+    for (int s = 0; s < G2STG; ++s) {
+      mbar_init(bar(G2_FULL + s), 1);   // the even CTA's expect-tx; bytes of both
+      mbar_init(bar(G2_EMPTY + s), 1);  // the pair's MMA commit
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar(G2_TFULL + b), 1);   // the pair's MMA commit
+      mbar_init(bar(G2_TEMPTY + b), 8);  // epilogue warps of both CTAs
+    }
+    mbar_init(bar(G2_DRAIN), 1);
+    ctl->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {  // one warp of each CTA allocates, collectively for the pair
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      const int rowA = ti * 256 + (int)rank * 128, rowB = tj * 256 + (int)rank * 128;
+      long long q = 0;
+      for (long long d = d0; d < d1; ++d) {
+        const CUtensorMap* map = P.tmaps + d;
+        bool stop = false;
+        for (int kb = 0; kb < nkb; ++kb, ++q) {
+          const int s = (int)(q % G2STG);
+          const uint32_t u = (uint32_t)(q / G2STG);
+          if (!bwait(bar(G2_EMPTY + s), (u & 1) ^ 1, ctl, P)) {
+            stop = true;
+            break;
+          }
+          const uint32_t full = mapa(bar(G2_FULL + s), 0);
+          if (lead) mbar_expect_tx(bar(G2_FULL + s), diag ? 2 * G2HALF : 2 * G2STAGE);
+          tma_load_2d_pair(sb + s * G2STAGE, map, kb * 64, rowA, full);
+          if (!diag) tma_load_2d_pair(sb + s * G2STAGE + G2HALF, map, kb * 64, rowB, full);
+        }
+        if (stop) break;
+      }
+      // The even CTA drains the loads of both CTAs before the pair leaves
+      // (its MMA issuer waits for the last MMAs, which read every stage);
+      // after an abort the teardown waits out the few still in flight.
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lead && lane == 0) {
+      const uint32_t idesc = idesc_bf16(256, 256, 0, 0);
+      long long q = 0;
+      bool ok = true;
+      for (int grp = 0; grp < ngroups && ok; ++grp) {
+        const int buf = grp & 1;
+        const uint32_t v = (uint32_t)(grp >> 1);
+        if (!bwait_cluster(bar(G2_TEMPTY + buf), (v & 1) ^ 1, ctl, P)) break;
+        tc_fence_after();
+        const long long dlo = d0 + (long long)grp * GFL;
+        const long long dhi = dlo + GFL < d1 ? dlo + GFL : d1;
+        bool first = true;
+        for (long long d = dlo; d < dhi && ok; ++d) {
+          for (int kb = 0; kb < nkb; ++kb, ++q) {
+            const int s = (int)(q % G2STG);
+            const uint32_t u = (uint32_t)(q / G2STG);
+            if (!bwait(bar(G2_FULL + s), u & 1, ctl, P)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = sb + s * G2STAGE, b0 = diag ? a0 : a0 + G2HALF;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              tc_mma_pair(tmem + buf * 256, sdesc(a0 + kk * 32, 16, 1024),
+                          sdesc(b0 + kk * 32, 16, 1024), idesc, (first && kk == 0) ? 0u : 1u);
+            first = false;
+            tc_commit_pair_mc(bar(G2_EMPTY + s));
+          }
+        }
+        if (ok) tc_commit_pair_mc(bar(G2_TFULL + buf));
+      }
+      tc_commit_pair(bar(G2_DRAIN));
+      drain_wait(bar(G2_DRAIN), 0, P);
+    }
+  } else {
+    // ------------------------------------- epilogue (warps 2-5): TMEM -> G
+    const int lane_base = (warp & 3) * 32;
+    const long long row = (long long)ti * 256 + rank * 128 + lane_base + lane;
+    const bool atomic = P.splits > 1;
+    const uint32_t tempty0 = lead ? 0u : mapa(bar(G2_TEMPTY), 0);
+    for (int grp = 0; grp < ngroups; ++grp) {
+      const int buf = grp & 1;
+      const uint32_t v = (uint32_t)(grp >> 1);
+      if (!bwait_warp(bar(G2_TFULL + buf), v & 1, ctl, P)) break;
+      tc_fence_after();
+#pragma unroll 1
+      for (int c0 = 0; c0 < 256; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)lane_base << 16) + buf * 256 + c0, r);
+        tmem_wait_ld();
+        tmem_regs8(r);
+        tmem_regs8(r + 8);
+        if (row < P.m) {
+          double* g = P.G + row * P.m + (long long)tj * 256 + c0;
+          const long long cmax = P.m - ((long long)tj * 256 + c0);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            if (i < cmax) {
+              const double x = (double)__uint_as_float(r[i]);
+              if (atomic)
+                atomicAdd(g + i, x);
+              else
+                g[i] += x;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if (lead)
+          mbar_arrive(bar(G2_TEMPTY + buf));
+        else
+          mbar_arrive_remote(tempty0 + 8 * buf);
+      }
+    }
+  }
+  // ---- teardown: neither CTA leaves while the other's operations may still
+  // touch its shared memory or TMEM
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  if (ctl->abort && tid == 0) {
+    const uint64_t t0 = globaltimer();
+    while (globaltimer() - t0 < 200000ull) {
+    }
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+  }
+}
+
+// G[a][b] = G[b][a] for a > b: the kernels above fill the upper block
 // triangle (diagonal blocks in full).
 __global__ void mirror_upper_kernel(double* __restrict__ G, long long m) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1347,7 +1652,7 @@ void gram_cache_destroy(GramCache* c) {
 
 cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long long n,
                            long long lda, double* G, int* status, long long spin_limit,
-                           GramCache* cache, cudaStream_t s) {
+                           GramCache* cache, bool pairs, cudaStream_t s) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
   if (!enc || !cache) return cudaErrorNotSupported;
   const bool hit = cache->dmaps && cache->m == m && cache->n == n && cache->lda == lda &&
@@ -1389,13 +1694,57 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
   int dev = 0, nsm = 148;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaSuccess;
+  if (pairs) {
+    // 256 x 256 tiles on CTA pairs; the matrices are split over pairs so
+    // that the grid fills the SMs
+    const int ntile2 = (int)((m + 255) / 256);
+    const long long ntp2 = (long long)ntile2 * (ntile2 + 1) / 2;
+    if (2 * ntp2 > 2147483647ll) return cudaErrorNotSupported;
+    long long splits2 = nsm / (2 * ntp2);
+    if (splits2 > D) splits2 = D;
+    if (splits2 < 1) splits2 = 1;
+    if (splits2 > 65535) splits2 = 65535;
+    Gram2Params q;
+    q.tmaps = cache->dmaps;
+    q.D = D;
+    q.m = m;
+    q.n = n;
+    q.G = G;
+    q.ntile = ntile2;
+    q.splits = (int)splits2;
+    q.status = status;
+    q.timeout_ns = std::max<long long>(spin_limit, 1) * 120;
+    e = cudaFuncSetAttribute(gram2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             G2_SMEM);
+    if (e == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      cfg.gridDim = dim3((unsigned)(2 * ntp2), (unsigned)splits2, 1);
+      cfg.blockDim = dim3(GNT, 1, 1);
+      cfg.dynamicSmemBytes = G2_SMEM;
+      cfg.stream = s;
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 2;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, gram2_tc_kernel, q);
+    }
+    if (e == cudaSuccess) {
+      const long long tot = m * m;
+      mirror_upper_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(G, m);
+      e = cudaGetLastError();
+    }
+    return e;
+  }
   const int ntile = (int)((m + 127) / 128);
   const long long ntp = (long long)ntile * (ntile + 1) / 2;
   if (ntp > 65535 * 8) return cudaErrorNotSupported;
   long long splits = nsm / ntp;
   if (splits > D) splits = D;
   if (splits < 1) splits = 1;
-  cudaError_t e = cudaSuccess;
   GramParams prm;
   prm.tmaps = cache->dmaps;
   prm.D = D;
@@ -1422,9 +1771,9 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
 }
 
 cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int count,
-                       const int* ids, int nids, int kp, void* dev_X, void* dev_Y,
-                       double* dev_normA2, int* status, long long spin_limit, char* msg,
-                       int msglen) {
+                       const int* ids, int nids, const int* mc_pref, int kp, void* dev_X,
+                       void* dev_Y, double* dev_normA2, int* status, long long spin_limit,
+                       char* msg, int msglen) {
   *out = nullptr;
   auto fail = [&](const char* why) {
     if (msg && msglen > 0) snprintf(msg, msglen, "%s", why);
@@ -1449,21 +1798,22 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
   for (int t = 0; t < nids; ++t) {
     const int i = ids[t];
     int C, mc;
-    cluster_shape(hm[i].m, &C, &mc);
+    cluster_shape(hm[i].m, &C, &mc, mc_pref ? mc_pref[i] : 0);
     byC[std::make_pair(C, mc)].push_back(i);
   }
   // distinct sketch images
-  std::map<std::tuple<const void*, long long, int>, long long> img_of;
+  std::map<std::tuple<const void*, long long, int, int>, long long> img_of;
   std::vector<SImgDesc> sdesc;
   std::vector<long long> simg_off(count, 0);
   long long img_total = 0;
   for (int t = 0; t < nids; ++t) {
     const int i = ids[t];
-    auto key = std::make_tuple(hm[i].S, hm[i].m, hm[i].k);
+    int C, mc;
+    cluster_shape(hm[i].m, &C, &mc, mc_pref ? mc_pref[i] : 0);
+    // one image per sketch and cluster shape (the shape fixes its chunk count)
+    auto key = std::make_tuple(hm[i].S, hm[i].m, hm[i].k, C * mc);
     auto it = img_of.find(key);
     if (it == img_of.end()) {
-      int C, mc;
-      cluster_shape(hm[i].m, &C, &mc);
       SImgDesc sd;
       sd.S = (const float*)hm[i].S;
       sd.m = hm[i].m;
@@ -1610,16 +1960,19 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
   return cudaSuccess;
 }
 
-cudaError_t tc_launch(TcPlan* p, cudaStream_t s) {
+cudaError_t tc_launch_prep(TcPlan* p, cudaStream_t s) {
   if (!p) return cudaErrorInvalidValue;
   simg_prep_kernel<<<dim3(p->nsdesc, p->max_chunks), 256, 0, s>>>(p->d_sdesc, p->kpad,
                                                                     p->simg);
-  cudaError_t e = cudaGetLastError();
-  for (const TcClass& cl : p->classes) {
-    if (e != cudaSuccess) break;
-    e = class_launch(cl.C, cl.MC, cl.prm, cl.nclusters, s);
-  }
-  return e;
+  return cudaGetLastError();
+}
+
+int tc_classes(const TcPlan* p) { return p ? (int)p->classes.size() : 0; }
+
+cudaError_t tc_launch_class(TcPlan* p, int i, cudaStream_t s) {
+  if (!p || i < 0 || i >= (int)p->classes.size()) return cudaErrorInvalidValue;
+  const TcClass& cl = p->classes[(size_t)i];
+  return class_launch(cl.C, cl.MC, cl.prm, cl.nclusters, s);
 }
 
 int tc_launches(const TcPlan* p) { return p ? 1 + (int)p->classes.size() : 0; }

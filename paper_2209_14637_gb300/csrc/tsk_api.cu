@@ -4,11 +4,14 @@
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "tsk_internal.cuh"
@@ -51,11 +54,29 @@ struct tsk_handle_s {
   char last_error[512] = {0};
   int* d_status = nullptr;
   cudaStream_t cap_stream = nullptr;
-  cudaStream_t cap_stream2 = nullptr;  // second branch of a captured plan
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // branches of a captured plan: the sketch pass of each cluster-size class
+  // of the tensor-core kernel and the CUDA-core kernels run concurrently
+  static constexpr int kBranches = 8;
+  cudaStream_t branch[kBranches] = {nullptr};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kBranches] = {nullptr};
   std::vector<tsk_plan> cache;
   GramCache* gram_cache = nullptr;  // tensor maps of the last BF16 training set
+  // Autotuned rows of A per CTA of the tensor-core sketch, by size class:
+  // (cluster size at 512 rows per CTA, k rounded up to 8) -> 256 or 512.
+  std::map<std::pair<int, int>, int> tune;
+  std::map<std::pair<int, int>, std::pair<double, double>> tune_us;  // us / matrix (512, 256)
+  int tune_version = 0;
+  int force_mc = 0;  // while tuning: every matrix takes this shape
 };
+
+// Size class of a matrix for the autotuner: the cluster size it needs at
+// 512 rows per CTA, and k rounded up to 8 (the kernel's X~ rows).
+static std::pair<int, int> tune_key(int64_t m, int32_t k) {
+  int c = 1;
+  while ((int64_t)c * 512 < m) c *= 2;
+  return {c, (k + 7) / 8 * 8};
+}
 
 static thread_local char g_create_error[512] = "no error";
 
@@ -99,7 +120,7 @@ extern "C" void tsk_default_options(tsk_options* o) {
   o->err_mode = 0;
   o->spin_limit = 1ll << 24;
   o->small_fp64 = 0;
-  o->reserved = 0;
+  o->gram_tile = 0;
 }
 
 extern "C" tsk_status tsk_create(tsk_handle* out, const tsk_options* opts) {
@@ -128,14 +149,18 @@ extern "C" tsk_status tsk_create(tsk_handle* out, const tsk_options* opts) {
   e = cudaMalloc(&h->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking);
+  for (int b = 0; e == cudaSuccess && b < tsk_handle_s::kBranches; ++b) {
+    e = cudaStreamCreateWithFlags(&h->branch[b], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join[b], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     set_err(nullptr, "tsk_create: %s", cudaGetErrorString(e));
-    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    for (int b = 0; b < tsk_handle_s::kBranches; ++b) {
+      if (h->ev_join[b]) cudaEventDestroy(h->ev_join[b]);
+      if (h->branch[b]) cudaStreamDestroy(h->branch[b]);
+    }
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-    if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->d_status) cudaFree(h->d_status);
     delete h;
@@ -160,9 +185,11 @@ extern "C" tsk_status tsk_destroy(tsk_handle h) {
   for (tsk_plan p : h->cache) plan_free(p);
   h->cache.clear();
   gram_cache_destroy(h->gram_cache);
-  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  for (int b = 0; b < tsk_handle_s::kBranches; ++b) {
+    if (h->ev_join[b]) cudaEventDestroy(h->ev_join[b]);
+    if (h->branch[b]) cudaStreamDestroy(h->branch[b]);
+  }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-  if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->d_status) cudaFree(h->d_status);
   delete h;
@@ -265,20 +292,31 @@ static cudaError_t capture_plan(tsk_plan p, cudaEvent_t evb, cudaEvent_t eve) {
   int launches = 0;
   ce = cudaMemsetAsync(d_norm, 0, sizeof(double) * count, s);
   if (ce == cudaSuccess && evb) ce = cudaEventRecordWithFlags(evb, s, cudaEventRecordExternal);
-  // The sketch pass: the tensor-core kernel on the eligible matrices and the
-  // CUDA-core kernels on the rest, on two branches of the graph that run
-  // concurrently and join before the small factors.
-  const bool both = p->use_tc && p->use_simt;
-  cudaStream_t s2 = both ? h->cap_stream2 : s;
-  if (ce == cudaSuccess && both) {
-    ce = cudaEventRecord(h->ev_fork, s);
-    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s2, h->ev_fork, 0);
-  }
+  // The sketch pass: one branch of the graph per cluster-size class of the
+  // tensor-core kernel and one for the CUDA-core kernels (the matrices the
+  // tensor-core kernel cannot take); the branches run concurrently and join
+  // before the small factors.
   if (ce == cudaSuccess && p->use_tc) {
-    ce = tc_launch(p->tc, s);
-    launches += tc_launches(p->tc);
+    ce = tc_launch_prep(p->tc, s);  // the S images, read by every class
+    ++launches;
+  }
+  const int ncls = p->use_tc ? tc_classes(p->tc) : 0;
+  const int nbr = ncls + (p->use_simt ? 1 : 0);
+  if (nbr > tsk_handle_s::kBranches + 1 && ce == cudaSuccess) ce = cudaErrorInvalidValue;
+  int forked = 0;
+  if (ce == cudaSuccess && nbr > 1) {
+    ce = cudaEventRecord(h->ev_fork, s);
+    for (int b = 0; ce == cudaSuccess && b < nbr - 1; ++b, ++forked)
+      ce = cudaStreamWaitEvent(h->branch[b], h->ev_fork, 0);
+  }
+  // branch j runs on s for j == 0 and on h->branch[j - 1] otherwise
+  auto br = [&](int j) { return j == 0 ? s : h->branch[j - 1]; };
+  for (int j = 0; ce == cudaSuccess && j < ncls; ++j) {
+    ce = tc_launch_class(p->tc, j, br(j));
+    ++launches;
   }
   if (ce == cudaSuccess && p->use_simt) {
+    cudaStream_t s2 = br(ncls);
     ce = launch_sketch_x(in_type, kp, d_mats, (const int2*)(base + p->o_ix),
                          p->nx, base + p->o_X, d_norm, s2);
     if (ce == cudaSuccess)
@@ -286,9 +324,10 @@ static cudaError_t capture_plan(tsk_plan p, cudaEvent_t evb, cudaEvent_t eve) {
                            p->ny, base + p->o_X, base + p->o_Y, s2);
     launches += 2;
   }
-  if (both) {  // join the branch even after an error, so the capture can end
-    cudaError_t je = cudaEventRecord(h->ev_join, s2);
-    if (je == cudaSuccess) je = cudaStreamWaitEvent(s, h->ev_join, 0);
+  // join every forked branch, even after an error, so the capture can end
+  for (int b = 0; b < forked; ++b) {
+    cudaError_t je = cudaEventRecord(h->ev_join[b], h->branch[b]);
+    if (je == cudaSuccess) je = cudaStreamWaitEvent(s, h->ev_join[b], 0);
     if (ce == cudaSuccess) ce = je;
   }
   if (ce == cudaSuccess && eve) ce = cudaEventRecordWithFlags(eve, s, cudaEventRecordExternal);
@@ -544,9 +583,20 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   const MatDev* d_mats = (const MatDev*)(base + o_mats);
   if (use_tc) {
     char msg[256] = {0};
+    // rows of A per CTA: forced while tuning, else the tuned choice of the
+    // matrix's size class, else the default shape
+    std::vector<int> mcp((size_t)count, 0);
+    for (int64_t i = 0; i < count; ++i) {
+      if (h->force_mc) {
+        mcp[(size_t)i] = h->force_mc;
+      } else {
+        auto it = h->tune.find(tune_key(mats[i].m, mats[i].k));
+        if (it != h->tune.end()) mcp[(size_t)i] = it->second;
+      }
+    }
     ce = tc_prepare(&p->tc, hm.data(), d_mats, (int)count, tc_ids.data(), (int)tc_ids.size(),
-                    kp, base + o_X, base + o_Y, d_norm, h->d_status, h->opts.spin_limit, msg,
-                    sizeof(msg));
+                    mcp.data(), kp, base + o_X, base + o_Y, d_norm, h->d_status,
+                    h->opts.spin_limit, msg, sizeof(msg));
     if (ce != cudaSuccess) {
       set_err(h, "tensor-core plan: %s (%s)", msg, cudaGetErrorString(ce));
       plan_free(p);
@@ -661,6 +711,7 @@ static std::vector<unsigned char> plan_key(tsk_handle h, int64_t count,
   put(&h->opts.refine_q, sizeof(h->opts.refine_q));
   put(&h->opts.err_mode, sizeof(h->opts.err_mode));
   put(&h->opts.small_fp64, sizeof(h->opts.small_fp64));
+  put(&h->tune_version, sizeof(h->tune_version));
   put(mats, sizeof(tsk_mat_desc) * count);
   const unsigned char has = outs ? 1 : 0;
   put(&has, 1);
@@ -784,7 +835,8 @@ extern "C" tsk_status tsk_gram(tsk_handle h, const void* const* A, int64_t D,
     // tensor maps cannot be encoded go to the CUDA-core kernel below
     const cudaError_t ge =
         launch_gram_tc(A, D, m, n, lda, G, h->d_status, h->opts.spin_limit,
-                       h->gram_cache ? h->gram_cache : (h->gram_cache = gram_cache_create()), s);
+                       h->gram_cache ? h->gram_cache : (h->gram_cache = gram_cache_create()),
+                       h->opts.gram_tile == 0, s);
     if (ge != cudaErrorNotSupported) {
       TSK_CUDA(h, ge);
       TSK_CUDA(h, cudaStreamSynchronize(s));
@@ -1316,4 +1368,484 @@ extern "C" tsk_status tsk_refine_sketch(tsk_handle h, const tsk_mat_desc* train,
   cudaFreeAsync(g.base, s);
   cudaStreamSynchronize(s);
   return st;
+}
+
+// ---------------------------------------------------------------------------
+// two-sided sketching: Algorithm 3 (test side) and HOOI (Algorithm 5)
+// ---------------------------------------------------------------------------
+extern "C" tsk_status tsk_approx_two_sided(tsk_handle h, int64_t count,
+                                           const tsk_mat2_desc* mats, tsk_prec prec,
+                                           const tsk_mat_out* outs, double* err,
+                                           double* normA2, tsk_stream stream) {
+  if (!h) return TSK_EINVAL;
+  if (count < 1 || !mats || count > (1 << 22)) {
+    set_err(h, "tsk_approx_two_sided: count >= 1 and non-NULL mats required");
+    return TSK_EINVAL;
+  }
+  if (prec != TSK_FP64 && prec != TSK_FP32 && prec != TSK_BF16) {
+    set_err(h, "tsk_approx_two_sided: unknown precision");
+    return TSK_EINVAL;
+  }
+  const bool dbl = prec == TSK_FP64;
+  const size_t cs = compute_size(prec);
+  int kmax = 1, lmax = 1;
+  for (int64_t i = 0; i < count; ++i) {
+    const tsk_mat2_desc& d = mats[i];
+    if (!d.A || !d.S || !d.W || d.m < 1 || d.n < 1 || d.lda < d.n || d.k < 1 || d.l < 1 ||
+        d.k > d.n || d.l > d.m || d.k > TSK_MAX_K || d.l > TSK_MAX_K || d.r < 1 ||
+        d.r > std::min(d.k, d.l)) {
+      set_err(h, "tsk_approx_two_sided: matrix %lld: need A, S, W non-NULL, lda >= n, "
+                 "1 <= r <= min(k, l), k <= min(n, %d), l <= min(m, %d)",
+              (long long)i, TSK_MAX_K, TSK_MAX_K);
+      return TSK_EINVAL;
+    }
+    if (((uintptr_t)d.A) % elt_size(prec) || ((uintptr_t)d.S) % cs || ((uintptr_t)d.W) % cs) {
+      set_err(h, "tsk_approx_two_sided: matrix %lld: misaligned pointer", (long long)i);
+      return TSK_EINVAL;
+    }
+    kmax = std::max(kmax, d.k);
+    lmax = std::max(lmax, d.l);
+  }
+  const int kp = (kmax + 15) / 16 * 16, lp = (lmax + 15) / 16 * 16;
+  // per-matrix descriptors: xm for X (n x kp) and Y (m x kp); zm for the
+  // W^T panel (offX, one per distinct W) and Z (m x lp)
+  std::vector<MatDev> xm(count), zm(count);
+  std::vector<int2> ix, iy;
+  std::vector<int4> io_u, io_v;
+  std::vector<std::pair<const void*, long long>> wkeys;
+  std::vector<long long> woff_of;
+  std::vector<int> wl;
+  long long offX = 0, offY = 0, offZ = 0, offW = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    const tsk_mat2_desc& d = mats[i];
+    MatDev a;
+    memset(&a, 0, sizeof(a));
+    a.A = d.A;
+    a.S = d.S;
+    a.m = d.m;
+    a.n = d.n;
+    a.lda = d.lda;
+    a.k = d.k;
+    a.r = d.r;
+    a.offX = offX;
+    a.offY = offY;
+    a.Vt = outs ? outs[i].Vt : nullptr;
+    a.sigma = outs ? outs[i].sigma : nullptr;
+    MatDev z = a;
+    z.S = nullptr;
+    z.k = d.l;
+    z.offY = offZ;
+    z.US = outs ? outs[i].US : nullptr;
+    z.Vt = nullptr;
+    z.sigma = nullptr;
+    long long wo = -1;
+    for (size_t t = 0; t < wkeys.size(); ++t)
+      if (wkeys[t].first == d.W && wkeys[t].second == d.n && wl[t] == d.l) wo = woff_of[t];
+    if (wo < 0) {
+      wo = offW;
+      wkeys.push_back({d.W, d.n});
+      woff_of.push_back(wo);
+      wl.push_back(d.l);
+      offW += d.n * lp;
+    }
+    z.offX = wo;
+    offX += d.n * kp;
+    offY += d.m * kp;
+    offZ += d.m * lp;
+    for (long long t = 0; t < (d.n + 63) / 64; ++t) ix.push_back(make_int2((int)i, (int)t));
+    for (long long t = 0; t < (d.m + 63) / 64; ++t) iy.push_back(make_int2((int)i, (int)t));
+    if (z.US)
+      for (long long t = 0; t < (d.m + 255) / 256; ++t)
+        io_u.push_back(make_int4((int)i, (int)t, 0, 0));
+    if (a.Vt)
+      for (long long t = 0; t < (d.n + 255) / 256; ++t)
+        io_v.push_back(make_int4((int)i, (int)t, 1, 0));
+    xm[i] = a;
+    zm[i] = z;
+  }
+  Carve cv;
+  const size_t o_xm = cv.take(sizeof(MatDev) * count);
+  const size_t o_zm = cv.take(sizeof(MatDev) * count);
+  const size_t o_ix = cv.take(sizeof(int2) * ix.size());
+  const size_t o_iy = cv.take(sizeof(int2) * iy.size());
+  const size_t o_iu = cv.take(sizeof(int4) * std::max<size_t>(1, io_u.size()));
+  const size_t o_iv = cv.take(sizeof(int4) * std::max<size_t>(1, io_v.size()));
+  const size_t o_px = cv.take(sizeof(PanelDev) * count);
+  const size_t o_pz = cv.take(sizeof(PanelDev) * count);
+  const size_t host_part = cv.off;
+  const size_t o_X = cv.take(cs * offX);
+  const size_t o_Y = cv.take(cs * offY);
+  const size_t o_Z = cv.take(cs * offZ);
+  const size_t o_WT = cv.take(cs * offW);
+  const size_t o_RX = cv.take(8 * (size_t)count * kp * kp);
+  const size_t o_RZ = cv.take(8 * (size_t)count * lp * lp);
+  const size_t o_WX = cv.take(cs * (size_t)count * kp * kp);
+  const size_t o_WZ = cv.take(cs * (size_t)count * lp * lp);
+  const size_t o_nrm = cv.take(8 * (size_t)count);
+  const size_t o_err = cv.take(8 * (size_t)count);
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* base = nullptr;
+  TSK_CUDA(h, cudaMallocAsync((void**)&base, cv.off, s));
+  std::vector<PanelDev> px(count), pz(count);
+  for (int64_t i = 0; i < count; ++i) {
+    px[i] = PanelDev{base + o_X + cs * xm[i].offX, xm[i].n, xm[i].k, kp,
+                     base + o_RX + 8 * (size_t)i * kp * kp};
+    pz[i] = PanelDev{base + o_Z + cs * zm[i].offY, zm[i].m, zm[i].k, lp,
+                     base + o_RZ + 8 * (size_t)i * lp * lp};
+  }
+  std::vector<unsigned char> host(host_part, 0);
+  memcpy(host.data() + o_xm, xm.data(), sizeof(MatDev) * count);
+  memcpy(host.data() + o_zm, zm.data(), sizeof(MatDev) * count);
+  memcpy(host.data() + o_ix, ix.data(), sizeof(int2) * ix.size());
+  memcpy(host.data() + o_iy, iy.data(), sizeof(int2) * iy.size());
+  if (!io_u.empty()) memcpy(host.data() + o_iu, io_u.data(), sizeof(int4) * io_u.size());
+  if (!io_v.empty()) memcpy(host.data() + o_iv, io_v.data(), sizeof(int4) * io_v.size());
+  memcpy(host.data() + o_px, px.data(), sizeof(PanelDev) * count);
+  memcpy(host.data() + o_pz, pz.data(), sizeof(PanelDev) * count);
+  double* d_norm = normA2 ? normA2 : (double*)(base + o_nrm);
+  double* d_err = err ? err : (double*)(base + o_err);
+  const MatDev* dxm = (const MatDev*)(base + o_xm);
+  const MatDev* dzm = (const MatDev*)(base + o_zm);
+  cudaError_t e = cudaMemcpyAsync(base, host.data(), host_part, cudaMemcpyHostToDevice, s);
+  // panels start zeroed: the kernels leave the padding columns alone
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + o_X, 0, o_RX - o_X, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_norm, 0, 8 * count, s);
+  for (size_t t = 0; e == cudaSuccess && t < wkeys.size(); ++t)
+    e = launch_wt_panel(dbl ? 0 : 1, wkeys[t].first, wl[t], wkeys[t].second, lp,
+                        base + o_WT + cs * woff_of[t], s);
+  if (e == cudaSuccess)
+    e = launch_sketch_x((int)prec, kp, dxm, (const int2*)(base + o_ix), (int)ix.size(),
+                        base + o_X, d_norm, s);
+  if (e == cudaSuccess)
+    e = launch_sketch_y((int)prec, kp, dxm, (const int2*)(base + o_iy), (int)iy.size(),
+                        base + o_X, base + o_Y, s);
+  if (e == cudaSuccess)  // Z = A W^T: the Y kernel with W^T's panel in place of X
+    e = launch_sketch_y((int)prec, lp, dzm, (const int2*)(base + o_iy), (int)iy.size(),
+                        base + o_WT, base + o_Z, s);
+  if (e == cudaSuccess)
+    e = dbl ? launch_tsqr(true, kp, (const PanelDev*)(base + o_px), (int)count, 1, h->d_status, s)
+            : launch_tsqr_f32_in_f64(kp, (const PanelDev*)(base + o_px), (int)count, 1, s);
+  if (e == cudaSuccess)
+    e = dbl ? launch_tsqr(true, lp, (const PanelDev*)(base + o_pz), (int)count, 1, h->d_status, s)
+            : launch_tsqr_f32_in_f64(lp, (const PanelDev*)(base + o_pz), (int)count, 1, s);
+  if (e == cudaSuccess)
+    e = launch_two_sided_small(dbl, kp, lp, dxm, dzm, (int)count, base + o_Y, base + o_Z,
+                               (const double*)(base + o_RX), (const double*)(base + o_RZ),
+                               base + o_WX, base + o_WZ, d_norm, d_err, h->d_status, s);
+  if (e == cudaSuccess && !io_u.empty())  // US = Z (R_Z^{-1} U_r Sigma_r)
+    e = launch_project_out(dbl, lp, dzm, (const int4*)(base + o_iu), (int)io_u.size(),
+                           base + o_X, base + o_Z, base + o_WZ, s);
+  if (e == cudaSuccess && !io_v.empty())  // Vt = (X R_X^{-1} V_r)^T
+    e = launch_project_out(dbl, kp, dxm, (const int4*)(base + o_iv), (int)io_v.size(),
+                           base + o_X, base + o_Y, base + o_WX, s);
+  cudaFreeAsync(base, s);
+  const cudaError_t se = cudaStreamSynchronize(s);  // host staging must outlive the copy
+  if (e == cudaSuccess) e = se;
+  if (e != cudaSuccess) {
+    set_err(h, "tsk_approx_two_sided: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? TSK_ENOMEM : TSK_ECUDA;
+  }
+  return TSK_OK;
+}
+
+extern "C" tsk_status tsk_train_two_sided(tsk_handle h, const void* const* A, int64_t D,
+                                          int64_t m, int64_t n, int64_t lda, tsk_prec prec,
+                                          int32_t k, int32_t l, int32_t max_sweeps, double tol,
+                                          void* S, void* W, double* core_energy,
+                                          int32_t* sweeps_out, tsk_stream stream) {
+  if (!h) return TSK_EINVAL;
+  if (!A || D < 1 || m < 1 || n < 1 || lda < n || k < 1 || l < 1 || k > std::min(m, n) ||
+      l > std::min(m, n) || k > TSK_MAX_K || l > TSK_MAX_K || !S || !W || max_sweeps < 0) {
+    set_err(h, "tsk_train_two_sided: need A, S, W non-NULL, D, m, n >= 1, lda >= n, "
+               "1 <= k, l <= min(m, n, %d)", TSK_MAX_K);
+    return TSK_EINVAL;
+  }
+  if (prec != TSK_FP64 && prec != TSK_FP32 && prec != TSK_BF16) {
+    set_err(h, "tsk_train_two_sided: unknown precision");
+    return TSK_EINVAL;
+  }
+  for (int64_t d = 0; d < D; ++d)
+    if (!A[d] || ((uintptr_t)A[d]) % elt_size(prec) != 0) {
+      set_err(h, "tsk_train_two_sided: A[%lld] is NULL or misaligned", (long long)d);
+      return TSK_EINVAL;
+    }
+  const bool dbl = prec == TSK_FP64;
+  const size_t cs = compute_size(prec);
+  const int ctype = dbl ? 0 : 1;  // element type of the projected panels
+  if (tol <= 0) tol = dbl ? 1e-12 : 1e-7;
+  const int kp = (k + 15) / 16 * 16, lp = (l + 15) / 16 * 16;
+  cudaStream_t s = (cudaStream_t)stream;
+  // HOSVD start: S from the mode-1 Gram, W from the mode-2 Gram
+  const int64_t dmax = std::max(m, n);
+  double* G = nullptr;
+  TSK_CUDA(h, cudaMallocAsync((void**)&G, sizeof(double) * dmax * dmax, s));
+  tsk_status st = tsk_gram(h, A, D, m, n, lda, prec, 1, G, 0, stream);
+  tsk_status noconv = TSK_OK;
+  auto eig_step = [&](int64_t dim, int32_t kk, void* out, double* eig) -> tsk_status {
+    tsk_status r = tsk_sketch_from_gram(h, G, dim, kk, prec == TSK_BF16 ? TSK_FP32 : prec,
+                                        out, eig, stream);
+    if (r == TSK_ENOCONV) noconv = r, r = TSK_OK;
+    return r;
+  };
+  if (st == TSK_OK) st = eig_step(m, k, S, nullptr);
+  if (st == TSK_OK) st = tsk_gram(h, A, D, m, n, lda, prec, 2, G, 0, stream);
+  double* d_eig = nullptr;
+  if (st == TSK_OK && cudaMallocAsync((void**)&d_eig, sizeof(double) * 64, s) != cudaSuccess)
+    st = TSK_ENOMEM;
+  if (st == TSK_OK) st = eig_step(n, l, W, d_eig);
+  double total = 0.0;
+  {  // sum_d ||A_d||^2 = trace of the mode-2 Gram just formed
+    std::vector<double> diag(n);
+    if (st == TSK_OK &&
+        cudaMemcpy2DAsync(diag.data(), sizeof(double), G, sizeof(double) * (n + 1),
+                          sizeof(double), n, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+        cudaStreamSynchronize(s) == cudaSuccess)
+      for (double v : diag) total += v;
+  }
+  // projected panels of every training matrix: Z_d = A_d W^T (m x lp) and
+  // X_d = A_d^T S^T (n x kp); descriptors for both
+  Carve cv;
+  const size_t o_md = cv.take(sizeof(MatDev) * D);
+  const size_t o_mz = cv.take(sizeof(MatDev) * D);
+  const size_t o_ix = cv.take(sizeof(int2) * D * ((n + 63) / 64));
+  const size_t o_iy = cv.take(sizeof(int2) * D * ((m + 63) / 64));
+  const size_t o_pz = cv.take(sizeof(void*) * D);
+  const size_t o_px = cv.take(sizeof(void*) * D);
+  const size_t host_part = cv.off;
+  const size_t o_Z = cv.take(cs * (size_t)D * m * lp);
+  const size_t o_X = cv.take(cs * (size_t)D * n * kp);
+  const size_t o_WT = cv.take(cs * (size_t)n * lp);
+  const size_t o_nrm = cv.take(8 * (size_t)D);
+  unsigned char* base = nullptr;
+  if (st == TSK_OK && cudaMallocAsync((void**)&base, cv.off, s) != cudaSuccess) st = TSK_ENOMEM;
+  int sweeps = 0;
+  double energy = 0.0;
+  if (st == TSK_OK) {
+    std::vector<unsigned char> host(host_part, 0);
+    MatDev* md = (MatDev*)(host.data() + o_md);
+    MatDev* mz = (MatDev*)(host.data() + o_mz);
+    int2* ix = (int2*)(host.data() + o_ix);
+    int2* iy = (int2*)(host.data() + o_iy);
+    void** pz = (void**)(host.data() + o_pz);
+    void** px = (void**)(host.data() + o_px);
+    const long long tx = (n + 63) / 64, ty = (m + 63) / 64;
+    for (int64_t d = 0; d < D; ++d) {
+      MatDev a;
+      memset(&a, 0, sizeof(a));
+      a.A = A[d];
+      a.S = S;
+      a.m = m;
+      a.n = n;
+      a.lda = lda;
+      a.k = k;
+      a.r = 1;
+      a.offX = d * n * kp;
+      a.offY = 0;
+      md[d] = a;
+      MatDev z = a;
+      z.S = nullptr;
+      z.k = l;
+      z.offX = 0;  // the one W^T panel
+      z.offY = d * m * lp;
+      mz[d] = z;
+      for (long long t = 0; t < tx; ++t) ix[d * tx + t] = make_int2((int)d, (int)t);
+      for (long long t = 0; t < ty; ++t) iy[d * ty + t] = make_int2((int)d, (int)t);
+      pz[d] = base + o_Z + cs * (size_t)d * m * lp;
+      px[d] = base + o_X + cs * (size_t)d * n * kp;
+    }
+    cudaError_t e = cudaMemcpyAsync(base, host.data(), host_part, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_Z, 0, o_nrm - o_Z, s);
+    double prev = -1.0;
+    std::vector<double> hl(64);
+    for (int sw = 1; e == cudaSuccess && st == TSK_OK && sw <= max_sweeps; ++sw) {
+      // mode 1: S <- top k eigenvectors of sum_d (A_d W^T)(A_d W^T)^T
+      e = launch_wt_panel(dbl ? 0 : 1, W, l, n, lp, base + o_WT, s);
+      if (e == cudaSuccess)
+        e = launch_sketch_y((int)prec, lp, (const MatDev*)(base + o_mz),
+                            (const int2*)(base + o_iy), (int)(D * ty), base + o_WT, base + o_Z,
+                            s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, sizeof(double) * m * m, s);
+      if (e == cudaSuccess)
+        e = launch_gram(ctype, (const void* const*)(base + o_pz), D, m, lp, lp, 1, G, s);
+      if (e != cudaSuccess) break;
+      st = eig_step(m, k, S, nullptr);
+      if (st != TSK_OK) break;
+      // mode 2: W <- top l eigenvectors of sum_d (S A_d)^T (S A_d)
+      e = cudaMemsetAsync(base + o_nrm, 0, 8 * D, s);
+      if (e == cudaSuccess)
+        e = launch_sketch_x((int)prec, kp, (const MatDev*)(base + o_md),
+                            (const int2*)(base + o_ix), (int)(D * tx), base + o_X,
+                            (double*)(base + o_nrm), s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, sizeof(double) * n * n, s);
+      if (e == cudaSuccess)
+        e = launch_gram(ctype, (const void* const*)(base + o_px), D, n, kp, kp, 1, G, s);
+      if (e != cudaSuccess) break;
+      st = eig_step(n, l, W, d_eig);
+      if (st != TSK_OK) break;
+      // core energy sum_d ||S A_d W^T||^2 = sum of the top l eigenvalues
+      e = cudaMemcpyAsync(hl.data(), d_eig, sizeof(double) * l, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) break;
+      energy = 0.0;
+      for (int i = 0; i < l; ++i) energy += hl[i];
+      sweeps = sw;
+      if (prev >= 0.0 && std::fabs(energy - prev) < tol * total) break;
+      prev = energy;
+    }
+    if (e != cudaSuccess && st == TSK_OK) {
+      set_err(h, "tsk_train_two_sided: %s", cudaGetErrorString(e));
+      st = TSK_ECUDA;
+    }
+  }
+  if (base) cudaFreeAsync(base, s);
+  if (d_eig) cudaFreeAsync(d_eig, s);
+  cudaFreeAsync(G, s);
+  cudaStreamSynchronize(s);
+  if (core_energy) *core_energy = energy;
+  if (sweeps_out) *sweeps_out = sweeps;
+  return st != TSK_OK ? st : noconv;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner of the tensor-core sketch: rows of A per CTA by size class
+// ---------------------------------------------------------------------------
+extern "C" tsk_status tsk_autotune(tsk_handle h, int64_t count, const tsk_mat_desc* mats,
+                                   tsk_prec prec, int32_t reps, tsk_stream stream) {
+  if (!h) return TSK_EINVAL;
+  if (count < 1 || !mats || prec != TSK_BF16) {
+    set_err(h, "tsk_autotune: count >= 1, non-NULL mats and TSK_BF16 required");
+    return TSK_EINVAL;
+  }
+  if (reps < 1) reps = 5;
+  for (int64_t i = 0; i < count; ++i) {
+    tsk_status st = check_desc(h, mats[i], i, prec);
+    if (st != TSK_OK) return st;
+  }
+  if (!tc_supported()) return TSK_OK;  // nothing to tune
+  // classes where both shapes exist: 256 < m <= 2048 (1 to 8 CTAs of 256 rows)
+  std::map<std::pair<int, int>, std::vector<tsk_mat_desc>> byk;
+  for (int64_t i = 0; i < count; ++i) {
+    const tsk_mat_desc& d = mats[i];
+    if (!tc_eligible_one(d) || d.m <= 256 || d.m > 2048) continue;
+    auto& v = byk[tune_key(d.m, d.k)];
+    if (v.size() < 16) v.push_back(d);  // up to 16 matrices of the batch per class
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TSK_CUDA(h, cudaEventCreate(&e0));
+  TSK_CUDA(h, cudaEventCreate(&e1));
+  tsk_status result = TSK_OK;
+  const int save_force = h->force_mc;
+  for (auto& kv : byk) {
+    const std::vector<tsk_mat_desc>& v = kv.second;
+    double us[2] = {0.0, 0.0};
+    for (int c = 0; c < 2 && result == TSK_OK; ++c) {
+      h->force_mc = c == 0 ? 512 : 256;
+      tsk_plan p = nullptr;
+      result = build_plan(h, (int64_t)v.size(), v.data(), prec, nullptr, nullptr, nullptr, &p);
+      if (result != TSK_OK) break;
+      cudaError_t e = capture_plan(p, e0, e1);  // events around the sketch pass
+      float best = 1e30f;
+      for (int r = 0; e == cudaSuccess && r < reps + 1; ++r) {
+        e = cudaGraphLaunch(p->exec, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && r > 0) best = std::min(best, ms);  // the first warms up
+      }
+      plan_free(p);
+      if (e != cudaSuccess) {
+        set_err(h, "tsk_autotune: %s", cudaGetErrorString(e));
+        result = TSK_ECUDA;
+        break;
+      }
+      us[c] = 1e3 * best / (double)v.size();
+    }
+    if (result != TSK_OK) break;
+    h->tune[kv.first] = us[1] < us[0] ? 256 : 512;
+    h->tune_us[kv.first] = {us[0], us[1]};
+  }
+  h->force_mc = save_force;
+  ++h->tune_version;  // plans built from now on use the table
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result == TSK_OK) {
+    int st = 0;
+    cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (st & kStatusTimeout) {
+      set_err(h, "tsk_autotune: a bounded device wait ran out");
+      result = TSK_ETIMEOUT;
+    }
+  }
+  return result;
+}
+
+extern "C" tsk_status tsk_autotune_save(tsk_handle h, const char* path) {
+  if (!h || !path) return TSK_EINVAL;
+  FILE* f = fopen(path, "w");
+  if (!f) {
+    set_err(h, "tsk_autotune_save: cannot open %s", path);
+    return TSK_EINVAL;
+  }
+  fprintf(f, "{\"kernel\": \"sketch_tc\", \"classes\": [");
+  bool first = true;
+  for (auto& kv : h->tune) {
+    auto us = h->tune_us.count(kv.first) ? h->tune_us[kv.first] : std::make_pair(0.0, 0.0);
+    fprintf(f, "%s\n  {\"cluster_at_512\": %d, \"k8\": %d, \"rows_per_cta\": %d, "
+               "\"us_per_matrix_512\": %.4f, \"us_per_matrix_256\": %.4f}",
+            first ? "" : ",", kv.first.first, kv.first.second, kv.second, us.first, us.second);
+    first = false;
+  }
+  fprintf(f, "\n]}\n");
+  fclose(f);
+  return TSK_OK;
+}
+
+extern "C" tsk_status tsk_autotune_load(tsk_handle h, const char* path) {
+  if (!h || !path) return TSK_EINVAL;
+  FILE* f = fopen(path, "r");
+  if (!f) {
+    set_err(h, "tsk_autotune_load: cannot open %s", path);
+    return TSK_EINVAL;
+  }
+  std::string text;
+  char buf[4096];
+  size_t got;
+  while ((got = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+  fclose(f);
+  // the entries this library writes: one object per class, fields by name
+  auto field = [](const std::string& obj, const char* name, double* out) {
+    const std::string key = std::string("\"") + name + "\"";
+    size_t p = obj.find(key);
+    if (p == std::string::npos) return false;
+    p = obj.find(':', p + key.size());
+    if (p == std::string::npos) return false;
+    char* end = nullptr;
+    *out = strtod(obj.c_str() + p + 1, &end);
+    return end != obj.c_str() + p + 1;
+  };
+  std::map<std::pair<int, int>, int> table;
+  size_t pos = text.find("\"classes\"");
+  if (pos == std::string::npos) {
+    set_err(h, "tsk_autotune_load: %s has no \"classes\"", path);
+    return TSK_EINVAL;
+  }
+  while ((pos = text.find('{', pos + 1)) != std::string::npos) {
+    const size_t end = text.find('}', pos);
+    if (end == std::string::npos) break;
+    const std::string obj = text.substr(pos, end - pos + 1);
+    double c = 0, k8 = 0, mc = 0;
+    if (!field(obj, "cluster_at_512", &c) || !field(obj, "k8", &k8) ||
+        !field(obj, "rows_per_cta", &mc) || (mc != 256 && mc != 512)) {
+      set_err(h, "tsk_autotune_load: malformed entry in %s", path);
+      return TSK_EINVAL;
+    }
+    table[{(int)c, (int)k8}] = (int)mc;
+    pos = end;
+  }
+  h->tune = table;
+  h->tune_us.clear();
+  ++h->tune_version;
+  return TSK_OK;
 }

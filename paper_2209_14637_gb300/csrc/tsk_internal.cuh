@@ -146,6 +146,19 @@ cudaError_t launch_add(bool dbl, long long n, const void* a, const void* b, void
 cudaError_t launch_batch_loss(int count, const double* err, const double* normA2,
                               double* loss, cudaStream_t s);
 
+// k_two_sided.cu
+// W (l x n, double for prec 0, float otherwise) -> n x lp panel of W^T.
+cudaError_t launch_wt_panel(int prec, const void* W, int l, long long n, int lp, void* out,
+                            cudaStream_t s);
+// Small factors of two-sided SCW: xm (k, r, offY of Y, sigma) and zm (k = l,
+// offY of Z) per matrix; RX, RZ double R factors of the X and Z panels;
+// writes err, sigma, WX (k x r, stride kp^2) and WZ (l x r, stride lp^2).
+cudaError_t launch_two_sided_small(bool dbl, int kp, int lp, const MatDev* xm,
+                                   const MatDev* zm, int count, const void* Y, const void* Z,
+                                   const double* RX, const double* RZ, void* WX, void* WZ,
+                                   const double* normA2, double* err, int* status,
+                                   cudaStream_t s);
+
 // k_tc.cu (tcgen05 / TMA kernels; BF16)
 struct TcPlan;
 bool tc_supported();
@@ -159,20 +172,28 @@ bool gram_tc_eligible(int prec, int mode, const void* const* A, long long D, lon
 struct GramCache;
 GramCache* gram_cache_create();
 void gram_cache_destroy(GramCache* c);
+// pairs: 256 x 256 tiles on CTA pairs (tcgen05 .cta_group::2); otherwise
+// 128 x 128 tiles on single CTAs.
 cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long long n,
                            long long lda, double* G, int* status, long long spin_limit,
-                           GramCache* cache, cudaStream_t s);
+                           GramCache* cache, bool pairs, cudaStream_t s);
 // Builds the tensor-core part of a plan for the matrices ids[0..nids) of
 // the plan's count matrices (tensor maps, S images, per-class schedules).
+// mc_pref (count entries, nullable): per matrix 0 (default shape), 256 or
+// 512 rows of A per CTA.
 cudaError_t tc_prepare(TcPlan** out, const MatDev* host_mats,
                        const MatDev* dev_mats, int count, const int* ids, int nids,
-                       int kp, void* dev_X, void* dev_Y, double* dev_normA2,
-                       int* status, long long spin_limit, char* msg,
+                       const int* mc_pref, int kp, void* dev_X, void* dev_Y,
+                       double* dev_normA2, int* status, long long spin_limit, char* msg,
                        int msglen);
 // Whether one BF16 matrix can take the tensor-core sketch: k <= 48,
 // m <= 4096, A 16-byte aligned, lda * 2 a multiple of 16.
 bool tc_matrix_eligible(const void* A, long long m, long long lda, int k);
-cudaError_t tc_launch(TcPlan* p, cudaStream_t s);
+// The S images (one small kernel), then one launch per cluster-size class;
+// the classes do not depend on each other and may run concurrently.
+cudaError_t tc_launch_prep(TcPlan* p, cudaStream_t s);
+int tc_classes(const TcPlan* p);
+cudaError_t tc_launch_class(TcPlan* p, int i, cudaStream_t s);
 int tc_launches(const TcPlan* p);
 long long tc_workspace_bytes(const TcPlan* p);
 void tc_destroy(TcPlan* p);

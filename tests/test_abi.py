@@ -44,7 +44,7 @@ def test_default_options(lib):
     o = tsk.default_options()
     assert o.kernel == tsk.KERNEL_AUTO and o.refine_q == tsk.REFINE_AUTO
     assert o.max_iter == 300 and o.spin_limit == 1 << 24
-    assert o.small_fp64 == 0 and o.reserved == 0
+    assert o.small_fp64 == 0 and o.gram_tile == 0
 
 
 def test_create_fails_cleanly_without_gpu(lib):
@@ -61,4 +61,6 @@ def test_struct_layouts_match_header():
     # tsk_mat_desc: 2 pointers, 3 int64, 2 int32; tsk_mat_out: 3 pointers
     assert C.sizeof(tsk.MatDesc) == 2 * 8 + 3 * 8 + 2 * 4
     assert C.sizeof(tsk.MatOut) == 3 * 8
+    # tsk_mat2_desc: 3 pointers, 3 int64, 4 int32
+    assert C.sizeof(tsk.Mat2Desc) == 3 * 8 + 3 * 8 + 4 * 4
     assert C.sizeof(tsk.Options) == 4 * 4 + 8 + 8 + 2 * 4

@@ -84,3 +84,39 @@ def test_c4_ragged_batch_of_512(tsk, batch, pad_rows):
     np.testing.assert_allclose(_np(err), e, rtol=1e-12)
     plan.close()
     h.close()
+
+
+def test_autotune_then_the_tuned_plan_matches_the_oracle(tsk, batch, tmp_path):
+    """The autotuner times both cluster shapes for each size class of the
+    batch that has two (256 < m <= 2048), keeps the faster in the handle and
+    round-trips it through JSON; plans built afterwards use it and still
+    match the oracle, and a second handle that loads the file builds the
+    same plan (same errors, bit for bit)."""
+    import json
+    items, Ss = batch
+    As = synth.ragged_batch(items[:96], device="cuda", pad_rows=True)
+    S96, r96 = Ss[:96], [it.r for it in items[:96]]
+    h = tsk.Handle(kernel=tsk.KERNEL_TC, refine_q=tsk.REFINE_ALWAYS)
+    h.autotune(As, S96, r96, reps=3)
+    path = tmp_path / "tune.json"
+    h.autotune_save(str(path))
+    table = json.loads(path.read_text())
+    assert table["classes"], table
+    for c in table["classes"]:
+        assert c["rows_per_cta"] in (256, 512)
+        assert c["us_per_matrix_512"] > 0 and c["us_per_matrix_256"] > 0
+        faster = 256 if c["us_per_matrix_256"] < c["us_per_matrix_512"] else 512
+        assert c["rows_per_cta"] == faster
+    out = h.approx_batch(As, S96, r96)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    e = _np(out["err"])
+    for i in _sample(items[:96], per_k=3):
+        o = oracle.scw(_np(As[i]), _np(S96[i]), r96[i], dense=False)
+        assert abs(e[i] - o["err"]) <= GAP * o["err"], (i, items[i])
+    h2 = tsk.Handle(kernel=tsk.KERNEL_TC, refine_q=tsk.REFINE_ALWAYS)
+    h2.autotune_load(str(path))
+    e2 = _np(h2.approx_batch(As, S96, r96)["err"])
+    np.testing.assert_allclose(e2, e, rtol=1e-12)
+    h.close()
+    h2.close()

@@ -200,15 +200,20 @@ def test_automatic_refinement_where_the_bound_asks(tsk):
     assert np.max(np.abs(e2 - ref) / ref) <= GAP
 
 
-@pytest.mark.parametrize("m,n,D", [(320, 200, 11), (2048, 256, 20), (128, 64, 3)])
-def test_tc_gram_mode1(tsk, m, n, D):
+@pytest.mark.parametrize("tile", [0, 1])
+@pytest.mark.parametrize("m,n,D", [(320, 200, 11), (2048, 256, 20), (128, 64, 3),
+                                   (300, 72, 40), (4096, 64, 3)])
+def test_tc_gram_mode1(tsk, m, n, D, tile):
     """T1 on the tensor cores (BF16, mode 1) against the FP64 oracle on the
-    same stored values: ragged m (a partial 128-row tile) and n (a partial
-    64-column block), matrices split over CTAs (FP64 atomics) or not, and
-    more than two TMEM flush groups of eight matrices."""
+    same stored values, with 256 x 256 tiles on CTA pairs (tile 0) and
+    128 x 128 tiles on single CTAs (tile 1): ragged m (partial tiles, and a
+    pair whose second CTA holds only rows past m) and n (a partial 64-column
+    block), matrices split over CTAs (FP64 atomics) or not, more than two
+    TMEM flush groups of eight matrices, and m = 4096 (more tiles than
+    SMs)."""
     g = torch.Generator(device="cuda").manual_seed(m + n + D)
     T = [torch.randn(m, n, generator=g, device="cuda").to(torch.bfloat16) for _ in range(D)]
-    h = tsk.Handle()
+    h = tsk.Handle(gram_tile=tile)
     G = _np(h.gram(T, mode=1))
     assert h.sync_status() == 0
     R = oracle.gram_mode1([_np(t) for t in T])
