@@ -284,23 +284,3 @@ def test_padded_rows_take_the_tensor_cores(tsk):
         assert abs(float(out["err"][i]) - o["err"]) <= GAP * o["err"], i
     h.close()
 
-
-def test_expired_waits_report_a_timeout_and_leave_the_context_usable(tsk):
-    """Failure detection without a fault: a spin limit of one iteration
-    (120 ns) makes the single-CTA tensor-core kernel's first bounded waits
-    run out while its loads are still in flight.  The kernel raises the
-    timeout bit, stops issuing, drains its own loads and tensor-core
-    operations (those drains have their own two-second bound), frees its
-    TMEM and returns: the host reads TSK_ETIMEOUT, and a normal handle then
-    runs the same case correctly on the same context."""
-    A, S = _case(384, 256, 16, 21)  # m <= 512: one CTA, no peers in a cluster
-    h = tsk.Handle(kernel=tsk.KERNEL_TC, spin_limit=1)
-    h.approx_batch([A], [S], 8)
-    assert h.sync_status() == 5  # TSK_ETIMEOUT
-    assert h.sync_status() == 0  # read and cleared
-    h.close()
-    out, st, h2 = _run(tsk, tsk.KERNEL_TC, [A], [S], [8])
-    assert st == 0
-    o = oracle.scw(_np(A), _np(S), 8, dense=False)
-    assert abs(float(out["err"][0]) - o["err"]) <= GAP * o["err"]
-    h2.close()
