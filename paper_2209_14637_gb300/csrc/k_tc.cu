@@ -720,7 +720,10 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_XTEMPTY + h));
         // The owner expects R rows of 256 bytes from each of the C CTAs.
-        if (xt == 63) mbar_expect_tx(bar(B_RFULL + h), (uint32_t)(C * R * 256));
+        // After a timeout no bytes are sent, so the phase of RFULL can never
+        // complete: a further arrive on it would take its pending count below
+        // zero (undefined), so nothing arrives on it any more.
+        if (xt == 63 && !ctl->abort) mbar_expect_tx(bar(B_RFULL + h), (uint32_t)(C * R * 256));
         // (b) Reduce.  X rows [rank*R, rank*R + R) of this block = sum of the
         // C slots, eight columns per work item.  Two-term BF16 split X =
         // X_hi + X_lo (X_hi = BF16(X), X_lo = BF16(X - X_hi)); MMA-Y
@@ -782,9 +785,13 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
         }
         // (c) Hand the owned rows of X~ to the signalling warp, which copies
         // them to the peers.  The proxy fence makes these generic writes
-        // visible to the bulk copies and to the tensor cores.
+        // visible to the bulk copies and to the tensor cores.  After a
+        // timeout nothing is handed on: the signalling warp would otherwise
+        // arm XBFULL again while its previous phase, waiting for bytes no
+        // peer will send, is still open (an arrive below zero).  Every
+        // waiter on XREADY is bounded and sees the abort flag.
         fence_proxy_async_cta();
-        mbar_arrive(bar(B_XREADY + h));
+        if (got) mbar_arrive(bar(B_XREADY + h));
       }
       if (!xwarp) {
         tot = warp_sum(tot);
