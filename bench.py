@@ -315,6 +315,17 @@ def run_tsk(args):
     stage(f"trained in {train_s:.2f} s (status {st}); generating the test stream")
     te = synth.stream(spec, "test", device="cuda", start=rank * count, count=count)
     err = torch.empty(count, dtype=torch.float64, device="cuda")
+    tune = None
+    if not args.no_tune and te.dtype == torch.bfloat16 and args.kernel != tsk.KERNEL_SIMT:
+        # the project's autotuner picks the sketch kernel's rows per CTA for
+        # this workload's size class (untimed, before the plan is built)
+        import tempfile
+        h.autotune(te, S, spec.r)
+        with tempfile.TemporaryDirectory() as td:
+            h.autotune_save(os.path.join(td, "t.json"))
+            with open(os.path.join(td, "t.json")) as f:
+                tune = json.load(f)["classes"]
+        stage(f"autotune: {tune}")
     plan = h.plan(te, S, spec.r, err)
     info = plan.info()
     plan_kind = "tcgen05" if te.dtype == torch.bfloat16 and args.kernel != tsk.KERNEL_SIMT else "simt"
@@ -520,7 +531,8 @@ def run_tsk(args):
                        "matrices_per_step_per_gpu": count,
                        "l2": f"inputs ({alg_bytes / 1e9:.2f} GB per step) larger than "
                              "L2 (129 MB); no flush",
-                       "sketch_kernel": plan_kind},
+                       "sketch_kernel": plan_kind,
+                       "autotune": tune},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": f"hbm_gbs of {peak_src}",
@@ -698,6 +710,8 @@ def run_extra_workloads(args, tsk, h, sgemm, peaks, ws, dist, rank):
         A4 = synth.ragged_batch(items, device="cuda", pad_rows=pad)
         alg4 = float(sum(it.m * it.n * 2 for it in items))
         h4 = tsk.Handle(refine_q=tsk.REFINE_ALWAYS)
+        if not args.no_tune:
+            h4.autotune(A4, S4, r4)
         e4 = torch.empty(len(items), dtype=torch.float64, device="cuda")
         p4 = h4.plan(A4, S4, r4, e4)
         inf4 = p4.info()
@@ -773,6 +787,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the refine_auto and small_fp64 timings")
     ap.add_argument("--c5-steps", type=int, default=2000)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="build the plans without running the sketch-shape autotuner")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the C2, C4 and C5 workloads")
     ap.add_argument("--refine", default="always", choices=["always", "auto", "never"],

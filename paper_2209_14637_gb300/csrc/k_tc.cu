@@ -70,11 +70,18 @@ constexpr int BAR_BYTES = 256;
 // kernel checks this and reports misalignment instead of reserving slack.
 template <int MC>
 struct Lay {
-  static constexpr int NST = MC == 256 ? 4 : 2;
+  // stages of A in flight: four of 32 KB (256 rows), three of 48 KB (384
+  // rows) or two of 64 KB (512 rows)
+  static constexpr int NST = MC == 256 ? 4 : (MC == 384 ? 3 : 2);
+  // TMA box height: 384 rows load as three boxes of 128
+  static constexpr int BOX = MC == 384 ? 128 : BOX_ROWS;
+  // rows of S image per 64-row chunk there is room for: 40 at 384 rows per
+  // CTA (so k <= 40 there), 48 otherwise
+  static constexpr int KPS = MC == 384 ? 40 : KPAD_MAX;
   static constexpr int STAGE_BYTES = MC * 128;
   static constexpr int OFF_A = 0;
   static constexpr int OFF_S = OFF_A + NST * STAGE_BYTES;
-  static constexpr int S_BYTES = (MC / 64) * KPAD_MAX * 128;
+  static constexpr int S_BYTES = (MC / 64) * KPS * 128;
   static constexpr int OFF_XB = OFF_S + S_BYTES;
   static constexpr int OFF_RECV = OFF_XB + 2 * XB_BYTES;
   static constexpr int OFF_BAR = OFF_RECV + 2 * RECV_BYTES;
@@ -82,8 +89,9 @@ struct Lay {
   // MMA-X reads 128 rows of S per 64-row chunk although only kpad rows are
   // real; the extra rows (whose results are never used) must stay inside the
   // allocation: from the last chunk they reach at most 16 KB past its start.
-  static_assert(OFF_S + (MC / 64 - 1) * KPAD_MAX * 128 + 128 * 128 <= OFF_BAR,
+  static_assert(OFF_S + (MC / 64 - 1) * KPS * 128 + 128 * 128 <= OFF_BAR,
                 "S over-read leaves the shared-memory allocation");
+  static_assert(MC % BOX == 0 && MC % 128 == 0, "whole boxes and MMA tiles");
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
   static_assert(NST <= NST_MAX, "barrier slots");
   static_assert(OFF_S % 1024 == 0 && OFF_XB % 1024 == 0 && XB_BYTES % 1024 == 0 &&
@@ -92,6 +100,7 @@ struct Lay {
   static_assert(OFF_RECV % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 };
 template struct Lay<256>;
+template struct Lay<384>;
 template struct Lay<512>;
 
 // barrier slots
@@ -128,8 +137,10 @@ struct TcParams {
   double* normA2;
   int* status;
   int kp;          // leading dimension of the X / Y panels
-  int kpad;        // rows of the S image: k rounded up to 16 (16, 32 or 48)
-  int kq;          // rows of X~_hi (and of X~_lo): k rounded up to 8; N of MMA-Y = 2 kq
+  int kpad;        // rows of each 64-row chunk of the S image (k rounded up to 16,
+                   // or to 8 at 384 rows per CTA)
+  int kq;          // rows of X~_hi (and of X~_lo): k rounded up to a multiple of 8
+                   // that the cluster size divides; N of MMA-Y = 2 kq
   int img_rank_bytes;  // bytes of S image per CTA: (MC / 64) chunks of kpad rows
   long long timeout_ns;
 };
@@ -547,14 +558,14 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
           }
           mbar_expect_tx(bar(B_AFULL + s), STAGE_BYTES);
 #pragma unroll
-          for (int b = 0; b < MC / BOX_ROWS; ++b)
-            tma_load_2d(sb + OFF_A + s * STAGE_BYTES + b * BOX_ROWS * 128, map, q * NB,
-                        (int)(rank * MC + b * BOX_ROWS), bar(B_AFULL + s));
+          for (int b = 0; b < MC / L::BOX; ++b)
+            tma_load_2d(sb + OFF_A + s * STAGE_BYTES + b * L::BOX * 128, map, q * NB,
+                        (int)(rank * MC + b * L::BOX), bar(B_AFULL + s));
           if (pwi < w1) {
             const CUtensorMap* pmap = P.tmaps + P.work[pwi];
 #pragma unroll
-            for (int b = 0; b < MC / BOX_ROWS; ++b)
-              tma_prefetch_2d(pmap, pq * NB, (int)(rank * MC + b * BOX_ROWS));
+            for (int b = 0; b < MC / L::BOX; ++b)
+              tma_prefetch_2d(pmap, pq * NB, (int)(rank * MC + b * L::BOX));
             padv();
           }
         }
@@ -612,7 +623,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
             const uint64_t a =
                 sdesc(sb + OFF_S + (kk >> 2) * kpad * 128 + (kk & 3) * 32, 16, 1024);
             const uint64_t b = sdesc(sb + OFF_A + s * STAGE_BYTES + kk * 16 * 128,
-                                     BOX_ROWS * 128, 1024);
+                                     L::BOX * 128, 1024);
             tc_mma(tmem + h * NB, a, b, idesc_x, kk > 0 ? 1u : 0u);
           }
           tc_commit(bar(B_XFULL + h));
@@ -710,10 +721,14 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
 #pragma unroll
           for (int j = 0; j < NB; j += 8) tmem_regs8(xr + j);
           if (c < kq && !ctl->abort) {
+            // rows k <= c < kq are zero in X (the S image may be narrower
+            // than kq, and then its rows there are another chunk's)
+            const uint32_t keep = c < md.k ? 0xFFFFFFFFu : 0u;
 #pragma unroll
             for (int e = 0; e < NB; e += 4)
-              st_async_v4(dst0 + e * 4, __uint_as_float(xr[e]), __uint_as_float(xr[e + 1]),
-                          __uint_as_float(xr[e + 2]), __uint_as_float(xr[e + 3]), rfull);
+              st_async_v4(dst0 + e * 4, __uint_as_float(xr[e] & keep),
+                          __uint_as_float(xr[e + 1] & keep), __uint_as_float(xr[e + 2] & keep),
+                          __uint_as_float(xr[e + 3] & keep), rfull);
           }
         }
         tc_fence_before();
@@ -806,7 +821,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
         for (int t = 0; t < MC / 128; ++t) {
           const long long row = (long long)rank * MC + t * 128 + lane_base + lane;
 #pragma unroll 1
-          for (int j = 0; j < kq; j += 8) {
+          for (int j = 0; j < kq && j < P.kp; j += 8) {  // columns past the panel are zero
             uint32_t yv[8], yl[8];
             const uint32_t col = tmem + ((uint32_t)lane_base << 16) + 2 * NB + t * 2 * kq + j;
             tmem_ld8(col, yv);
@@ -977,14 +992,16 @@ struct SImgDesc {
   long long m;
   int k;
   int nchunks;  // 64-row chunks in this image (covers C * MC rows)
+  int kpad;     // rows per chunk (the class's kpad)
   long long off;
 };
 
-__global__ void simg_prep_kernel(const SImgDesc* __restrict__ descs, int kpad,
+__global__ void simg_prep_kernel(const SImgDesc* __restrict__ descs,
                                  unsigned char* __restrict__ simg) {
   const SImgDesc sd = descs[blockIdx.x];
   const int qc = blockIdx.y;  // chunk
   if (qc >= sd.nchunks) return;
+  const int kpad = sd.kpad;
   unsigned char* img = simg + sd.off + (long long)qc * kpad * 128;
   for (int e = threadIdx.x; e < kpad * 8; e += blockDim.x) {
     const int c = e / 8, u = e % 8;
@@ -1073,13 +1090,31 @@ cudaError_t launch_class(const TcParams& prm, int nclusters, cudaStream_t s) {
 // same per column block whatever MC is, so 512 rows per CTA (two 64 KB
 // stages) beat 256 rows (four 32 KB stages) once a cluster is needed; a
 // matrix of at most 256 rows takes one CTA with four stages.
-void cluster_shape(long long m, int* C, int* MC, int mc_pref = 0) {
+void cluster_shape(long long m, int* C, int* MC, int mc_pref = 0, int k = 0) {
   *MC = m <= 256 ? 256 : 512;
   if (mc_pref == 256 && m <= 8 * 256) *MC = 256;  // up to clusters of 8
   if (mc_pref == 512) *MC = 512;
+  if (mc_pref == 384 && m <= 6 * 384 && (k + 7) / 8 * 8 <= 40) {
+    // clusters of 1, 2, 3 or 6 CTAs of 384 rows
+    *MC = 384;
+    *C = m <= 384 ? 1 : (m <= 768 ? 2 : (m <= 1152 ? 3 : 6));
+    return;
+  }
   int c = 1;
   while ((long long)c * *MC < m) c *= 2;
   *C = c;
+}
+
+// Rows of X~ for a class: k rounded up to a multiple of 8 that the cluster
+// size divides (each CTA reduces kq / C rows).
+int class_kq(int kmax, int C) {
+  const int unit = (C == 3 || C == 6) ? 24 : 8;
+  return (kmax + unit - 1) / unit * unit;
+}
+// Rows per 64-row chunk of the S image: k rounded up to 16, or to 8 at 384
+// rows per CTA (shared memory has room for 40 there).
+int class_kpad(int kmax, int MC) {
+  return MC == 384 ? (kmax + 7) / 8 * 8 : (kmax + 15) / 16 * 16;
 }
 
 // The instantiated (C, MC) pairs, in one place for attributes and launches.
@@ -1094,6 +1129,10 @@ cudaError_t class_attrs(int C, int MC, int* ncl) {
   TSK_TC_CASE(2, 256)
   TSK_TC_CASE(4, 256)
   TSK_TC_CASE(8, 256)
+  TSK_TC_CASE(1, 384)
+  TSK_TC_CASE(2, 384)
+  TSK_TC_CASE(3, 384)
+  TSK_TC_CASE(6, 384)
   TSK_TC_CASE(1, 512)
   TSK_TC_CASE(2, 512)
   TSK_TC_CASE(4, 512)
@@ -1107,6 +1146,10 @@ cudaError_t class_launch(int C, int MC, const TcParams& prm, int nclusters, cuda
   if (C == 2 && MC == 256) return launch_class<2, 256>(prm, nclusters, s);
   if (C == 4 && MC == 256) return launch_class<4, 256>(prm, nclusters, s);
   if (C == 8 && MC == 256) return launch_class<8, 256>(prm, nclusters, s);
+  if (C == 1 && MC == 384) return launch_class<1, 384>(prm, nclusters, s);
+  if (C == 2 && MC == 384) return launch_class<2, 384>(prm, nclusters, s);
+  if (C == 3 && MC == 384) return launch_class<3, 384>(prm, nclusters, s);
+  if (C == 6 && MC == 384) return launch_class<6, 384>(prm, nclusters, s);
   if (C == 1 && MC == 512) return launch_class<1, 512>(prm, nclusters, s);
   if (C == 2 && MC == 512) return launch_class<2, 512>(prm, nclusters, s);
   if (C == 4 && MC == 512) return launch_class<4, 512>(prm, nclusters, s);
@@ -1611,8 +1654,6 @@ struct TcPlan {
   std::vector<TcClass> classes;
   const SImgDesc* d_sdesc = nullptr;
   int nsdesc = 0;
-  int kpad = 16;
-  int kq = 8;
   int max_chunks = 1;
   unsigned char* simg = nullptr;
 };
@@ -1798,27 +1839,30 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
     kmax = std::max(kmax, hm[i].k);
   }
   TcPlan* p = new TcPlan();
-  p->kpad = ((kmax + 15) / 16) * 16;
-  p->kq = ((kmax + 7) / 8) * 8;
-  // classes by cluster shape (C, MC)
+  // classes by cluster shape (C, MC); each has its own kq and S-image rows
   std::map<std::pair<int, int>, std::vector<int>> byC;
+  std::map<std::pair<int, int>, int> class_k;  // largest k of the class
+  std::vector<std::pair<int, int>> shape_of(count, std::make_pair(0, 0));
   for (int t = 0; t < nids; ++t) {
     const int i = ids[t];
     int C, mc;
-    cluster_shape(hm[i].m, &C, &mc, mc_pref ? mc_pref[i] : 0);
-    byC[std::make_pair(C, mc)].push_back(i);
+    cluster_shape(hm[i].m, &C, &mc, mc_pref ? mc_pref[i] : 0, hm[i].k);
+    const auto key = std::make_pair(C, mc);
+    byC[key].push_back(i);
+    class_k[key] = std::max(class_k[key], hm[i].k);
+    shape_of[i] = key;
   }
-  // distinct sketch images
-  std::map<std::tuple<const void*, long long, int, int>, long long> img_of;
+  // distinct sketch images: one per sketch and cluster shape (the shape
+  // fixes the chunk count and the rows per chunk)
+  std::map<std::tuple<const void*, long long, int, int, int>, long long> img_of;
   std::vector<SImgDesc> sdesc;
   std::vector<long long> simg_off(count, 0);
   long long img_total = 0;
   for (int t = 0; t < nids; ++t) {
     const int i = ids[t];
-    int C, mc;
-    cluster_shape(hm[i].m, &C, &mc, mc_pref ? mc_pref[i] : 0);
-    // one image per sketch and cluster shape (the shape fixes its chunk count)
-    auto key = std::make_tuple(hm[i].S, hm[i].m, hm[i].k, C * mc);
+    const int C = shape_of[i].first, mc = shape_of[i].second;
+    const int kpad = class_kpad(class_k[shape_of[i]], mc);
+    auto key = std::make_tuple(hm[i].S, hm[i].m, hm[i].k, C, mc);
     auto it = img_of.find(key);
     if (it == img_of.end()) {
       SImgDesc sd;
@@ -1826,9 +1870,11 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
       sd.m = hm[i].m;
       sd.k = hm[i].k;
       sd.nchunks = C * mc / 64;
+      sd.kpad = kpad;
       sd.off = img_total;
       p->max_chunks = std::max(p->max_chunks, sd.nchunks);
-      img_total += (long long)sd.nchunks * p->kpad * 128;
+      img_total += (long long)sd.nchunks * kpad * 128;
+      img_total = (img_total + 1023) / 1024 * 1024;  // images start on 1024 bytes
       it = img_of.emplace(key, sd.off).first;
       sdesc.push_back(sd);
     }
@@ -1854,7 +1900,8 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
         snprintf(msg, msglen,
                  "cudaFuncSetAttribute(%d bytes of shared memory) failed: %s (device opt-in "
                  "limit %d bytes)",
-                 MCc == 256 ? Lay<256>::SMEM_BYTES : Lay<512>::SMEM_BYTES,
+                 MCc == 256 ? Lay<256>::SMEM_BYTES
+                            : (MCc == 384 ? Lay<384>::SMEM_BYTES : Lay<512>::SMEM_BYTES),
                  cudaGetErrorString(ae), optin);
       cudaGetLastError();
       delete p;
@@ -1912,7 +1959,8 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
     CUtensorMap* map = reinterpret_cast<CUtensorMap*>(host.data() + o_map) + i;
     cuuint64_t dims[2] = {(cuuint64_t)hm[i].n, (cuuint64_t)hm[i].m};
     cuuint64_t strides[1] = {(cuuint64_t)hm[i].lda * 2};
-    cuuint32_t box[2] = {(cuuint32_t)NB, (cuuint32_t)BOX_ROWS};
+    const cuuint32_t box_rows = shape_of[i].second == 384 ? 128 : BOX_ROWS;
+    cuuint32_t box[2] = {(cuuint32_t)NB, box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(hm[i].A),
                      dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -1957,9 +2005,10 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
     prm.normA2 = dev_normA2;
     prm.status = status;
     prm.kp = kp;
-    prm.kpad = p->kpad;
-    prm.kq = p->kq;
-    prm.img_rank_bytes = (ct.MC / 64) * p->kpad * 128;
+    const int kc = class_k[std::make_pair(ct.C, ct.MC)];
+    prm.kpad = class_kpad(kc, ct.MC);
+    prm.kq = class_kq(kc, ct.C);
+    prm.img_rank_bytes = (ct.MC / 64) * prm.kpad * 128;
     prm.timeout_ns = timeout_ns;
     p->classes.push_back(cl);
   }
@@ -1969,8 +2018,7 @@ cudaError_t tc_prepare(TcPlan** out, const MatDev* hm, const MatDev* d_mats, int
 
 cudaError_t tc_launch_prep(TcPlan* p, cudaStream_t s) {
   if (!p) return cudaErrorInvalidValue;
-  simg_prep_kernel<<<dim3(p->nsdesc, p->max_chunks), 256, 0, s>>>(p->d_sdesc, p->kpad,
-                                                                    p->simg);
+  simg_prep_kernel<<<dim3(p->nsdesc, p->max_chunks), 256, 0, s>>>(p->d_sdesc, p->simg);
   return cudaGetLastError();
 }
 

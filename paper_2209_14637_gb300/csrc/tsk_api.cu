@@ -65,7 +65,7 @@ struct tsk_handle_s {
   // Autotuned rows of A per CTA of the tensor-core sketch, by size class:
   // (cluster size at 512 rows per CTA, k rounded up to 8) -> 256 or 512.
   std::map<std::pair<int, int>, int> tune;
-  std::map<std::pair<int, int>, std::pair<double, double>> tune_us;  // us / matrix (512, 256)
+  std::map<std::pair<int, int>, std::vector<double>> tune_us;  // us / matrix at 512, 256, 384
   int tune_version = 0;
   int force_mc = 0;  // while tuning: every matrix takes this shape
 };
@@ -1723,11 +1723,12 @@ extern "C" tsk_status tsk_autotune(tsk_handle h, int64_t count, const tsk_mat_de
     if (st != TSK_OK) return st;
   }
   if (!tc_supported()) return TSK_OK;  // nothing to tune
-  // classes where both shapes exist: 256 < m <= 2048 (1 to 8 CTAs of 256 rows)
+  // classes where more than one shape exists: 256 < m <= 2304 (CTAs of 256
+  // rows up to m = 2048, of 384 rows up to 2304 when k <= 40, of 512 rows)
   std::map<std::pair<int, int>, std::vector<tsk_mat_desc>> byk;
   for (int64_t i = 0; i < count; ++i) {
     const tsk_mat_desc& d = mats[i];
-    if (!tc_eligible_one(d) || d.m <= 256 || d.m > 2048) continue;
+    if (!tc_eligible_one(d) || d.m <= 256 || d.m > 2304) continue;
     auto& v = byk[tune_key(d.m, d.k)];
     if (v.size() < 16) v.push_back(d);  // up to 16 matrices of the batch per class
   }
@@ -1739,9 +1740,17 @@ extern "C" tsk_status tsk_autotune(tsk_handle h, int64_t count, const tsk_mat_de
   const int save_force = h->force_mc;
   for (auto& kv : byk) {
     const std::vector<tsk_mat_desc>& v = kv.second;
-    double us[2] = {0.0, 0.0};
-    for (int c = 0; c < 2 && result == TSK_OK; ++c) {
-      h->force_mc = c == 0 ? 512 : 256;
+    int mmax = 0, kmax = 0;
+    for (const tsk_mat_desc& d : v) {
+      mmax = std::max<int>(mmax, (int)d.m);
+      kmax = std::max(kmax, d.k);
+    }
+    const int shapes[3] = {512, 256, 384};
+    bool valid[3] = {true, mmax <= 2048, (kmax + 7) / 8 * 8 <= 40};
+    double us[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < 3 && result == TSK_OK; ++c) {
+      if (!valid[c]) continue;
+      h->force_mc = shapes[c];
       tsk_plan p = nullptr;
       result = build_plan(h, (int64_t)v.size(), v.data(), prec, nullptr, nullptr, nullptr, &p);
       if (result != TSK_OK) break;
@@ -1763,8 +1772,11 @@ extern "C" tsk_status tsk_autotune(tsk_handle h, int64_t count, const tsk_mat_de
       us[c] = 1e3 * best / (double)v.size();
     }
     if (result != TSK_OK) break;
-    h->tune[kv.first] = us[1] < us[0] ? 256 : 512;
-    h->tune_us[kv.first] = {us[0], us[1]};
+    int best = 0;
+    for (int c = 1; c < 3; ++c)
+      if (valid[c] && us[c] < us[best]) best = c;
+    h->tune[kv.first] = shapes[best];
+    h->tune_us[kv.first] = {us[0], valid[1] ? us[1] : 0.0, valid[2] ? us[2] : 0.0};
   }
   h->force_mc = save_force;
   ++h->tune_version;  // plans built from now on use the table
@@ -1791,10 +1803,14 @@ extern "C" tsk_status tsk_autotune_save(tsk_handle h, const char* path) {
   fprintf(f, "{\"kernel\": \"sketch_tc\", \"classes\": [");
   bool first = true;
   for (auto& kv : h->tune) {
-    auto us = h->tune_us.count(kv.first) ? h->tune_us[kv.first] : std::make_pair(0.0, 0.0);
+    std::vector<double> us = h->tune_us.count(kv.first) ? h->tune_us[kv.first]
+                                                        : std::vector<double>(3, 0.0);
+    us.resize(3, 0.0);
+    // a shape that was not timed (not valid for the class) is written as 0
     fprintf(f, "%s\n  {\"cluster_at_512\": %d, \"k8\": %d, \"rows_per_cta\": %d, "
-               "\"us_per_matrix_512\": %.4f, \"us_per_matrix_256\": %.4f}",
-            first ? "" : ",", kv.first.first, kv.first.second, kv.second, us.first, us.second);
+               "\"us_per_matrix_512\": %.4f, \"us_per_matrix_256\": %.4f, "
+               "\"us_per_matrix_384\": %.4f}",
+            first ? "" : ",", kv.first.first, kv.first.second, kv.second, us[0], us[1], us[2]);
     first = false;
   }
   fprintf(f, "\n]}\n");
@@ -1837,7 +1853,7 @@ extern "C" tsk_status tsk_autotune_load(tsk_handle h, const char* path) {
     const std::string obj = text.substr(pos, end - pos + 1);
     double c = 0, k8 = 0, mc = 0;
     if (!field(obj, "cluster_at_512", &c) || !field(obj, "k8", &k8) ||
-        !field(obj, "rows_per_cta", &mc) || (mc != 256 && mc != 512)) {
+        !field(obj, "rows_per_cta", &mc) || (mc != 256 && mc != 384 && mc != 512)) {
       set_err(h, "tsk_autotune_load: malformed entry in %s", path);
       return TSK_EINVAL;
     }

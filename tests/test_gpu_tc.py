@@ -284,3 +284,52 @@ def test_padded_rows_take_the_tensor_cores(tsk):
         assert abs(float(out["err"][i]) - o["err"]) <= GAP * o["err"], i
     h.close()
 
+
+
+@pytest.mark.parametrize("m,n,k", [(300, 200, 16), (700, 136, 40), (1000, 448, 24),
+                                   (2048, 576, 40), (2200, 100, 10)])
+def test_tc_384_row_ctas(tsk, tmp_path, m, n, k):
+    """The 384-row shape (three stages of A; clusters of 1, 2, 3 and 6 CTAs,
+    rows of X~ padded to a multiple the cluster size divides, an S image of
+    round8(k) rows) chosen through a tuning table, against the oracle."""
+    import json
+    c512 = 1
+    while c512 * 512 < m:
+        c512 *= 2
+    path = tmp_path / "t.json"
+    path.write_text(json.dumps({"kernel": "sketch_tc", "classes": [
+        {"cluster_at_512": c512, "k8": (k + 7) // 8 * 8, "rows_per_cta": 384}]}))
+    A, S = _case(m, n, k, 900 + m)
+    h = tsk.Handle(kernel=tsk.KERNEL_TC)
+    h.autotune_load(str(path))
+    out = h.approx_batch([A], [S], k // 2, outputs=True)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    o = oracle.scw(_np(A), _np(S), k // 2)
+    assert abs(float(out["err"][0]) - o["err"]) <= GAP * o["err"]
+    np.testing.assert_allclose(_np(out["normA2"])[0], o["normA2"], rtol=1e-6)
+    B = _np(out["US"][0]) @ _np(out["Vt"][0])
+    assert np.linalg.norm(B - o["B"]) <= 2e-2 * np.linalg.norm(o["B"])
+    h.close()
+
+
+def test_expired_waits_report_a_timeout_and_leave_the_context_usable(tsk):
+    """Failure detection without a fault: a spin limit of one iteration
+    (120 ns) makes the single-CTA tensor-core kernel's bounded waits run out
+    while its loads are still in flight.  The kernel raises the timeout bit,
+    stops issuing and stops arriving on barriers whose phases can no longer
+    complete, drains its own loads and tensor-core operations (those drains
+    have their own two-second bound), frees its TMEM and returns: the host
+    reads TSK_ETIMEOUT, and a normal handle then runs the same case
+    correctly on the same context."""
+    A, S = _case(384, 256, 16, 21)  # m <= 512: one CTA, no peers in a cluster
+    h = tsk.Handle(kernel=tsk.KERNEL_TC, spin_limit=1)
+    h.approx_batch([A], [S], 8)
+    assert h.sync_status() == 5  # TSK_ETIMEOUT
+    assert h.sync_status() == 0  # read and cleared
+    h.close()
+    out, st, h2 = _run(tsk, tsk.KERNEL_TC, [A], [S], [8])
+    assert st == 0
+    o = oracle.scw(_np(A), _np(S), 8, dense=False)
+    assert abs(float(out["err"][0]) - o["err"]) <= GAP * o["err"]
+    h2.close()
