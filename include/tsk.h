@@ -240,8 +240,9 @@ tsk_status tsk_plan_info(tsk_plan plan, int64_t* workspace_bytes,
    the batch where the kernel has more than one shape -- 256 < m <= 2304,
    where a matrix can be split over CTAs of 512 rows, of 256 rows (m <=
    2048) or of 384 rows (k <= 40; clusters of 1, 2, 3 or 6 CTAs, three
-   stages of A in flight instead of two) -- it builds a plan of up to 16 of
-   the class's matrices for each shape, times the sketch pass
+   stages of A in flight instead of two) -- it builds a plan of the class's
+   matrices (up to 2048 of them: a shape's throughput depends on how many
+   SMs the class fills) for each shape, times the sketch pass
    (CUDA events around it inside the plan's graph; best of reps executions
    after one warm-up) and keeps the faster shape in the handle.  A size
    class is (the cluster size at 512 rows per CTA, k rounded up to 8).  Plans

@@ -185,9 +185,9 @@ template <typename Tin, int KP>
 __global__ void __launch_bounds__(128)
 sketch_x_f32_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ items,
                     float* __restrict__ X, double* __restrict__ normA2) {
-  constexpr int BJ = 64, BI = 32, CPT = KP / 16;
-  __shared__ __align__(16) float As[BI][BJ];
-  __shared__ __align__(16) float Ss[BI][KP];
+  constexpr int BJ = 64, BI = 32, CPT = KP / 16, SQ = BI * KP / 128;
+  __shared__ __align__(16) float As[2][BI][BJ];
+  __shared__ float Ss[2][BI][KP + 1];  // rows padded: the transposing stores hit 32 banks
   __shared__ double red[4];
   const int2 it = items[blockIdx.x];
   const MatDev md = mats[it.x];
@@ -203,48 +203,73 @@ sketch_x_f32_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ it
   for (int q = 0; q < 8; ++q)
 #pragma unroll
     for (int p = 0; p < CPT; ++p) acc[q][p] = 0.f;
-  double sq = 0.0;
-  for (long long i0 = 0; i0 < m; i0 += BI) {
-    float part = 0.f;
+  // the next chunk is fetched into registers while the current one is used
+  float va[4][4], vs[SQ];
+  auto fetch = [&](long long i0) {
 #pragma unroll
     for (int t = 0; t < 4; ++t) {  // 512 quads of the 32 x 64 chunk
       const int e4 = tid + 128 * t, ii = e4 >> 4, c4 = (e4 & 15) * 4;
       const long long i = i0 + ii, j = j0 + c4;
-      float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) va[t][u] = 0.f;
       if (i < m) {
         if (vec && j + 3 < n) {
-          load4(A + i * lda + j, v);
+          load4(A + i * lda + j, va[t]);
         } else {
 #pragma unroll
           for (int u = 0; u < 4; ++u)
-            if (j + u < n) v[u] = to_float(A[i * lda + j + u]);
+            if (j + u < n) va[t][u] = to_float(A[i * lda + j + u]);
         }
       }
+    }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) part = fmaf(v[u], v[u], part);
-      *reinterpret_cast<float4*>(&As[ii][c4]) = make_float4(v[0], v[1], v[2], v[3]);
+    for (int q = 0; q < SQ; ++q) {
+      const int e = tid + 128 * q, c = e / BI, ii = e % BI;
+      const long long i = i0 + ii;
+      vs[q] = (c < k && i < m) ? S[(long long)c * m + i] : 0.f;
+    }
+  };
+  double sq = 0.0;
+  auto park = [&](int buf) {  // registers -> shared buffer, squares summed
+    float part = 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e4 = tid + 128 * t, ii = e4 >> 4, c4 = (e4 & 15) * 4;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) part = fmaf(va[t][u], va[t][u], part);
+      *reinterpret_cast<float4*>(&As[buf][ii][c4]) =
+          make_float4(va[t][0], va[t][1], va[t][2], va[t][3]);
     }
     sq += (double)part;
-    for (int e = tid; e < BI * KP; e += 128) {
-      const int c = e / BI, ii = e % BI;
-      const long long i = i0 + ii;
-      Ss[ii][c] = (c < k && i < m) ? S[(long long)c * m + i] : 0.f;
+#pragma unroll
+    for (int q = 0; q < SQ; ++q) {
+      const int e = tid + 128 * q;
+      Ss[buf][e % BI][e / BI] = vs[q];
     }
-    __syncthreads();
+  };
+  const int nch = (int)((m + BI - 1) / BI);
+  fetch(0);
+  park(0);
+  __syncthreads();
+  for (int ch = 0; ch < nch; ++ch) {
+    const int cur = ch & 1;
+    if (ch + 1 < nch) fetch((long long)(ch + 1) * BI);
 #pragma unroll 4
     for (int ii = 0; ii < BI; ++ii) {
       float a[8], sv[CPT];
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[ii][jg * 8]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[ii][jg * 8 + 4]);
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][ii][jg * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][ii][jg * 8 + 4]);
       a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
       a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
 #pragma unroll
-      for (int p = 0; p < CPT; ++p) sv[p] = Ss[ii][cg * CPT + p];
+      for (int p = 0; p < CPT; ++p) sv[p] = Ss[cur][ii][cg * CPT + p];
 #pragma unroll
       for (int q = 0; q < 8; ++q)
 #pragma unroll
         for (int p = 0; p < CPT; ++p) acc[q][p] = fmaf(a[q], sv[p], acc[q][p]);
     }
+    // the other buffer was last read in the previous chunk, before its barrier
+    if (ch + 1 < nch) park(cur ^ 1);
     __syncthreads();
   }
   float* __restrict__ Xm = X + md.offX;
@@ -266,9 +291,9 @@ template <typename Tin, int KP>
 __global__ void __launch_bounds__(128)
 sketch_y_f32_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ items,
                     const float* __restrict__ X, float* __restrict__ Y) {
-  constexpr int BI = 64, BJ = 32, CPT = KP / 16, LDT = BI + 4;
-  __shared__ __align__(16) float AsT[BJ][LDT];
-  __shared__ __align__(16) float Xs[BJ][KP];
+  constexpr int BI = 64, BJ = 32, CPT = KP / 16, LDT = BI + 4, XQ = BJ * KP / 4 / 128;
+  __shared__ __align__(16) float AsT[2][BJ][LDT];
+  __shared__ __align__(16) float Xs[2][BJ][KP];
   const int2 it = items[blockIdx.x];
   const MatDev md = mats[it.x];
   const Tin* __restrict__ A = (const Tin*)md.A;
@@ -282,46 +307,68 @@ sketch_y_f32_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ it
   for (int q = 0; q < 8; ++q)
 #pragma unroll
     for (int p = 0; p < CPT; ++p) acc[q][p] = 0.f;
-  for (long long j0 = 0; j0 < n; j0 += BJ) {
+  float va[4][4];
+  float4 vx[XQ];
+  auto fetch = [&](long long j0) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {  // 512 quads of the 64 x 32 chunk, stored transposed
+    for (int t = 0; t < 4; ++t) {  // 512 quads of the 64 x 32 chunk
       const int e4 = tid + 128 * t, ii = e4 >> 3, c4 = (e4 & 7) * 4;
       const long long i = i0 + ii, j = j0 + c4;
-      float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) va[t][u] = 0.f;
       if (i < m) {
         if (vec && j + 3 < n) {
-          load4(A + i * lda + j, v);
+          load4(A + i * lda + j, va[t]);
         } else {
 #pragma unroll
           for (int u = 0; u < 4; ++u)
-            if (j + u < n) v[u] = to_float(A[i * lda + j + u]);
+            if (j + u < n) va[t][u] = to_float(A[i * lda + j + u]);
         }
       }
+    }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) AsT[c4 + u][ii] = v[u];
-    }
-    for (int e = tid; e < BJ * KP / 4; e += 128) {  // X rows are KP floats, 16-byte aligned
-      const int jj = e / (KP / 4), c4 = (e % (KP / 4)) * 4;
+    for (int q = 0; q < XQ; ++q) {  // X rows are KP floats, 16-byte aligned
+      const int e = tid + 128 * q, jj = e / (KP / 4), c4 = (e % (KP / 4)) * 4;
       const long long j = j0 + jj;
-      float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (j < n) w = *reinterpret_cast<const float4*>(Xm + j * KP + c4);
-      *reinterpret_cast<float4*>(&Xs[jj][c4]) = w;
+      vx[q] = j < n ? *reinterpret_cast<const float4*>(Xm + j * KP + c4)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __syncthreads();
+  };
+  auto park = [&](int buf) {  // registers -> shared buffer, A transposed
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e4 = tid + 128 * t, ii = e4 >> 3, c4 = (e4 & 7) * 4;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) AsT[buf][c4 + u][ii] = va[t][u];
+    }
+#pragma unroll
+    for (int q = 0; q < XQ; ++q) {
+      const int e = tid + 128 * q, jj = e / (KP / 4), c4 = (e % (KP / 4)) * 4;
+      *reinterpret_cast<float4*>(&Xs[buf][jj][c4]) = vx[q];
+    }
+  };
+  const int nch = (int)((n + BJ - 1) / BJ);
+  fetch(0);
+  park(0);
+  __syncthreads();
+  for (int ch = 0; ch < nch; ++ch) {
+    const int cur = ch & 1;
+    if (ch + 1 < nch) fetch((long long)(ch + 1) * BJ);
 #pragma unroll 4
     for (int jj = 0; jj < BJ; ++jj) {
       float a[8], xv[CPT];
-      const float4 a0 = *reinterpret_cast<const float4*>(&AsT[jj][ig * 8]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&AsT[jj][ig * 8 + 4]);
+      const float4 a0 = *reinterpret_cast<const float4*>(&AsT[cur][jj][ig * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&AsT[cur][jj][ig * 8 + 4]);
       a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
       a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
 #pragma unroll
-      for (int p = 0; p < CPT; ++p) xv[p] = Xs[jj][cg * CPT + p];
+      for (int p = 0; p < CPT; ++p) xv[p] = Xs[cur][jj][cg * CPT + p];
 #pragma unroll
       for (int q = 0; q < 8; ++q)
 #pragma unroll
         for (int p = 0; p < CPT; ++p) acc[q][p] = fmaf(a[q], xv[p], acc[q][p]);
     }
+    if (ch + 1 < nch) park(cur ^ 1);
     __syncthreads();
   }
   float* __restrict__ Ym = Y + md.offY;

@@ -1729,8 +1729,11 @@ extern "C" tsk_status tsk_autotune(tsk_handle h, int64_t count, const tsk_mat_de
   for (int64_t i = 0; i < count; ++i) {
     const tsk_mat_desc& d = mats[i];
     if (!tc_eligible_one(d) || d.m <= 256 || d.m > 2304) continue;
+    // every matrix of the class (up to 2048): a shape's throughput depends on
+    // how many SMs the class fills, so a small sample can rank the shapes
+    // the wrong way round (wider clusters win while SMs are idle)
     auto& v = byk[tune_key(d.m, d.k)];
-    if (v.size() < 16) v.push_back(d);  // up to 16 matrices of the batch per class
+    if (v.size() < 2048) v.push_back(d);
   }
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -287,7 +287,7 @@ def test_padded_rows_take_the_tensor_cores(tsk):
 
 
 @pytest.mark.parametrize("m,n,k", [(300, 200, 16), (700, 136, 40), (1000, 448, 24),
-                                   (2048, 576, 40), (2200, 100, 10)])
+                                   (2048, 576, 40), (2200, 104, 10)])
 def test_tc_384_row_ctas(tsk, tmp_path, m, n, k):
     """The 384-row shape (three stages of A; clusters of 1, 2, 3 and 6 CTAs,
     rows of X~ padded to a multiple the cluster size divides, an S image of
