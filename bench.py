@@ -249,6 +249,48 @@ def _sgemm_peak():
         torch.backends.cuda.matmul.allow_tf32 = prev
 
 
+def fp8_training_gram(tsk, h, tr, G_bf16, k, peaks, peak_src):
+    """The training Gram from E4M3 copies (per-row, per-8-matrix power-of-two
+    scales): quantisation and Gram timed on the device, the Gram against
+    twice the measured BF16 peak (the nominal FP8 / BF16 tensor ratio), and
+    the sketch it gives scored on the BF16 Gram: the fraction of the best
+    captured energy trace(S G S^T) (Eq. 3.2) that it keeps."""
+    import torch
+    D, m, n = tr.shape
+    mats = [tr[i] for i in range(D)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    A8, scales = h.quantize_e4m3(mats)
+    ev[1].record()
+    G8 = h.gram_e4m3(A8, scales, n)
+    ev[2].record()
+    torch.cuda.synchronize()
+    ev[0].record()  # once more, with the tensor maps cached
+    A8, scales = h.quantize_e4m3(mats)
+    ev[1].record()
+    G8 = h.gram_e4m3(A8, scales, n, out=G8)
+    ev[2].record()
+    torch.cuda.synchronize()
+    q_ms, g_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    flops = float(m) ** 2 * n * D
+    tf = flops / (g_ms / 1e3) / 1e12
+    peak = 2.0 * float(peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]))
+    S8, _, st8 = h.sketch_from_gram(G8, k, prec=tsk.FP32)
+    Sb, _, stb = h.sketch_from_gram(G_bf16, k, prec=tsk.FP32)
+    Gd = G_bf16.double()
+    cap8 = float(torch.trace(S8.double() @ Gd @ S8.double().T))
+    capb = float(torch.trace(Sb.double() @ Gd @ Sb.double().T))
+    rel = float((G8 - Gd).abs().max() / Gd.diagonal().max())
+    del A8, scales, G8
+    return {"quantize_ms": q_ms, "gram_ms": g_ms, "status": [st8, stb],
+            "gram_max_abs_diff_over_max_diag": rel,
+            "captured_energy_vs_bf16_gram": cap8 / capb,
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tf / peak,
+                         "peak_source": "2 x bf16_tflops (burst) of " + peak_src +
+                                        " (nominal FP8 / BF16 ratio)", "flops": flops}}
+
+
 def run_tsk(args):
     import numpy as np
     import torch
@@ -307,6 +349,8 @@ def run_tsk(args):
                                "unit": "TFLOP/s", "frac": gram_tf / gpeak,
                                "peak_source": "bf16_tflops (burst) of " + peak_src,
                                "flops": gram_flops}}
+    if args.kernel != tsk.KERNEL_SIMT:
+        train_info["fp8"] = fp8_training_gram(tsk, h, tr, G, spec.k, peaks, peak_src)
     stage(f"training Gram: {train_info}")
     del tr, G
     torch.cuda.empty_cache()

@@ -170,12 +170,39 @@ tsk_status tsk_sync_status(tsk_handle h, tsk_stream stream);
    training shards can be summed (the one exchange step of a multi-GPU
    training side).  Products are accumulated in the precision's compute type
    (double for TSK_FP64, float otherwise) and summed into G in double.
-   TSK_BF16 mode 1 with 16-byte aligned rows (lda * 2 a multiple of 16,
-   16-byte aligned A[d]) runs on the tensor cores (FP32 accumulation over
-   eight matrices at a time) and leaves G exactly symmetric. */
+   TSK_BF16 with 16-byte aligned rows (lda * 2 a multiple of 16, 16-byte
+   aligned A[d]) runs on the tensor cores (FP32 accumulation over eight
+   matrices at a time; mode 1 on 256 x 256 tiles of CTA pairs unless
+   gram_tile = 1, mode 2 on 128 x 128 tiles reading A's columns) and leaves
+   G exactly symmetric.  The tensor maps of the last training set are kept
+   in the handle, so a repeated call on the same matrices skips encoding
+   them. */
 tsk_status tsk_gram(tsk_handle h, const void* const* A, int64_t D, int64_t m,
                     int64_t n, int64_t lda, tsk_prec prec, int32_t mode,
                     double* G, int32_t accumulate, tsk_stream stream);
+
+/* FP8 training Gram (E4M3 with per-tile scaling).  tsk_quantize_e4m3 stores
+   each training matrix A[d] (TSK_FP32 or TSK_BF16, m x n, lda >= n) as E4M3
+   bytes in A8[d] (device, m x n, ld8 >= n bytes per row): with one
+   power-of-two scale per row and per group of eight consecutive matrices,
+   scales[(d / 8) * m + i] (device, ceil(D / 8) * m floats), the smallest
+   that keeps max_{d in group, j} |A_d[i, j]| / scale <= 448, each byte is
+   E4M3(A_d[i, j] / scale) rounded to nearest.  E4M3 keeps 3 mantissa bits:
+   the stored values are within 2^-4 of A relative to each element (rounding
+   is to nearest, so the error is at most half that).  D <= 65535.
+   tsk_gram_e4m3 then forms the mode-1 Gram of the stored values,
+   G (device, m x m, double) = sum_d S_d A8_d A8_d^T S_d (S_d the diagonal of
+   the group's scales), on the tensor cores (tcgen05 kind::f8f6f4, CTA pairs,
+   FP32 accumulation over each group of eight, scaled and summed in double);
+   ld8 must be a multiple of 16 and every A8[d] 16-byte aligned (the TMA rule),
+   A8 is a host array of device pointers; accumulate != 0 adds to G.  Both
+   block until done. */
+tsk_status tsk_quantize_e4m3(tsk_handle h, const void* const* A, int64_t D, int64_t m,
+                             int64_t n, int64_t lda, tsk_prec prec, void* const* A8,
+                             int64_t ld8, float* scales, tsk_stream stream);
+tsk_status tsk_gram_e4m3(tsk_handle h, const void* const* A8, const float* scales, int64_t D,
+                         int64_t m, int64_t n, int64_t ld8, double* G, int32_t accumulate,
+                         tsk_stream stream);
 
 /* Leading k eigenvectors of the symmetric dim x dim G (device, double) as the
    rows of S (device, k x dim; double for TSK_FP64, float otherwise), in

@@ -107,6 +107,9 @@ def load_library(path: str = LIB_PATH):
         "tsk_error": ([P, I64, C.POINTER(MatDesc), I32, C.POINTER(MatOut), P, P], I32),
         "tsk_ivy_grad": ([P, I64, C.POINTER(MatDesc), I32, P, P, P, P], I32),
         "tsk_approx_noalloc": ([C.POINTER(MatDesc), I32, P, P, P, P], I32),
+        "tsk_quantize_e4m3": ([P, C.POINTER(P), I64, I64, I64, I64, I32, C.POINTER(P), I64,
+                               P, P], I32),
+        "tsk_gram_e4m3": ([P, C.POINTER(P), P, I64, I64, I64, I64, P, I32, P], I32),
         "tsk_autotune": ([P, I64, C.POINTER(MatDesc), I32, I32, P], I32),
         "tsk_autotune_save": ([P, C.c_char_p], I32),
         "tsk_autotune_load": ([P, C.c_char_p], I32),
@@ -207,6 +210,38 @@ class Handle:
         self._check(self._lib.tsk_gram(self._h, ptrs, len(As), m, n, As[0].stride(0),
                                        prec, mode, _ptr(out), int(accumulate),
                                        _stream(stream)))
+        return out
+
+    def quantize_e4m3(self, As, stream=None):
+        """E4M3 copies of FP32 / BF16 training matrices with one power-of-two
+        scale per row and group of eight matrices.  Returns (A8 uint8 of
+        shape (D, m, ld8) with ld8 = n rounded up to 16, scales float32 of
+        shape (ceil(D / 8), m))."""
+        mats = [As[i] for i in range(As.shape[0])] if isinstance(As, torch.Tensor) else list(As)
+        _require_cuda(*mats)
+        m, n = mats[0].shape
+        D = len(mats)
+        ld8 = (n + 15) // 16 * 16
+        A8 = torch.zeros(D, m, ld8, dtype=torch.uint8, device=mats[0].device)
+        scales = torch.empty((D + 7) // 8, m, dtype=torch.float32, device=mats[0].device)
+        src = (C.c_void_p * D)(*[a.data_ptr() for a in mats])
+        dst = (C.c_void_p * D)(*[A8[d].data_ptr() for d in range(D)])
+        self._check(self._lib.tsk_quantize_e4m3(self._h, src, D, m, n, mats[0].stride(0),
+                                                _DTYPE_PREC[mats[0].dtype], dst, ld8,
+                                                _ptr(scales), _stream(stream)))
+        return A8, scales
+
+    def gram_e4m3(self, A8: torch.Tensor, scales: torch.Tensor, n: int,
+                  out: Optional[torch.Tensor] = None, accumulate: bool = False, stream=None):
+        """Mode-1 Gram of E4M3 matrices (from quantize_e4m3) on the tensor
+        cores, scaled back to the stored values; float64 (m x m)."""
+        _require_cuda(A8, scales)
+        D, m, ld8 = A8.shape
+        if out is None:
+            out = torch.zeros(m, m, dtype=torch.float64, device=A8.device)
+        ptrs = (C.c_void_p * D)(*[A8[d].data_ptr() for d in range(D)])
+        self._check(self._lib.tsk_gram_e4m3(self._h, ptrs, _ptr(scales), D, m, n, ld8, _ptr(out),
+                                            int(accumulate), _stream(stream)))
         return out
 
     def sketch_from_gram(self, G: torch.Tensor, k: int, prec: int = FP32,

@@ -1174,10 +1174,12 @@ cudaError_t class_launch(int C, int MC, const TcParams& prm, int nclusters, cuda
 // the other one.  The lower triangle is mirrored afterwards.
 // ---------------------------------------------------------------------------
 struct GramParams {
-  const CUtensorMap* tmaps;  // one per matrix: box 64 columns x 128 rows
+  const CUtensorMap* tmaps;  // one per matrix: box 64 columns x 128 rows (mode 1)
+                             // or 64 columns x 64 rows (mode 2)
   long long D, m, n;
-  double* G;                 // m x m, row-major
-  int ntile;                 // ceil(m / 128)
+  double* G;                 // dim x dim, row-major (dim = m in mode 1, n in mode 2)
+  int mode;                  // 1: G = sum A A^T; 2: G = sum A^T A
+  int ntile;                 // ceil(dim / 128)
   int splits;                // CTAs per tile (contiguous ranges of matrices)
   int* status;
   long long timeout_ns;
@@ -1216,7 +1218,11 @@ __global__ void __launch_bounds__(GNT, 1) gram_tc_kernel(const __grid_constant__
   const bool diag = ti == tj;
   const long long d0 = P.D * (long long)blockIdx.y / P.splits;
   const long long d1 = P.D * (long long)(blockIdx.y + 1) / P.splits;
-  const int nkb = (int)((P.n + 63) / 64);
+  // mode 1: rows of G are rows of A, the sum runs over the n columns;
+  // mode 2: rows of G are columns of A, the sum runs over the m rows
+  const bool m2 = P.mode == 2;
+  const long long dim = m2 ? P.n : P.m;
+  const int nkb = (int)(((m2 ? P.m : P.n) + 63) / 64);
   const int ngroups = (int)((d1 - d0 + GFL - 1) / GFL);
   if (tid == 0) {
     for (int s = 0; s < GSTG; ++s) {
@@ -1258,9 +1264,22 @@ __global__ void __launch_bounds__(GNT, 1) gram_tc_kernel(const __grid_constant__
             break;
           }
           mbar_expect_tx(bar(GB_FULL + s), diag ? GTILE : GSTAGE);
-          tma_load_2d(sb + s * GSTAGE, map, kb * 64, ti * 128, bar(GB_FULL + s));
-          if (!diag)
-            tma_load_2d(sb + s * GSTAGE + GTILE, map, kb * 64, tj * 128, bar(GB_FULL + s));
+          if (!m2) {
+            // K-major: rows ti*128.. of A, 64 of its columns
+            tma_load_2d(sb + s * GSTAGE, map, kb * 64, ti * 128, bar(GB_FULL + s));
+            if (!diag)
+              tma_load_2d(sb + s * GSTAGE + GTILE, map, kb * 64, tj * 128, bar(GB_FULL + s));
+          } else {
+            // MN-major: 64 rows of A (the K slice), its columns ti*128.. as
+            // two boxes of 64 (the two 128-byte atoms along M)
+            for (int hh = 0; hh < 2; ++hh) {
+              tma_load_2d(sb + s * GSTAGE + hh * (GTILE / 2), map, ti * 128 + hh * 64, kb * 64,
+                          bar(GB_FULL + s));
+              if (!diag)
+                tma_load_2d(sb + s * GSTAGE + GTILE + hh * (GTILE / 2), map, tj * 128 + hh * 64,
+                            kb * 64, bar(GB_FULL + s));
+            }
+          }
         }
       }
       for (int s = 0; s < GSTG; ++s) {  // every load issued must land before exit
@@ -1273,7 +1292,7 @@ __global__ void __launch_bounds__(GNT, 1) gram_tc_kernel(const __grid_constant__
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(128, 128, 0, 0);
+      const uint32_t idesc = m2 ? idesc_bf16(128, 128, 1, 1) : idesc_bf16(128, 128, 0, 0);
       long long q = 0;
       bool ok = true;
       for (int grp = 0; grp < ngroups && ok; ++grp) {
@@ -1295,9 +1314,16 @@ __global__ void __launch_bounds__(GNT, 1) gram_tc_kernel(const __grid_constant__
             tc_fence_after();
             const uint32_t a0 = sb + s * GSTAGE, b0 = diag ? a0 : a0 + GTILE;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              tc_mma(tmem + buf * 128, sdesc(a0 + kk * 32, 16, 1024),
-                     sdesc(b0 + kk * 32, 16, 1024), idesc, (first && kk == 0) ? 0u : 1u);
+            for (int kk = 0; kk < 4; ++kk) {
+              // K-major: the K slice advances 32 bytes inside the 128-byte
+              // rows; MN-major: it advances 16 rows (2 KB), the 8-row groups
+              // are 1 KB apart and the two 64-wide atoms along M 8 KB apart
+              const uint64_t da = m2 ? sdesc(a0 + kk * 2048, GTILE / 2, 1024)
+                                     : sdesc(a0 + kk * 32, 16, 1024);
+              const uint64_t db = m2 ? sdesc(b0 + kk * 2048, GTILE / 2, 1024)
+                                     : sdesc(b0 + kk * 32, 16, 1024);
+              tc_mma(tmem + buf * 128, da, db, idesc, (first && kk == 0) ? 0u : 1u);
+            }
             first = false;
             tc_commit(bar(GB_EMPTY + s));
           }
@@ -1312,6 +1338,7 @@ __global__ void __launch_bounds__(GNT, 1) gram_tc_kernel(const __grid_constant__
     const int lane_base = (warp & 3) * 32;  // the TMEM lanes this warp may read
     const long long row = (long long)ti * 128 + lane_base + lane;
     const bool atomic = P.splits > 1;
+    const long long ldg = dim;
     for (int grp = 0; grp < ngroups; ++grp) {
       const int buf = grp & 1;
       const uint32_t v = (uint32_t)(grp >> 1);
@@ -1324,9 +1351,9 @@ __global__ void __launch_bounds__(GNT, 1) gram_tc_kernel(const __grid_constant__
         tmem_wait_ld();
         tmem_regs8(r);
         tmem_regs8(r + 8);
-        if (row < P.m) {
-          double* g = P.G + row * P.m + (long long)tj * 128 + c0;
-          const long long cmax = P.m - ((long long)tj * 128 + c0);
+        if (row < dim) {
+          double* g = P.G + row * ldg + (long long)tj * 128 + c0;
+          const long long cmax = dim - ((long long)tj * 128 + c0);
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             if (i < cmax) {
@@ -1372,11 +1399,12 @@ __global__ void __launch_bounds__(GNT, 1) gram_tc_kernel(const __grid_constant__
 // to G and arrive on the even CTA's TEMPTY barrier.
 // ---------------------------------------------------------------------------
 struct Gram2Params {
-  const CUtensorMap* tmaps;  // one per matrix: box 64 columns x 128 rows
+  const CUtensorMap* tmaps;  // one per matrix: box 128 bytes x 128 rows
   long long D, m, n;
   double* G;
+  const float* scales;  // FP8 operands: per group of GFL matrices, m row scales
   int ntile;   // ceil(m / 256)
-  int splits;  // pairs per tile (contiguous ranges of matrices)
+  int splits;  // pairs per tile (contiguous ranges of groups of GFL matrices)
   int* status;
   long long timeout_ns;
 };
@@ -1406,6 +1434,20 @@ __device__ __forceinline__ void tc_mma_pair(uint32_t d_tmem, uint64_t adesc, uin
       "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
       : "memory");
+}
+// The same MMA on 8-bit operands (both E4M3), K = 32 per instruction.
+__device__ __forceinline__ void tc_mma_pair_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                               uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+// Instruction descriptor, kind::f8f6f4 with E4M3 operands (format code 0)
+// and FP32 accumulation, both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 __device__ __forceinline__ void tc_commit_pair_mc(uint32_t bar) {
   asm volatile(
@@ -1453,6 +1495,10 @@ __device__ __forceinline__ bool bwait_cluster(uint32_t bar, uint32_t parity, vol
   }
 }
 
+// F8: E4M3 operands with per-(group, row) scales applied at each flush;
+// otherwise BF16.  A stage row is 128 bytes either way: 64 BF16 or 128 E4M3
+// values of K, consumed by four MMAs of 32 bytes.
+template <bool F8>
 __global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant__ Gram2Params P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw;
@@ -1476,10 +1522,16 @@ __global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant_
   }
   const int tj = ti + t;
   const bool diag = ti == tj;
-  const long long d0 = P.D * (long long)blockIdx.y / P.splits;
-  const long long d1 = P.D * (long long)(blockIdx.y + 1) / P.splits;
-  const int nkb = (int)((P.n + 63) / 64);
-  const int ngroups = (int)((d1 - d0 + GFL - 1) / GFL);
+  // matrices split over the pairs by whole groups of GFL (a flush group is
+  // then a group of the FP8 scales)
+  const long long gtot = (P.D + GFL - 1) / GFL;
+  const long long g0 = gtot * (long long)blockIdx.y / P.splits;
+  const long long d0 = g0 * GFL;
+  const long long d1e = gtot * (long long)(blockIdx.y + 1) / P.splits * GFL;
+  const long long d1 = d1e < P.D ? d1e : P.D;
+  constexpr int KB = F8 ? 128 : 64;  // K values per 128-byte stage row
+  const int nkb = (int)((P.n + KB - 1) / KB);
+  const int ngroups = d1 > d0 ? (int)((d1 - d0 + GFL - 1) / GFL) : 0;
   if (tid == 0) {
     for (int s = 0; s < G2STG; ++s) {
       mbar_init(bar(G2_FULL + s), 1);   // the even CTA's expect-tx; bytes of both
@@ -1523,8 +1575,8 @@ __global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant_
           }
           const uint32_t full = mapa(bar(G2_FULL + s), 0);
           if (lead) mbar_expect_tx(bar(G2_FULL + s), diag ? 2 * G2HALF : 2 * G2STAGE);
-          tma_load_2d_pair(sb + s * G2STAGE, map, kb * 64, rowA, full);
-          if (!diag) tma_load_2d_pair(sb + s * G2STAGE + G2HALF, map, kb * 64, rowB, full);
+          tma_load_2d_pair(sb + s * G2STAGE, map, kb * KB, rowA, full);
+          if (!diag) tma_load_2d_pair(sb + s * G2STAGE + G2HALF, map, kb * KB, rowB, full);
         }
         if (stop) break;
       }
@@ -1535,7 +1587,7 @@ __global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant_
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lead && lane == 0) {
-      const uint32_t idesc = idesc_bf16(256, 256, 0, 0);
+      const uint32_t idesc = F8 ? idesc_e4m3(256, 256) : idesc_bf16(256, 256, 0, 0);
       long long q = 0;
       bool ok = true;
       for (int grp = 0; grp < ngroups && ok; ++grp) {
@@ -1557,9 +1609,15 @@ __global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant_
             tc_fence_after();
             const uint32_t a0 = sb + s * G2STAGE, b0 = diag ? a0 : a0 + G2HALF;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              tc_mma_pair(tmem + buf * 256, sdesc(a0 + kk * 32, 16, 1024),
-                          sdesc(b0 + kk * 32, 16, 1024), idesc, (first && kk == 0) ? 0u : 1u);
+            for (int kk = 0; kk < 4; ++kk) {
+              if (F8)
+                tc_mma_pair_f8(tmem + buf * 256, sdesc(a0 + kk * 32, 16, 1024),
+                               sdesc(b0 + kk * 32, 16, 1024), idesc,
+                               (first && kk == 0) ? 0u : 1u);
+              else
+                tc_mma_pair(tmem + buf * 256, sdesc(a0 + kk * 32, 16, 1024),
+                            sdesc(b0 + kk * 32, 16, 1024), idesc, (first && kk == 0) ? 0u : 1u);
+            }
             first = false;
             tc_commit_pair_mc(bar(G2_EMPTY + s));
           }
@@ -1590,10 +1648,14 @@ __global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant_
         if (row < P.m) {
           double* g = P.G + row * P.m + (long long)tj * 256 + c0;
           const long long cmax = P.m - ((long long)tj * 256 + c0);
+          // FP8: the group's row scale times the column's (powers of two)
+          const float* sc = F8 ? P.scales + (g0 + grp) * P.m : nullptr;
+          const double srow = F8 ? (double)sc[row] : 1.0;
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             if (i < cmax) {
-              const double x = (double)__uint_as_float(r[i]);
+              double x = (double)__uint_as_float(r[i]);
+              if (F8) x *= srow * (double)sc[(long long)tj * 256 + c0 + i];
               if (atomic)
                 atomicAdd(g + i, x);
               else
@@ -1673,7 +1735,7 @@ bool tc_matrix_eligible(const void* A, long long m, long long lda, int k) {
 
 bool gram_tc_eligible(int prec, int mode, const void* const* A, long long D, long long m,
                       long long n, long long lda) {
-  if (prec != 2 || mode != 1 || D < 1 || m < 1 || n < 1) return false;
+  if (prec != 2 || (mode != 1 && mode != 2) || D < 1 || m < 1 || n < 1) return false;
   if ((lda * 2) % 16 != 0 || lda > (1ll << 31) || n > (1ll << 31) || m > (1ll << 31))
     return false;
   for (long long d = 0; d < D; ++d)
@@ -1687,6 +1749,8 @@ bool gram_tc_eligible(int prec, int mode, const void* const* A, long long D, lon
 struct GramCache {
   std::vector<const void*> key;
   long long m = 0, n = 0, lda = 0;
+  int box_rows = 0;  // 128 for the mode-1 maps, 64 for mode 2
+  bool f8 = false;   // maps of E4M3 bytes (box 128 x 128)
   CUtensorMap* dmaps = nullptr;
   size_t cap = 0;
 };
@@ -1699,21 +1763,29 @@ void gram_cache_destroy(GramCache* c) {
 }
 
 cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long long n,
-                           long long lda, double* G, int* status, long long spin_limit,
-                           GramCache* cache, bool pairs, cudaStream_t s) {
+                           long long lda, int mode, double* G, int* status,
+                           long long spin_limit, GramCache* cache, bool pairs, cudaStream_t s,
+                           const float* f8_scales) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
-  if (!enc || !cache) return cudaErrorNotSupported;
+  const bool f8 = f8_scales != nullptr;
+  if (!enc || !cache || (mode != 1 && mode != 2) || (f8 && mode != 1)) return cudaErrorNotSupported;
+  if (mode == 2) pairs = false;  // the pair tiles read K-major rows only
+  if (f8) pairs = true;          // E4M3 operands: the pair kernel only
+  const int box_rows = mode == 1 ? 128 : 64;
+  const long long dim = mode == 1 ? m : n;
   const bool hit = cache->dmaps && cache->m == m && cache->n == n && cache->lda == lda &&
+                   cache->box_rows == box_rows && cache->f8 == f8 &&
                    (long long)cache->key.size() == D &&
                    std::equal(cache->key.begin(), cache->key.end(), A);
   if (!hit) {
     std::vector<CUtensorMap> maps((size_t)D);
     for (long long d = 0; d < D; ++d) {
       cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
-      cuuint64_t strides[1] = {(cuuint64_t)lda * 2};
-      cuuint32_t box[2] = {64, 128};
+      cuuint64_t strides[1] = {(cuuint64_t)lda * (f8 ? 1 : 2)};
+      cuuint32_t box[2] = {f8 ? 128u : 64u, (cuuint32_t)box_rows};
       cuuint32_t es[2] = {1, 1};
-      CUresult r = enc(&maps[(size_t)d], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+      CUresult r = enc(&maps[(size_t)d],
+                       f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                        const_cast<void*>(A[d]), dims, strides, box, es,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1738,6 +1810,8 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
     cache->m = m;
     cache->n = n;
     cache->lda = lda;
+    cache->box_rows = box_rows;
+    cache->f8 = f8;
   }
   int dev = 0, nsm = 148;
   if (cudaGetDevice(&dev) == cudaSuccess)
@@ -1750,7 +1824,8 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
     const long long ntp2 = (long long)ntile2 * (ntile2 + 1) / 2;
     if (2 * ntp2 > 2147483647ll) return cudaErrorNotSupported;
     long long splits2 = nsm / (2 * ntp2);
-    if (splits2 > D) splits2 = D;
+    const long long groups = (D + GFL - 1) / GFL;  // the pairs split whole groups
+    if (splits2 > groups) splits2 = groups;
     if (splits2 < 1) splits2 = 1;
     if (splits2 > 65535) splits2 = 65535;
     Gram2Params q;
@@ -1759,12 +1834,13 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
     q.m = m;
     q.n = n;
     q.G = G;
+    q.scales = f8_scales;
     q.ntile = ntile2;
     q.splits = (int)splits2;
     q.status = status;
     q.timeout_ns = std::max<long long>(spin_limit, 1) * 120;
-    e = cudaFuncSetAttribute(gram2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             G2_SMEM);
+    auto kern = f8 ? gram2_tc_kernel<true> : gram2_tc_kernel<false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G2_SMEM);
     if (e == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute attr[1];
@@ -1778,7 +1854,7 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      e = cudaLaunchKernelEx(&cfg, gram2_tc_kernel, q);
+      e = cudaLaunchKernelEx(&cfg, kern, q);
     }
     if (e == cudaSuccess) {
       const long long tot = m * m;
@@ -1787,13 +1863,14 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
     }
     return e;
   }
-  const int ntile = (int)((m + 127) / 128);
+  const int ntile = (int)((dim + 127) / 128);
   const long long ntp = (long long)ntile * (ntile + 1) / 2;
   if (ntp > 65535 * 8) return cudaErrorNotSupported;
   long long splits = nsm / ntp;
   if (splits > D) splits = D;
   if (splits < 1) splits = 1;
   GramParams prm;
+  prm.mode = mode;
   prm.tmaps = cache->dmaps;
   prm.D = D;
   prm.m = m;
@@ -1811,8 +1888,8 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    const long long tot = m * m;
-    mirror_upper_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(G, m);
+    const long long tot = dim * dim;
+    mirror_upper_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(G, dim);
     e = cudaGetLastError();
   }
   return e;

@@ -831,10 +831,11 @@ extern "C" tsk_status tsk_gram(tsk_handle h, const void* const* A, int64_t D,
   const int64_t dim = (mode == 1) ? m : n;
   if (!accumulate) TSK_CUDA(h, cudaMemsetAsync(G, 0, sizeof(double) * dim * dim, s));
   if (h->opts.kernel != TSK_KERNEL_SIMT && gram_tc_eligible((int)prec, mode, A, D, m, n, lda)) {
-    // BF16 mode 1: tcgen05 SYRK (FP32 in TMEM, FP64 in G); shapes whose
-    // tensor maps cannot be encoded go to the CUDA-core kernel below
+    // BF16: tcgen05 SYRK (FP32 in TMEM, FP64 in G), mode 1 on CTA pairs
+    // (or single CTAs with gram_tile = 1), mode 2 on single CTAs; shapes
+    // whose tensor maps cannot be encoded go to the CUDA-core kernel below
     const cudaError_t ge =
-        launch_gram_tc(A, D, m, n, lda, G, h->d_status, h->opts.spin_limit,
+        launch_gram_tc(A, D, m, n, lda, mode, G, h->d_status, h->opts.spin_limit,
                        h->gram_cache ? h->gram_cache : (h->gram_cache = gram_cache_create()),
                        h->opts.gram_tile == 0, s);
     if (ge != cudaErrorNotSupported) {
@@ -1866,5 +1867,74 @@ extern "C" tsk_status tsk_autotune_load(tsk_handle h, const char* path) {
   h->tune = table;
   h->tune_us.clear();
   ++h->tune_version;
+  return TSK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FP8 (E4M3) training Gram: quantization with per-(group, row) scales and the
+// tensor-core Gram of the E4M3 copies
+// ---------------------------------------------------------------------------
+extern "C" tsk_status tsk_quantize_e4m3(tsk_handle h, const void* const* A, int64_t D,
+                                        int64_t m, int64_t n, int64_t lda, tsk_prec prec,
+                                        void* const* A8, int64_t ld8, float* scales,
+                                        tsk_stream stream) {
+  if (!h) return TSK_EINVAL;
+  if (!A || !A8 || !scales || D < 1 || D > 65535 || m < 1 || n < 1 || lda < n || ld8 < n ||
+      (prec != TSK_FP32 && prec != TSK_BF16)) {
+    set_err(h, "tsk_quantize_e4m3: need A, A8, scales non-NULL, 1 <= D <= 65535, m, n >= 1, "
+               "lda >= n, ld8 >= n and TSK_FP32 or TSK_BF16 input");
+    return TSK_EINVAL;
+  }
+  for (int64_t d = 0; d < D; ++d)
+    if (!A[d] || !A8[d] || ((uintptr_t)A[d]) % elt_size(prec) != 0) {
+      set_err(h, "tsk_quantize_e4m3: A[%lld] or A8[%lld] is NULL or misaligned", (long long)d,
+              (long long)d);
+      return TSK_EINVAL;
+    }
+  cudaStream_t s = (cudaStream_t)stream;
+  void* dp = nullptr;
+  TSK_CUDA(h, cudaMallocAsync(&dp, 2 * sizeof(void*) * D, s));
+  std::vector<const void*> ptrs(2 * D);
+  for (int64_t d = 0; d < D; ++d) {
+    ptrs[d] = A[d];
+    ptrs[D + d] = A8[d];
+  }
+  TSK_CUDA(h, cudaMemcpyAsync(dp, ptrs.data(), 2 * sizeof(void*) * D, cudaMemcpyHostToDevice, s));
+  TSK_CUDA(h, launch_quantize_e4m3((int)prec, (const void* const*)dp, D, m, n, lda,
+                                   (unsigned char* const*)dp + D, ld8, scales, s));
+  TSK_CUDA(h, cudaFreeAsync(dp, s));
+  TSK_CUDA(h, cudaStreamSynchronize(s));  // the host pointer array must outlive the copy
+  return TSK_OK;
+}
+
+extern "C" tsk_status tsk_gram_e4m3(tsk_handle h, const void* const* A8, const float* scales,
+                                    int64_t D, int64_t m, int64_t n, int64_t ld8, double* G,
+                                    int32_t accumulate, tsk_stream stream) {
+  if (!h) return TSK_EINVAL;
+  if (!A8 || !scales || !G || D < 1 || m < 1 || n < 1 || ld8 < n || ld8 % 16 != 0) {
+    set_err(h, "tsk_gram_e4m3: need A8, scales, G non-NULL, D, m, n >= 1, ld8 >= n and a "
+               "multiple of 16");
+    return TSK_EINVAL;
+  }
+  for (int64_t d = 0; d < D; ++d)
+    if (!A8[d] || ((uintptr_t)A8[d]) % 16 != 0) {
+      set_err(h, "tsk_gram_e4m3: A8[%lld] is NULL or not 16-byte aligned", (long long)d);
+      return TSK_EINVAL;
+    }
+  if (!tc_supported()) {
+    set_err(h, "tsk_gram_e4m3: needs the tensor cores of a GB300");
+    return TSK_EUNSUPPORTED;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!accumulate) TSK_CUDA(h, cudaMemsetAsync(G, 0, sizeof(double) * m * m, s));
+  if (!h->gram_cache) h->gram_cache = gram_cache_create();
+  const cudaError_t ge = launch_gram_tc(A8, D, m, n, ld8, 1, G, h->d_status, h->opts.spin_limit,
+                                        h->gram_cache, true, s, scales);
+  if (ge == cudaErrorNotSupported) {
+    set_err(h, "tsk_gram_e4m3: tensor maps cannot be encoded for these shapes");
+    return TSK_EUNSUPPORTED;
+  }
+  TSK_CUDA(h, ge);
+  TSK_CUDA(h, cudaStreamSynchronize(s));
   return TSK_OK;
 }

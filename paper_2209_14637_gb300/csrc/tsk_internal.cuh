@@ -174,9 +174,21 @@ GramCache* gram_cache_create();
 void gram_cache_destroy(GramCache* c);
 // pairs: 256 x 256 tiles on CTA pairs (tcgen05 .cta_group::2); otherwise
 // 128 x 128 tiles on single CTAs.
+// mode 1: G (m x m) += sum A A^T; mode 2: G (n x n) += sum A^T A (MN-major
+// operands, 128 x 128 tiles on single CTAs).
+// f8_scales != NULL: A holds E4M3 bytes (lda in bytes, a multiple of 16)
+// with a power-of-two scale per row and group of eight matrices,
+// f8_scales[(d / 8) * m + i]; mode 1 only, on CTA pairs.
 cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long long n,
-                           long long lda, double* G, int* status, long long spin_limit,
-                           GramCache* cache, bool pairs, cudaStream_t s);
+                           long long lda, int mode, double* G, int* status,
+                           long long spin_limit, GramCache* cache, bool pairs, cudaStream_t s,
+                           const float* f8_scales = nullptr);
+// Quantizes D matrices (in_type 1 float, 2 bfloat16; host array of device
+// pointers) to E4M3 in A8[d] (ld8 bytes per row) with the per-(group of 8,
+// row) power-of-two scales that keep every |value| / scale <= 448.
+cudaError_t launch_quantize_e4m3(int in_type, const void* const* dA, long long D, long long m,
+                                 long long n, long long lda, unsigned char* const* dA8,
+                                 long long ld8, float* scales, cudaStream_t s);
 // Builds the tensor-core part of a plan for the matrices ids[0..nids) of
 // the plan's count matrices (tensor maps, S images, per-class schedules).
 // mc_pref (count entries, nullable): per matrix 0 (default shape), 256 or

@@ -225,6 +225,28 @@ def test_tc_gram_mode1(tsk, m, n, D, tile):
     h.close()
 
 
+@pytest.mark.parametrize("m,n,D", [(200, 320, 11), (2048, 256, 20), (64, 128, 3),
+                                   (72, 300, 40), (96, 2048, 3)])
+def test_tc_gram_mode2(tsk, m, n, D):
+    """T1' on the tensor cores: G2 = sum A_d^T A_d (n x n) with MN-major
+    operands (columns of A along M, rows along K) against the FP64 oracle
+    on the same stored values, entrywise: ragged n (partial 128-wide tiles)
+    and m (a partial 64-row K slice), splits over CTAs or not, several flush
+    groups, n = 2048 (many tiles)."""
+    g = torch.Generator(device="cuda").manual_seed(7 * m + n + D)
+    T = [torch.randn(m, n, generator=g, device="cuda").to(torch.bfloat16) for _ in range(D)]
+    h = tsk.Handle()
+    G = _np(h.gram(T, mode=2))
+    assert h.sync_status() == 0
+    R = oracle.gram_mode2([_np(t) for t in T])
+    _gram_entrywise(G, R, 1e-5)
+    assert np.array_equal(G, G.T)
+    Gs = h.gram(T[:2], mode=2)
+    h.gram(T[2:], mode=2, out=Gs, accumulate=True)
+    _gram_entrywise(_np(Gs), R, 1e-5)
+    h.close()
+
+
 def _gram_entrywise(G, R, tol):
     """|G_ij - R_ij| <= tol sqrt(R_ii R_jj) for every entry (Cauchy-Schwarz
     scale of the entry)."""
@@ -333,3 +355,43 @@ def test_expired_waits_report_a_timeout_and_leave_the_context_usable(tsk):
     o = oracle.scw(_np(A), _np(S), 8, dense=False)
     assert abs(float(out["err"][0]) - o["err"]) <= GAP * o["err"]
     h2.close()
+
+
+def _dequant(A8, scales, n):
+    """The values an E4M3 copy stands for: byte decoded by torch's float8
+    type, times the (group, row) scale."""
+    D, m, _ = A8.shape
+    vals = A8[:, :, :n].cpu().view(torch.float8_e4m3fn).to(torch.float64)
+    s = scales.cpu().to(torch.float64).repeat_interleave(8, dim=0)[:D]
+    return vals * s[:, :, None]
+
+
+@pytest.mark.parametrize("m,n,D", [(320, 200, 11), (2048, 256, 20), (130, 64, 3)])
+def test_e4m3_quantization_and_gram(tsk, m, n, D):
+    """FP8 training Gram: the quantizer's scales are the smallest powers of
+    two keeping |A| / scale <= 448 per (group of eight, row), its bytes are
+    E4M3 rounding of A / scale (torch's own conversion, bit for bit), and the
+    tensor-core Gram of the E4M3 copies (kind::f8f6f4 on CTA pairs) equals
+    the oracle's FP64 Gram of the values they stand for, entrywise."""
+    g = torch.Generator(device="cuda").manual_seed(m + 3 * n + D)
+    rows = torch.logspace(-3, 3, m, device="cuda")[:, None]  # rows of very unequal size
+    T = [(torch.randn(m, n, generator=g, device="cuda") * rows).to(torch.bfloat16)
+         for _ in range(D)]
+    h = tsk.Handle()
+    A8, scales = h.quantize_e4m3(T)
+    torch.cuda.synchronize()
+    sc = scales.cpu().double()
+    assert torch.all(torch.log2(sc) == torch.round(torch.log2(sc)))
+    Ad = torch.stack([t.double().cpu() for t in T])
+    for gi in range(sc.shape[0]):
+        mx = Ad[8 * gi:8 * gi + 8].abs().amax(dim=(0, 2))
+        assert torch.all(mx / sc[gi] < 448) and torch.all(mx / sc[gi] >= 224)
+    s_full = sc.repeat_interleave(8, dim=0)[:D]
+    ref = (Ad / s_full[:, :, None]).to(torch.float32).to(torch.float8_e4m3fn)
+    assert torch.equal(A8[:, :, :n].cpu(), ref.view(torch.uint8))
+    G = _np(h.gram_e4m3(A8, scales, n))
+    assert h.sync_status() == 0
+    R = oracle.gram_mode1(list(_dequant(A8, scales, n).numpy()))
+    _gram_entrywise(G, R, 1e-5)
+    assert np.array_equal(G, G.T)
+    h.close()
