@@ -249,29 +249,38 @@ def _sgemm_peak():
         torch.backends.cuda.matmul.allow_tf32 = prev
 
 
+def device_median_ms(fn, reps):
+    """Median over `reps` calls of fn's time between CUDA events on the
+    current stream."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return sorted(ts)[len(ts) // 2]
+
+
 def fp8_training_gram(tsk, h, tr, G_bf16, k, peaks, peak_src):
     """The training Gram from E4M3 copies (per-row, per-8-matrix power-of-two
-    scales): quantisation and Gram timed on the device, the Gram against
+    scales): quantisation (into buffers allocated once; the call's host-side
+    pointer copy and stream synchronisation included) and Gram timed on the
+    device, the Gram against
     twice the measured BF16 peak (the nominal FP8 / BF16 tensor ratio), and
     the sketch it gives scored on the BF16 Gram: the fraction of the best
     captured energy trace(S G S^T) (Eq. 3.2) that it keeps."""
     import torch
     D, m, n = tr.shape
     mats = [tr[i] for i in range(D)]
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    ev[0].record()
     A8, scales = h.quantize_e4m3(mats)
-    ev[1].record()
-    G8 = h.gram_e4m3(A8, scales, n)
-    ev[2].record()
+    G8 = h.gram_e4m3(A8, scales, n)  # encodes and caches the tensor maps
     torch.cuda.synchronize()
-    ev[0].record()  # once more, with the tensor maps cached
-    A8, scales = h.quantize_e4m3(mats)
-    ev[1].record()
-    G8 = h.gram_e4m3(A8, scales, n, out=G8)
-    ev[2].record()
-    torch.cuda.synchronize()
-    q_ms, g_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    q_ms = device_median_ms(lambda: h.quantize_e4m3(mats, out=(A8, scales)), 3)
+    g_ms = device_median_ms(lambda: h.gram_e4m3(A8, scales, n, out=G8), 3)
     flops = float(m) ** 2 * n * D
     tf = flops / (g_ms / 1e3) / 1e12
     peak = 2.0 * float(peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]))
@@ -282,7 +291,12 @@ def fp8_training_gram(tsk, h, tr, G_bf16, k, peaks, peak_src):
     capb = float(torch.trace(Sb.double() @ Gd @ Sb.double().T))
     rel = float((G8 - Gd).abs().max() / Gd.diagonal().max())
     del A8, scales, G8
+    qbytes = float(D) * m * n * (tr.element_size() + 1)  # A read once, E4M3 written
+    qgbs = qbytes / (q_ms / 1e3) / 1e9
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     return {"quantize_ms": q_ms, "gram_ms": g_ms, "status": [st8, stb],
+            "quantize_roofline": {"bound": "hbm", "achieved": qgbs, "peak": hbm, "unit": "GB/s",
+                                  "frac": qgbs / hbm, "bytes": qbytes},
             "gram_max_abs_diff_over_max_diag": rel,
             "captured_energy_vs_bf16_gram": cap8 / capb,
             "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
@@ -333,13 +347,8 @@ def run_tsk(args):
     # the Gram (T1) once more, timed on the device (its tensor maps are
     # cached by the handle, so this is the kernel's time): a tensor-bound
     # SYRK of m^2 n multiply-adds' worth of flops per matrix (half of 2 m^2 n)
-    g0 = torch.cuda.Event(enable_timing=True)
-    g1 = torch.cuda.Event(enable_timing=True)
-    g0.record()
-    h.gram([tr[i] for i in range(tr.shape[0])], mode=1, out=G)
-    g1.record()
-    torch.cuda.synchronize()
-    gram_ms = g0.elapsed_time(g1)
+    mats = [tr[i] for i in range(tr.shape[0])]
+    gram_ms = device_median_ms(lambda: h.gram(mats, mode=1, out=G), 3)
     gram_flops = float(spec.m) ** 2 * spec.n * (b - a)
     gram_tf = gram_flops / (gram_ms / 1e3) / 1e12
     gpeak = float(peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]))

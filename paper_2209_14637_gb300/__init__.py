@@ -212,18 +212,24 @@ class Handle:
                                        _stream(stream)))
         return out
 
-    def quantize_e4m3(self, As, stream=None):
+    def quantize_e4m3(self, As, out=None, stream=None):
         """E4M3 copies of FP32 / BF16 training matrices with one power-of-two
         scale per row and group of eight matrices.  Returns (A8 uint8 of
         shape (D, m, ld8) with ld8 = n rounded up to 16, scales float32 of
-        shape (ceil(D / 8), m))."""
+        shape (ceil(D / 8), m)); `out` = such a pair from an earlier call
+        with the same shapes is written in place."""
         mats = [As[i] for i in range(As.shape[0])] if isinstance(As, torch.Tensor) else list(As)
         _require_cuda(*mats)
         m, n = mats[0].shape
         D = len(mats)
         ld8 = (n + 15) // 16 * 16
-        A8 = torch.zeros(D, m, ld8, dtype=torch.uint8, device=mats[0].device)
-        scales = torch.empty((D + 7) // 8, m, dtype=torch.float32, device=mats[0].device)
+        if out is None:
+            A8 = torch.zeros(D, m, ld8, dtype=torch.uint8, device=mats[0].device)
+            scales = torch.empty((D + 7) // 8, m, dtype=torch.float32, device=mats[0].device)
+        else:
+            A8, scales = out
+            if tuple(A8.shape) != (D, m, ld8) or tuple(scales.shape) != ((D + 7) // 8, m):
+                raise ValueError("out does not have the shapes of these matrices")
         src = (C.c_void_p * D)(*[a.data_ptr() for a in mats])
         dst = (C.c_void_p * D)(*[A8[d].data_ptr() for d in range(D)])
         self._check(self._lib.tsk_quantize_e4m3(self._h, src, D, m, n, mats[0].stride(0),

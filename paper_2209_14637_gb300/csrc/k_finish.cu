@@ -104,6 +104,23 @@ __device__ __forceinline__ void st4(float* p, float a, float b, float c, float d
   *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
 }
 
+// Two FP32 operations in one instruction (fma / mul .rn.f32x2): lane 0 and
+// lane 1 of each pair, each rounded as fmaf / __fmul_rn would round it.
+__device__ __forceinline__ void ffma2(float& d0, float& d1, float a0, float a1, float b0,
+                                      float b1) {
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rd, {%0, %1};\n\tfma.rn.f32x2 rd, ra, rb, rd;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "+f"(d0), "+f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void fmul2(float& d0, float& d1, float a0, float a1, float b0,
+                                      float b1) {
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
 __device__ __forceinline__ void cp16(float* dst, const float* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
 }
@@ -205,22 +222,14 @@ __device__ __forceinline__ void fin_stream(const FinLay& L, float* sm, int kc, i
             const float* rr = RI + (4 * q) * kc + 4 * c;
             const float4 e0 = ld4(rr), e1 = ld4(rr + kc), e2 = ld4(rr + 2 * kc),
                          e3 = ld4(rr + 3 * kc);
-            t0 = fmaf(p.x, e0.x, t0);
-            t1 = fmaf(p.x, e0.y, t1);
-            t2 = fmaf(p.x, e0.z, t2);
-            t3 = fmaf(p.x, e0.w, t3);
-            t0 = fmaf(p.y, e1.x, t0);
-            t1 = fmaf(p.y, e1.y, t1);
-            t2 = fmaf(p.y, e1.z, t2);
-            t3 = fmaf(p.y, e1.w, t3);
-            t0 = fmaf(p.z, e2.x, t0);
-            t1 = fmaf(p.z, e2.y, t1);
-            t2 = fmaf(p.z, e2.z, t2);
-            t3 = fmaf(p.z, e2.w, t3);
-            t0 = fmaf(p.w, e3.x, t0);
-            t1 = fmaf(p.w, e3.y, t1);
-            t2 = fmaf(p.w, e3.z, t2);
-            t3 = fmaf(p.w, e3.w, t3);
+            ffma2(t0, t1, p.x, p.x, e0.x, e0.y);
+            ffma2(t2, t3, p.x, p.x, e0.z, e0.w);
+            ffma2(t0, t1, p.y, p.y, e1.x, e1.y);
+            ffma2(t2, t3, p.y, p.y, e1.z, e1.w);
+            ffma2(t0, t1, p.z, p.z, e2.x, e2.y);
+            ffma2(t2, t3, p.z, p.z, e2.z, e2.w);
+            ffma2(t0, t1, p.w, p.w, e3.x, e3.y);
+            ffma2(t2, t3, p.w, p.w, e3.z, e3.w);
           }
           st4(trow + 4 * c, t0, t1, t2, t3);
         }
@@ -237,9 +246,10 @@ __device__ __forceinline__ void fin_stream(const FinLay& L, float* sm, int kc, i
         const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
         const float yv[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < 8; a += 2)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(xv[a], yv[c], acc[a][c]);
+          for (int c = 0; c < 4; ++c)
+            ffma2(acc[a][c], acc[a + 1][c], xv[a], xv[a + 1], yv[c], yv[c]);
       }
     }
     cp_wait<NST - 2>();  // this thread's pieces of block bi + 1 have landed
@@ -481,12 +491,16 @@ __device__ void fin_eigen(const MatDev& md, int k, int r, int kc, int gld, int g
           y[i + 2] = v.z;
           y[i + 3] = v.w;
         }
+        float aa1 = 0.f, pp1 = 0.f, ap1 = 0.f;  // odd rows
 #pragma unroll
-        for (int i = 0; i < QMAX; ++i) {
-          aa = fmaf(bc[i], bc[i], aa);
-          pp = fmaf(y[i], y[i], pp);
-          ap = fmaf(bc[i], y[i], ap);
+        for (int i = 0; i < QMAX; i += 2) {
+          ffma2(aa, aa1, bc[i], bc[i + 1], bc[i], bc[i + 1]);
+          ffma2(pp, pp1, y[i], y[i + 1], y[i], y[i + 1]);
+          ffma2(ap, ap1, bc[i], bc[i + 1], y[i], y[i + 1]);
         }
+        aa += aa1;
+        pp += pp1;
+        ap += ap1;
         aa += __shfl_xor_sync(gmask, aa, 1);
         pp += __shfl_xor_sync(gmask, pp, 1);
         ap += __shfl_xor_sync(gmask, ap, 1);
@@ -510,7 +524,13 @@ __device__ void fin_eigen(const MatDev& md, int k, int r, int kc, int gld, int g
           // [b_p b_q] <- [c b_p - s b_q, s b_p + c b_q]
           const float cp = low ? -sn : sn;
 #pragma unroll
-          for (int i = 0; i < QMAX; ++i) bc[i] = fmaf(cs, bc[i], cp * y[i]);
+          for (int i = 0; i < QMAX; i += 2) {
+            float u0, u1;
+            fmul2(u0, u1, cp, cp, y[i], y[i + 1]);
+            ffma2(u0, u1, cs, cs, bc[i], bc[i + 1]);
+            bc[i] = u0;
+            bc[i + 1] = u1;
+          }
           rot |= meas > 2.0e-3f;
         }
       }

@@ -1891,6 +1891,12 @@ extern "C" tsk_status tsk_quantize_e4m3(tsk_handle h, const void* const* A, int6
               (long long)d);
       return TSK_EINVAL;
     }
+  // 16-byte loads and 8-byte (BF16) or 4-byte (FP32) stores where every
+  // row of every matrix starts aligned for them
+  const int per = prec == TSK_BF16 ? 8 : 4;
+  bool vec = (lda * elt_size(prec)) % 16 == 0 && ld8 % per == 0;
+  for (int64_t d = 0; d < D && vec; ++d)
+    vec = ((uintptr_t)A[d]) % 16 == 0 && ((uintptr_t)A8[d]) % per == 0;
   cudaStream_t s = (cudaStream_t)stream;
   void* dp = nullptr;
   TSK_CUDA(h, cudaMallocAsync(&dp, 2 * sizeof(void*) * D, s));
@@ -1901,7 +1907,7 @@ extern "C" tsk_status tsk_quantize_e4m3(tsk_handle h, const void* const* A, int6
   }
   TSK_CUDA(h, cudaMemcpyAsync(dp, ptrs.data(), 2 * sizeof(void*) * D, cudaMemcpyHostToDevice, s));
   TSK_CUDA(h, launch_quantize_e4m3((int)prec, (const void* const*)dp, D, m, n, lda,
-                                   (unsigned char* const*)dp + D, ld8, scales, s));
+                                   (unsigned char* const*)dp + D, ld8, scales, vec, s));
   TSK_CUDA(h, cudaFreeAsync(dp, s));
   TSK_CUDA(h, cudaStreamSynchronize(s));  // the host pointer array must outlive the copy
   return TSK_OK;

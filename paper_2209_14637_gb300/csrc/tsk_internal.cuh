@@ -188,7 +188,7 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
 // row) power-of-two scales that keep every |value| / scale <= 448.
 cudaError_t launch_quantize_e4m3(int in_type, const void* const* dA, long long D, long long m,
                                  long long n, long long lda, unsigned char* const* dA8,
-                                 long long ld8, float* scales, cudaStream_t s);
+                                 long long ld8, float* scales, bool vec, cudaStream_t s);
 // Builds the tensor-core part of a plan for the matrices ids[0..nids) of
 // the plan's count matrices (tensor maps, S images, per-class schedules).
 // mc_pref (count entries, nullable): per matrix 0 (default shape), 256 or

@@ -366,8 +366,15 @@ def _dequant(A8, scales, n):
     return vals * s[:, :, None]
 
 
-@pytest.mark.parametrize("m,n,D", [(320, 200, 11), (2048, 256, 20), (130, 64, 3)])
-def test_e4m3_quantization_and_gram(tsk, m, n, D):
+@pytest.mark.parametrize("m,n,D,dtype,lda", [
+    (320, 200, 11, torch.bfloat16, 200),   # 16-byte rows: vector loads
+    (2048, 256, 20, torch.bfloat16, 256),
+    (130, 64, 3, torch.bfloat16, 64),
+    (150, 100, 9, torch.bfloat16, 100),    # 200-byte rows: scalar loads
+    (96, 203, 10, torch.float32, 208),     # FP32, padded rows: vectors and a 3-wide tail
+    (64, 77, 17, torch.float32, 77),       # FP32, scalar
+])
+def test_e4m3_quantization_and_gram(tsk, m, n, D, dtype, lda):
     """FP8 training Gram: the quantizer's scales are the smallest powers of
     two keeping |A| / scale <= 448 per (group of eight, row), its bytes are
     E4M3 rounding of A / scale (torch's own conversion, bit for bit), and the
@@ -375,8 +382,8 @@ def test_e4m3_quantization_and_gram(tsk, m, n, D):
     the oracle's FP64 Gram of the values they stand for, entrywise."""
     g = torch.Generator(device="cuda").manual_seed(m + 3 * n + D)
     rows = torch.logspace(-3, 3, m, device="cuda")[:, None]  # rows of very unequal size
-    T = [(torch.randn(m, n, generator=g, device="cuda") * rows).to(torch.bfloat16)
-         for _ in range(D)]
+    buf = (torch.randn(D, m, lda, generator=g, device="cuda") * rows).to(dtype)
+    T = [buf[d, :, :n] for d in range(D)]
     h = tsk.Handle()
     A8, scales = h.quantize_e4m3(T)
     torch.cuda.synchronize()
