@@ -66,13 +66,22 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # nvidia-smi takes a moment to start: wait for its first sample, so
+        # that the samples kept (those that arrive between mark() and stop())
+        # fall inside the timed region
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+
+    def mark(self):
+        self.first = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -81,6 +90,7 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return None
+        last = len(self.lines)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -91,7 +101,8 @@ class ClockSampler:
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
                  "sw_power_cap"]
-        for ln in self.lines:
+        kept = self.lines[getattr(self, "first", 0):last]
+        for ln in kept:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -390,6 +401,7 @@ def run_tsk(args):
     stage(f"timing the BF16 path (refine {args.refine})")
     clocks = ClockSampler(local)
     clocks.start()
+    clocks.mark()
     total_ms, stage_ms = _timed_plan(plan, args.steps, ws, dist)
     clk = clocks.stop()
     assert h.sync_status() == 0
@@ -822,7 +834,7 @@ def main():
     faulthandler.dump_traceback_later(600, repeat=True)
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="tsk", choices=["tsk", "reference"])
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 simt, 2 tcgen05")
