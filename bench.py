@@ -784,7 +784,9 @@ def run_extra_workloads(args, tsk, h, sgemm, peaks, ws, dist, rank):
         key = "padded_rows" if pad else "contiguous_rows"
         c4[key] = {"value": v4, "ms_per_step": ms4, "sketch_pass_ms": sk4,
                    "launches": inf4["launches"],
-                   "tensor_core_matrices": sum((A.stride(0) * 2) % 16 == 0 for A in A4),
+                   "tensor_core_matrices": sum(it.m <= 4096 and it.k <= 48 for it in items),
+                   "copied_to_aligned_rows": sum((A.stride(0) * 2) % 16 != 0
+                                                 or A.data_ptr() % 16 != 0 for A in A4),
                    "roofline": {"bound": "hbm", "achieved": alg4 / (sk4 / 1e3) / 1e9,
                                 "peak": peak_hbm, "unit": "GB/s",
                                 "frac": alg4 / (sk4 / 1e3) / 1e9 / peak_hbm,

@@ -36,12 +36,16 @@
  *   - Requirements on sizes: 1 <= r <= k <= min(m, n) (thin QR of the n x k
  *     matrix (SA)^T needs k <= n; Theorem 1 needs k > r for its bound but
  *     r = k is accepted) and k <= TSK_MAX_K.  The tensor-core sketch of a
- *     BF16 matrix also needs k <= 48, m <= 4096, a 16-byte aligned A and
- *     lda * 2 a multiple of 16 bytes (TMA moves rows that start on 16-byte
- *     boundaries); with TSK_KERNEL_AUTO the BF16 matrices of a batch that
- *     miss one of these go to the CUDA-core sketch kernels, in the same
- *     plan and concurrently with the rest.  The CUDA-core paths need only
- *     natural alignment.
+ *     BF16 matrix also needs k <= 48 and m <= 4096.  TMA moves rows that
+ *     start on 16-byte boundaries: a matrix whose A is not 16-byte aligned
+ *     or whose lda * 2 is not a multiple of 16 is copied, at every
+ *     execution of its plan, to rows of ceil(n / 8) * 8 elements in the
+ *     plan's workspace (2 m ceil(n / 8) * 8 bytes more workspace; one more
+ *     read and write of A), and the tensor-core kernel reads the copy.
+ *     With TSK_KERNEL_AUTO the BF16 matrices of a batch with k > 48 or
+ *     m > 4096 go to the CUDA-core sketch kernels, in the same plan and
+ *     concurrently with the rest; TSK_KERNEL_SIMT sends every matrix there
+ *     and copies nothing.  The CUDA-core paths need only natural alignment.
  */
 #ifndef TSK_H_
 #define TSK_H_
@@ -70,7 +74,7 @@ typedef enum { TSK_FP64 = 0, TSK_FP32 = 1, TSK_BF16 = 2 } tsk_prec;
 
 /* Which kernels run the test-side sketch pass (X = A^T S^T and Y = A X). */
 typedef enum {
-  TSK_KERNEL_AUTO = 0, /* tensor cores for TSK_BF16 when eligible, else SIMT */
+  TSK_KERNEL_AUTO = 0, /* tensor cores for TSK_BF16 when k, m allow, else SIMT */
   TSK_KERNEL_SIMT = 1, /* CUDA-core kernels, two passes over A               */
   TSK_KERNEL_TC = 2    /* tcgen05/TMA kernel, one pass over A (TSK_BF16 only) */
 } tsk_kernel;

@@ -104,23 +104,6 @@ __device__ __forceinline__ void st4(float* p, float a, float b, float c, float d
   *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
 }
 
-// Two FP32 operations in one instruction (fma / mul .rn.f32x2): lane 0 and
-// lane 1 of each pair, each rounded as fmaf / __fmul_rn would round it.
-__device__ __forceinline__ void ffma2(float& d0, float& d1, float a0, float a1, float b0,
-                                      float b1) {
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "mov.b64 rd, {%0, %1};\n\tfma.rn.f32x2 rd, ra, rb, rd;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "+f"(d0), "+f"(d1)
-      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
-}
-__device__ __forceinline__ void fmul2(float& d0, float& d1, float a0, float a1, float b0,
-                                      float b1) {
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d0), "=f"(d1)
-      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
-}
-
 __device__ __forceinline__ void cp16(float* dst, const float* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
 }
@@ -143,11 +126,14 @@ struct FinPass {
 };
 
 // The area is free on entry (a barrier precedes its reuse); a target in the
-// area is written only after the last block.
-__device__ __forceinline__ void fin_stream(const FinLay& L, float* sm, int kc, int kp,
-                                           const FinPass& S, bool tr) {
+// area is written only after the last block.  The panel width KC (k rounded
+// up to 8) is a compile-time constant, so that the block loops unroll.
+template <int KC>
+__device__ __forceinline__ void fin_stream_kc(const FinLay& L, float* sm, int kp, const FinPass& S,
+                                           bool tr) {
+  constexpr int kc = KC;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int srow = kc + 4, ldo = kc + 1, n4 = kc / 4;
+  constexpr int srow = kc + 4, ldo = kc + 1, n4 = kc / 4;
   float* area = sm + L.area;
   float* Ts = area + NST * L.stage;
   const float* RI = sm + L.ri;
@@ -178,9 +164,10 @@ __device__ __forceinline__ void fin_stream(const FinLay& L, float* sm, int kc, i
   for (int bi = 0; bi < NST - 1; ++bi) issue(bi);
   // Gram tiles (ty, tx) of 8 rows x 4 columns meeting the upper triangle
   // (tx >= 2 ty); `groups` row groups share each tile.
-  const int n8 = kc / 8;
-  const int ntiles = n8 * n4 - n8 * (n8 - 1);  // sum over ty of (n4 - 2 ty)
-  const int groups = max(1, min(FT / ntiles, 8));
+  constexpr int n8 = kc / 8;
+  constexpr int ntiles = n8 * n4 - n8 * (n8 - 1);  // sum over ty of (n4 - 2 ty)
+  constexpr int groups = FT / ntiles < 1 ? 1 : (FT / ntiles > 8 ? 8 : FT / ntiles);
+  constexpr int per = (FSB + groups - 1) / groups;  // rows of a block per row group
   const bool active = tid < groups * ntiles;
   const int tile = tid % ntiles, grp = tid / ntiles;
   int ty = 0, rem = tile;
@@ -189,7 +176,7 @@ __device__ __forceinline__ void fin_stream(const FinLay& L, float* sm, int kc, i
     ++ty;
   }
   const int tx = 2 * ty + rem;
-  const int npairs = n4 / 2;
+  constexpr int npairs = n4 / 2;
   float acc[8][4];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
@@ -216,8 +203,9 @@ __device__ __forceinline__ void fin_stream(const FinLay& L, float* sm, int kc, i
         for (int h = 0; h < 2; ++h) {
           const int c = h ? c2 : cg;
           float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
-#pragma unroll 2
-          for (int q = 0; q <= c; ++q) {
+#pragma unroll
+          for (int q = 0; q < n4; ++q) {
+            if (q > c) break;
             const float4 p = ld4(prow + 4 * q);
             const float* rr = RI + (4 * q) * kc + 4 * c;
             const float4 e0 = ld4(rr), e1 = ld4(rr + kc), e2 = ld4(rr + 2 * kc),
@@ -238,8 +226,10 @@ __device__ __forceinline__ void fin_stream(const FinLay& L, float* sm, int kc, i
       src = Ts;
     }
     if (active) {
-#pragma unroll 2
-      for (int ii = grp; ii < nrows; ii += groups) {
+#pragma unroll
+      for (int t = 0; t < per; ++t) {
+        const int ii = grp + t * groups;
+        if (ii >= nrows) break;
         const float4 x0 = ld4(src + ii * srow + 8 * ty);
         const float4 x1 = ld4(src + ii * srow + 8 * ty + 4);
         const float4 y = ld4(src + ii * srow + 4 * tx);
@@ -277,6 +267,7 @@ __device__ __forceinline__ void fin_stream(const FinLay& L, float* sm, int kc, i
   }
   cp_wait<0>();
 }
+
 
 // Cholesky of the upper triangle of G (k x k, row stride ld) in place, right
 // looking: at step j, thread (a0, c) = (t / 64, t % 64) updates entries
@@ -639,21 +630,23 @@ __device__ void fin_eigen(const MatDev& md, int k, int r, int kc, int gld, int g
   __syncthreads();
 }
 
-// One CTA per matrix; QMAX = fin_quarter(kcm).  refine: 0 never, 1 always,
+// One CTA per matrix of a class (ids); KC = k rounded up to 8 for every
+// matrix of the class, QMAX = fin_quarter(KC).  refine: 0 never, 1 always,
 // 2 when est > 1e-3 (||A||^2 - energy) after the unrefined pass.
-template <int QMAX>
+template <int KC>
 __global__ void __launch_bounds__(FT, 4)
-finish_kernel(FinLay L, int kp, const MatDev* __restrict__ mats,
+finish_kernel(FinLay L, int kp, const int* __restrict__ ids, const MatDev* __restrict__ mats,
               const PanelDev* __restrict__ xpanels, const PanelDev* __restrict__ ypanels,
               float* __restrict__ Wm, const double* __restrict__ normA2,
               double* __restrict__ err, int* __restrict__ flags, int err_mode, double tau,
               int refine, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sm = (float*)smem_raw;
-  const int b = blockIdx.x, tid = threadIdx.x;
+  constexpr int QMAX = fin_quarter(KC);
+  const int b = ids[blockIdx.x], tid = threadIdx.x;
   const MatDev md = mats[b];
   const int k = md.k, r = md.r;
-  const int kc = (k + 7) & ~7, gld = kc + 1, g4 = (kc * gld + 3) & ~3;
+  constexpr int kc = KC, gld = kc + 1, g4 = (kc * gld + 3) & ~3;
   const PanelDev px = xpanels[b], py = ypanels[b];
   float* RI = sm + L.ri;
   float* GA = sm + L.ga;
@@ -671,7 +664,7 @@ finish_kernel(FinLay L, int kp, const MatDev* __restrict__ mats,
   ps.rows1 = 0;
   ps.out1 = nullptr;
   ps.nseg = 1;
-  fin_stream(L, sm, kc, kp, ps, false);
+  fin_stream_kc<KC>(L, sm, kp, ps, false);
   for (int i = tid; i < k; i += FT) DX[i] = sqrtf(fmaxf(GA[i * gld + i], 0.f));
   fin_chol(GA, gld, k, DV, true, status);
   fin_rinv(GA, gld, DV, k, kc, RI);
@@ -682,13 +675,13 @@ finish_kernel(FinLay L, int kp, const MatDev* __restrict__ mats,
     ps.rows1 = py.rows;
     ps.out1 = GB;
     ps.nseg = 2;  // Q1 = X R1^{-1}: Gram into GA; M1 = Y R1^{-1}: Gram into GB
-    fin_stream(L, sm, kc, kp, ps, true);
+    fin_stream_kc<KC>(L, sm, kp, ps, true);
     fin_refine(GA, GB, GA, RI, area, DV, k, kc, gld, g4, status);
   } else {
     ps.P0 = (const float*)py.P;
     ps.rows0 = py.rows;
     ps.out0 = GA;  // M1 = Y R1^{-1}
-    fin_stream(L, sm, kc, kp, ps, true);
+    fin_stream_kc<KC>(L, sm, kp, ps, true);
   }
   // ---- eigenpairs, W, energy; one refinement afterwards if the bound asks
   for (int pass = 0;; ++pass) {
@@ -700,7 +693,7 @@ finish_kernel(FinLay L, int kp, const MatDev* __restrict__ mats,
     ps.rows0 = px.rows;
     ps.out0 = GB;  // Q1 = X R1^{-1}
     ps.nseg = 1;
-    fin_stream(L, sm, kc, kp, ps, true);
+    fin_stream_kc<KC>(L, sm, kp, ps, true);
     fin_refine(GB, GA, GA, RI, area, DV, k, kc, gld, g4, status);
   }
   // ---- outputs: W (kp x kp, zero outside k x r), err, flags
@@ -717,43 +710,46 @@ finish_kernel(FinLay L, int kp, const MatDev* __restrict__ mats,
   }
 }
 
-template <int QMAX>
-cudaError_t launch_finish_t(int kp, int kcm, const MatDev* mats, int count,
+template <int KC>
+cudaError_t launch_finish_t(int kp, const int* ids, int count, const MatDev* mats,
                             const PanelDev* xpanels, const PanelDev* ypanels, float* Wm,
                             double* normA2, double* err, int* flags, int err_mode, double tau,
                             int refine, int* status, cudaStream_t s) {
-  const FinLay L = fin_layout(kcm);
-  cudaError_t e = cudaFuncSetAttribute(finish_kernel<QMAX>,
+  const FinLay L = fin_layout(KC);
+  cudaError_t e = cudaFuncSetAttribute(finish_kernel<KC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
   if (e != cudaSuccess) return e;
-  finish_kernel<QMAX><<<count, FT, L.bytes, s>>>(L, kp, mats, xpanels, ypanels, Wm, normA2, err,
-                                                 flags, err_mode, tau, refine, status);
+  finish_kernel<KC><<<count, FT, L.bytes, s>>>(L, kp, ids, mats, xpanels, ypanels, Wm, normA2,
+                                               err, flags, err_mode, tau, refine, status);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_finish(int kp, int kmax, const MatDev* mats, int count,
+cudaError_t launch_finish(int kp, int kc, const int* ids, int count, const MatDev* mats,
                           const PanelDev* xpanels, const PanelDev* ypanels, float* Wm,
                           double* normA2, double* err, int* flags, int err_mode, double tau,
                           int refine, int* status, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  if (kp % 16 != 0 || kp > TSK_MAX_K || kmax > kp || kmax < 1) return cudaErrorInvalidValue;
-  const int kcm = (kmax + 7) & ~7;
-  switch (fin_quarter(kcm)) {
-    case 4:
-      return launch_finish_t<4>(kp, kcm, mats, count, xpanels, ypanels, Wm, normA2, err, flags,
+  if (kp % 16 != 0 || kp > TSK_MAX_K || kc > kp || kc < 8 || kc % 8 != 0)
+    return cudaErrorInvalidValue;
+#define TSK_FIN_CASE(KCV)                                                                   \
+  case KCV:                                                                                 \
+    return launch_finish_t<KCV>(kp, ids, count, mats, xpanels, ypanels, Wm, normA2, err, flags, \
                                 err_mode, tau, refine, status, s);
-    case 8:
-      return launch_finish_t<8>(kp, kcm, mats, count, xpanels, ypanels, Wm, normA2, err, flags,
-                                err_mode, tau, refine, status, s);
-    case 12:
-      return launch_finish_t<12>(kp, kcm, mats, count, xpanels, ypanels, Wm, normA2, err, flags,
-                                 err_mode, tau, refine, status, s);
+  switch (kc) {
+    TSK_FIN_CASE(8)
+    TSK_FIN_CASE(16)
+    TSK_FIN_CASE(24)
+    TSK_FIN_CASE(32)
+    TSK_FIN_CASE(40)
+    TSK_FIN_CASE(48)
+    TSK_FIN_CASE(56)
+    TSK_FIN_CASE(64)
     default:
-      return launch_finish_t<16>(kp, kcm, mats, count, xpanels, ypanels, Wm, normA2, err, flags,
-                                 err_mode, tau, refine, status, s);
+      return cudaErrorInvalidValue;
   }
+#undef TSK_FIN_CASE
 }
 
 }  // namespace tsk

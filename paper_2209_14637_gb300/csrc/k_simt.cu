@@ -264,9 +264,10 @@ sketch_x_f32_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ it
 #pragma unroll
       for (int p = 0; p < CPT; ++p) sv[p] = Ss[cur][ii][cg * CPT + p];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
+      for (int q = 0; q < 8; q += 2)
 #pragma unroll
-        for (int p = 0; p < CPT; ++p) acc[q][p] = fmaf(a[q], sv[p], acc[q][p]);
+        for (int p = 0; p < CPT; ++p)
+          ffma2(acc[q][p], acc[q + 1][p], a[q], a[q + 1], sv[p], sv[p]);
     }
     // the other buffer was last read in the previous chunk, before its barrier
     if (ch + 1 < nch) park(cur ^ 1);
@@ -364,9 +365,10 @@ sketch_y_f32_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ it
 #pragma unroll
       for (int p = 0; p < CPT; ++p) xv[p] = Xs[cur][jj][cg * CPT + p];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
+      for (int q = 0; q < 8; q += 2)
 #pragma unroll
-        for (int p = 0; p < CPT; ++p) acc[q][p] = fmaf(a[q], xv[p], acc[q][p]);
+        for (int p = 0; p < CPT; ++p)
+          ffma2(acc[q][p], acc[q + 1][p], a[q], a[q + 1], xv[p], xv[p]);
     }
     if (ch + 1 < nch) park(cur ^ 1);
     __syncthreads();
@@ -1158,6 +1160,44 @@ cudaError_t launch_emit_sketch(bool dbl, const void* U, long long rows, int p,
   else
     emit_sketch_kernel<float><<<k, 256, 0, s>>>((const float*)U, rows, p,
                                                 (float*)S);
+  return cudaGetLastError();
+}
+
+// One CTA per 8 rows of one matrix.  A thread takes eight consecutive
+// elements of a row: eight 2-byte loads in flight (the source rows have no
+// alignment beyond 2 bytes) and one 16-byte store (the copy's rows start on
+// 16-byte boundaries); past n it stores zeros, within the padding.
+__global__ void __launch_bounds__(256) pack_rows_kernel(const PackDev* __restrict__ packs,
+                                                        const int2* __restrict__ items) {
+  const int2 it = items[blockIdx.x];
+  const PackDev pk = packs[it.x];
+  const unsigned short* src = (const unsigned short*)pk.src;
+  unsigned short* dst = (unsigned short*)pk.dst;
+  const long long r0 = (long long)it.y * 8;
+  const long long r1 = min(pk.m, r0 + 8);
+  const long long nch = (pk.n + 7) / 8;
+  for (long long r = r0; r < r1; ++r) {
+    const unsigned short* a = src + r * pk.lda;
+    unsigned short* b = dst + r * pk.ldp;
+    for (long long c = threadIdx.x; c < nch; c += blockDim.x) {
+      const long long j0 = 8 * c;
+      unsigned short v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = (j0 + e < pk.n) ? a[j0 + e] : (unsigned short)0;
+      uint4 w;
+      w.x = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
+      w.y = (uint32_t)v[2] | ((uint32_t)v[3] << 16);
+      w.z = (uint32_t)v[4] | ((uint32_t)v[5] << 16);
+      w.w = (uint32_t)v[6] | ((uint32_t)v[7] << 16);
+      *reinterpret_cast<uint4*>(b + j0) = w;
+    }
+  }
+}
+
+cudaError_t launch_pack_rows(const PackDev* packs, const int2* items, int nitems,
+                             cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  pack_rows_kernel<<<nitems, 256, 0, s>>>(packs, items);
   return cudaGetLastError();
 }
 

@@ -42,6 +42,13 @@ struct tsk_plan_s {
   size_t o_mats = 0, o_ix = 0, o_iy = 0, o_io = 0, o_pan = 0, o_X = 0, o_Y = 0,
          o_RX = 0, o_RY = 0, o_W = 0, o_flag = 0, o_U2 = 0, o_V2 = 0, o_e2 = 0,
          o_pan64 = 0, o_RX64 = 0, o_RY64 = 0, o_W64 = 0;
+  // BF16 matrices copied to 16-byte aligned rows before the sketch pass
+  int npack_items = 0;
+  size_t o_pk = 0, o_pki = 0;
+  // FP32 / BF16 small factors: matrix ids grouped by k rounded up to 8, one
+  // launch per group (kc, first id, count)
+  size_t o_fids = 0;
+  std::vector<int3> fin_cls;
   // Gram route (FP32 / BF16)
   double* d_norm = nullptr;
   double* d_err = nullptr;
@@ -252,6 +259,12 @@ static tsk_status check_desc(tsk_handle h, const tsk_mat_desc& d, int64_t i,
 static bool tc_eligible_one(const tsk_mat_desc& d) {
   return tc_matrix_eligible(d.A, d.m, d.lda, d.k);
 }
+// Padded leading dimension of the aligned copy: n rounded up to 8 elements.
+static long long pack_ld(long long n) { return (n + 7) / 8 * 8; }
+// Eligible once copied to rows with that leading dimension (an aligned base).
+static bool tc_eligible_packed(const tsk_mat_desc& d) {
+  return tc_matrix_eligible((const void*)256, d.m, pack_ld(d.n), d.k);
+}
 
 // ---------------------------------------------------------------------------
 // plans
@@ -298,6 +311,11 @@ static cudaError_t capture_plan(tsk_plan p, cudaEvent_t evb, cudaEvent_t eve) {
   // before the small factors.
   if (ce == cudaSuccess && p->use_tc) {
     ce = tc_launch_prep(p->tc, s);  // the S images, read by every class
+    ++launches;
+  }
+  if (ce == cudaSuccess && p->npack_items > 0) {  // aligned copies, before every branch
+    ce = launch_pack_rows((const PackDev*)(base + p->o_pk), (const int2*)(base + p->o_pki),
+                          p->npack_items, s);
     ++launches;
   }
   const int ncls = p->use_tc ? tc_classes(p->tc) : 0;
@@ -361,12 +379,30 @@ static cudaError_t capture_plan(tsk_plan p, cudaEvent_t evb, cudaEvent_t eve) {
     ++launches;
   } else if (ce == cudaSuccess) {
     // FP32 / BF16: Cholesky of X^T X (+ one refinement), eigenpairs of M^T M,
-    // one CTA per matrix
+    // one CTA per matrix, one launch per k class; the classes run
+    // concurrently on branches of the graph
     const PanelDev* pan = (const PanelDev*)(base + p->o_pan);
-    ce = launch_finish(kp, p->kmax, d_mats, count, pan, pan + count, (float*)(base + p->o_W),
-                       d_norm, d_err, (int*)(base + p->o_flag), h->opts.err_mode, tau,
-                       h->opts.refine_q, h->d_status, s);
-    ++launches;
+    const int* fids = (const int*)(base + p->o_fids);
+    const int nfc = (int)p->fin_cls.size();
+    if (nfc > tsk_handle_s::kBranches + 1) ce = cudaErrorInvalidValue;
+    int fforked = 0;
+    if (ce == cudaSuccess && nfc > 1) {
+      ce = cudaEventRecord(h->ev_fork, s);
+      for (int b = 0; ce == cudaSuccess && b < nfc - 1; ++b, ++fforked)
+        ce = cudaStreamWaitEvent(h->branch[b], h->ev_fork, 0);
+    }
+    for (int j = 0; ce == cudaSuccess && j < nfc; ++j) {
+      const int3 c = p->fin_cls[(size_t)j];
+      ce = launch_finish(kp, c.x, fids + c.y, c.z, d_mats, pan, pan + count,
+                         (float*)(base + p->o_W), d_norm, d_err, (int*)(base + p->o_flag),
+                         h->opts.err_mode, tau, h->opts.refine_q, h->d_status, br(j));
+      ++launches;
+    }
+    for (int b = 0; b < fforked; ++b) {
+      cudaError_t je = cudaEventRecord(h->ev_join[b], h->branch[b]);
+      if (je == cudaSuccess) je = cudaStreamWaitEvent(s, h->ev_join[b], 0);
+      if (ce == cudaSuccess) ce = je;
+    }
   }
   if (ce == cudaSuccess && h->opts.err_mode != 1) {
     ce = cudaMemsetAsync(base + p->o_e2, 0, sizeof(double) * count, s);
@@ -432,14 +468,20 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   }
   const int req = h->opts.kernel;
   // per matrix: tensor-core sketch (1) or CUDA-core sketch (0)
+  // BF16 rows that TMA cannot address (not 16-byte aligned) are copied to
+  // aligned rows in the workspace at every execution and take the
+  // tensor-core kernel too
   std::vector<char> on_tc((size_t)count, 0);
-  std::vector<int> tc_ids;
+  std::vector<int> tc_ids, pack_ids;
   if (prec == TSK_BF16 && req != TSK_KERNEL_SIMT && tc_supported()) {
-    for (int64_t i = 0; i < count; ++i)
-      if (tc_eligible_one(mats[i])) {
+    for (int64_t i = 0; i < count; ++i) {
+      const bool direct = tc_eligible_one(mats[i]);
+      if (direct || tc_eligible_packed(mats[i])) {
         on_tc[(size_t)i] = 1;
         tc_ids.push_back((int)i);
+        if (!direct) pack_ids.push_back((int)i);
       }
+    }
   }
   if (req == TSK_KERNEL_TC) {
     if (prec != TSK_BF16) {
@@ -448,8 +490,7 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
     }
     if ((int64_t)tc_ids.size() != count) {
       set_err(h, "tensor-core kernel requested but unavailable for these "
-                 "arguments (needs a GB300, k <= 48, m <= 4096, a 16-byte aligned A and "
-                 "lda * 2 a multiple of 16)");
+                 "arguments (needs a GB300, k <= 48 and m <= 4096)");
       return TSK_EUNSUPPORTED;
     }
   }
@@ -509,6 +550,31 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   const size_t o_iy = cv.take(sizeof(int2) * std::max<size_t>(1, iy.size()));
   const size_t o_io = cv.take(sizeof(int4) * std::max<size_t>(1, io.size()));
   const size_t o_pan = cv.take(sizeof(PanelDev) * 2 * count);
+  // aligned copies: descriptors and row-block items (uploaded with the
+  // other descriptors), then the copies themselves
+  std::vector<PackDev> hpk(pack_ids.size());
+  std::vector<int2> pki;
+  for (size_t q = 0; q < pack_ids.size(); ++q) {
+    const tsk_mat_desc& d = mats[pack_ids[q]];
+    for (long long t = 0; t < (d.m + 7) / 8; ++t) pki.push_back(make_int2((int)q, (int)t));
+  }
+  if (pki.size() > (size_t)INT32_MAX) {
+    set_err(h, "too many rows to copy");
+    delete p;
+    return TSK_EINVAL;
+  }
+  std::vector<int> fids;
+  std::vector<int3> fcls;
+  // the widest class first: its CTAs run longest, so they start first
+  for (int kc = TSK_MAX_K; kc >= 8; kc -= 8) {
+    const int first = (int)fids.size();
+    for (int64_t i = 0; i < count; ++i)
+      if (((mats[i].k + 7) & ~7) == kc) fids.push_back((int)i);
+    if ((int)fids.size() > first) fcls.push_back(make_int3(kc, first, (int)fids.size() - first));
+  }
+  const size_t o_fids = cv.take(sizeof(int) * fids.size());
+  const size_t o_pk = cv.take(sizeof(PackDev) * std::max<size_t>(1, hpk.size()));
+  const size_t o_pki = cv.take(sizeof(int2) * std::max<size_t>(1, pki.size()));
   const size_t o_X = cv.take(cs * offX);
   const size_t o_Y = cv.take(cs * offY);
   const size_t o_RX = cv.take(cs * count * kp * kp);
@@ -527,6 +593,11 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   const size_t o_RX64 = cv.take(s64 ? 8 * (size_t)count * kp * kp : 0);
   const size_t o_RY64 = cv.take(s64 ? 8 * (size_t)count * kp * kp : 0);
   const size_t o_W64 = cv.take(s64 ? 8 * (size_t)count * kp * kp : 0);
+  std::vector<size_t> o_copy(pack_ids.size());
+  for (size_t q = 0; q < pack_ids.size(); ++q) {
+    const tsk_mat_desc& d = mats[pack_ids[q]];
+    o_copy[q] = cv.take(2 * (size_t)d.m * (size_t)pack_ld(d.n));
+  }
   const size_t host_part = o_X;  // descriptors live before X
   p->ws_bytes = cv.off;
   cudaError_t ce = cudaMalloc(&p->ws, p->ws_bytes);
@@ -559,6 +630,18 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   if (!iy.empty()) memcpy(staging.data() + o_iy, iy.data(), sizeof(int2) * iy.size());
   if (!io.empty()) memcpy(staging.data() + o_io, io.data(), sizeof(int4) * io.size());
   memcpy(staging.data() + o_pan, hp.data(), sizeof(PanelDev) * 2 * count);
+  for (size_t q = 0; q < pack_ids.size(); ++q) {
+    const tsk_mat_desc& d = mats[pack_ids[q]];
+    hpk[q].src = d.A;
+    hpk[q].dst = base + o_copy[q];
+    hpk[q].m = d.m;
+    hpk[q].n = d.n;
+    hpk[q].lda = d.lda;
+    hpk[q].ldp = pack_ld(d.n);
+  }
+  memcpy(staging.data() + o_fids, fids.data(), sizeof(int) * fids.size());
+  if (!hpk.empty()) memcpy(staging.data() + o_pk, hpk.data(), sizeof(PackDev) * hpk.size());
+  if (!pki.empty()) memcpy(staging.data() + o_pki, pki.data(), sizeof(int2) * pki.size());
   ce = cudaMemcpy(p->ws, staging.data(), host_part, cudaMemcpyHostToDevice);
   if (ce == cudaSuccess && s64) {
     // the same float panels, with double R factors
@@ -594,7 +677,13 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
         if (it != h->tune.end()) mcp[(size_t)i] = it->second;
       }
     }
-    ce = tc_prepare(&p->tc, hm.data(), d_mats, (int)count, tc_ids.data(), (int)tc_ids.size(),
+    // the tensor maps of copied matrices address the copies
+    std::vector<MatDev> hmt(hm);
+    for (size_t q = 0; q < pack_ids.size(); ++q) {
+      hmt[(size_t)pack_ids[q]].A = hpk[q].dst;
+      hmt[(size_t)pack_ids[q]].lda = hpk[q].ldp;
+    }
+    ce = tc_prepare(&p->tc, hmt.data(), d_mats, (int)count, tc_ids.data(), (int)tc_ids.size(),
                     mcp.data(), kp, base + o_X, base + o_Y, d_norm, h->d_status,
                     h->opts.spin_limit, msg, sizeof(msg));
     if (ce != cudaSuccess) {
@@ -627,6 +716,11 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   p->o_RX64 = o_RX64;
   p->o_RY64 = o_RY64;
   p->o_W64 = o_W64;
+  p->npack_items = (int)pki.size();
+  p->o_fids = o_fids;
+  p->fin_cls = fcls;
+  p->o_pk = o_pk;
+  p->o_pki = o_pki;
   p->d_norm = d_norm;
   p->d_err = d_err;
   ce = capture_plan(p, nullptr, nullptr);

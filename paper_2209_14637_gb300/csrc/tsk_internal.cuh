@@ -38,6 +38,23 @@ struct PanelDev {
   void* R;  // kp x kp row-major, upper triangle holds R
 };
 
+// Two FP32 operations in one instruction (fma / mul .rn.f32x2): lane 0 and
+// lane 1 of each pair, each rounded as fmaf / __fmul_rn would round it.
+__device__ __forceinline__ void ffma2(float& d0, float& d1, float a0, float a1, float b0,
+                                      float b1) {
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rd, {%0, %1};\n\tfma.rn.f32x2 rd, ra, rb, rd;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "+f"(d0), "+f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void fmul2(float& d0, float& d1, float a0, float a1, float b0,
+                                      float b1) {
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
 // Element conversions used by the loaders.
 __device__ __forceinline__ float to_float(float x) { return x; }
 __device__ __forceinline__ float to_float(double x) { return (float)x; }
@@ -68,6 +85,18 @@ void set_thread_error(const char* fmt, ...);
 // ---- launchers (host functions), defined in the .cu files ---------------
 
 // k_simt.cu
+// A BF16 matrix whose rows TMA cannot address (row starts off a 16-byte
+// boundary) and its copy with a padded leading dimension ldp (n rounded up to
+// 8 elements) in the plan's workspace, which the tensor-core kernel reads.
+struct PackDev {
+  const void* src;
+  void* dst;
+  long long m, n, lda, ldp;
+};
+// Copies rows [8 t, 8 t + 8) of pack items[i].x for t = items[i].y; the
+// padding columns [n, ldp) are not written (the tensor maps stop at n).
+cudaError_t launch_pack_rows(const PackDev* packs, const int2* items, int nitems,
+                             cudaStream_t s);
 cudaError_t launch_sketch_x(int in_type, int kp, const MatDev* mats,
                             const int2* items, int nitems, void* X,
                             double* normA2, cudaStream_t s);
@@ -126,7 +155,9 @@ cudaError_t launch_sym_eig(bool dbl, const void* H, int p, void* theta,
                            void* V, cudaStream_t s);
 // Fused small factors of the FP32 / BF16 paths (k_finish.cu): one CTA per
 // matrix takes the X and Y panels to W = R_X^{-1} V_r, sigma and err.
-cudaError_t launch_finish(int kp, int kmax, const MatDev* mats, int count,
+// The small factors of the FP32 / BF16 paths for the matrices ids[0 .. count)
+// of mats, all with k rounded up to 8 equal to kc.
+cudaError_t launch_finish(int kp, int kc, const int* ids, int count, const MatDev* mats,
                           const PanelDev* xpanels, const PanelDev* ypanels, float* Wm,
                           double* normA2, double* err, int* flags, int err_mode, double tau,
                           int refine, int* status, cudaStream_t s);

@@ -4,11 +4,12 @@ uneven size, m log-uniform in [256, 4096], n in [256, 2048], k in {10, 20,
 Section 1).
 
 Sizes are not rounded, so most contiguous BF16 rows do not start on 16-byte
-boundaries: those matrices take the CUDA-core sketch kernels and the rest the
-tensor-core kernel, on two branches of one graph.  Stored with a padded
-leading dimension, every matrix takes the tensor-core kernel.  Sampled
-outputs are compared with the oracle at the 1e-3 gap; every ||A||^2 is
-compared with the oracle's sum of squares.
+boundaries: the plan copies those matrices to aligned rows in its workspace
+at every execution, and every matrix takes the tensor-core kernel
+(TSK_KERNEL_TC accepts both layouts).  Stored with a padded leading
+dimension, nothing is copied.  Sampled outputs are compared with the oracle
+at the 1e-3 gap; every ||A||^2 is compared with the oracle's sum of
+squares.
 """
 import numpy as np
 import pytest
@@ -63,8 +64,7 @@ def test_c4_ragged_batch_of_512(tsk, batch, pad_rows):
         assert unaligned == 0
     else:
         assert unaligned > 256  # most rows start off a 16-byte boundary
-    h = tsk.Handle(kernel=tsk.KERNEL_TC if pad_rows else tsk.KERNEL_AUTO,
-                   refine_q=tsk.REFINE_ALWAYS)
+    h = tsk.Handle(kernel=tsk.KERNEL_TC, refine_q=tsk.REFINE_ALWAYS)
     err = torch.empty(len(As), dtype=torch.float64, device="cuda")
     nrm = torch.empty(len(As), dtype=torch.float64, device="cuda")
     plan = h.plan(As, Ss, rs, err, nrm)

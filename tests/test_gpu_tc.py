@@ -105,20 +105,25 @@ def test_tc_ragged_batch_matches_simt(tsk):
     h2.close()
 
 
-def test_tc_rejects_unaligned_rows(tsk):
-    # a row of 70 BF16 values is 140 bytes: not a multiple of 16, so TMA
-    # cannot tile it; asking for the tensor-core kernel explicitly fails
+def test_unaligned_rows_are_copied_for_the_tensor_cores(tsk):
+    """A row of 70 BF16 values is 140 bytes, not a multiple of 16, so TMA
+    cannot tile it: the plan copies A to rows of 72 elements in its
+    workspace and the tensor-core kernel reads the copy (TSK_KERNEL_TC
+    accepts it); the error matches the oracle and the CUDA-core kernels,
+    also for an A that starts off a 16-byte boundary."""
     A, S = _case(128, 70, 8, 3)
-    h = tsk.Handle(kernel=tsk.KERNEL_TC)
-    with pytest.raises(tsk.TskError) as e:
-        h.approx_batch([A], [S], 4)
-    assert e.value.status == 7  # TSK_EUNSUPPORTED
-    h.close()
-    # the automatic choice falls back to the CUDA-core kernels
-    out, st, h = _run(tsk, tsk.KERNEL_AUTO, [A], [S], [4])
+    buf = torch.zeros(128 * 70 + 3, dtype=torch.bfloat16, device="cuda")
+    buf[3:].view(128, 70).copy_(A)
+    A_off = buf[3:].view(128, 70)  # starts 6 bytes past a 16-byte boundary
+    assert A_off.data_ptr() % 16 != 0
     o = oracle.scw(_np(A), _np(S), 4, dense=False)
-    assert st == 0 and abs(float(out["err"][0]) - o["err"]) <= GAP * o["err"]
-    h.close()
+    for Ax in (A, A_off):
+        for kern in (tsk.KERNEL_TC, tsk.KERNEL_AUTO, tsk.KERNEL_SIMT):
+            out, st, h = _run(tsk, kern, [Ax], [S], [4])
+            assert st == 0, kern
+            assert abs(float(out["err"][0]) - o["err"]) <= GAP * o["err"], kern
+            np.testing.assert_allclose(float(out["normA2"][0]), o["normA2"], rtol=1e-6)
+            h.close()
 
 
 def test_tc_repeated_plan_is_deterministic(tsk):
@@ -255,14 +260,15 @@ def _gram_entrywise(G, R, tol):
     assert worst <= 1.0, worst
 
 
-def test_mixed_batch_routes_unaligned_rows(tsk):
-    """A BF16 batch where some rows cannot be moved by TMA (a row of n BF16
-    values with 2n not a multiple of 16 bytes) and some can: the aligned
-    matrices take the tensor-core kernel and the rest the CUDA-core kernels,
-    in one plan; every error matches the oracle, and asking for the
-    tensor-core kernel alone is refused."""
+def test_mixed_batch_routes_by_k_and_copies_unaligned_rows(tsk):
+    """A BF16 batch with rows TMA cannot move as they are (2n not a multiple
+    of 16 bytes: copied to aligned rows, then the tensor-core kernel),
+    aligned rows (tensor-core kernel directly) and k = 56 > 48 (CUDA-core
+    kernels), in one plan: every error, ||A||^2 and factor matches the
+    oracle, and asking for the tensor-core kernel alone is refused because
+    of the k = 56 matrix only."""
     sizes = [(300, 77, 16), (512, 200, 20), (257, 131, 10), (1024, 64, 40),
-             (129, 333, 12), (700, 520, 24)]
+             (129, 333, 12), (700, 520, 24), (400, 300, 56)]
     As, Ss, rs = [], [], []
     for i, (m, n, k) in enumerate(sizes):
         A, S = _case(m, n, k, 500 + i)
@@ -282,6 +288,10 @@ def test_mixed_batch_routes_unaligned_rows(tsk):
     with pytest.raises(tsk.TskError) as e:
         h2.approx_batch(As, Ss, rs)
     assert e.value.status == 7
+    out2 = h2.approx_batch(As[:-1], Ss[:-1], rs[:-1])  # without k = 56
+    torch.cuda.synchronize()
+    assert h2.sync_status() == 0
+    np.testing.assert_allclose(_np(out2["err"]), _np(out["err"])[:-1], rtol=1e-12)
     h2.close()
 
 
