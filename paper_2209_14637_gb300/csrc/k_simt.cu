@@ -8,6 +8,8 @@
 #include <cuda_bf16.h>
 #include <stdio.h>
 
+#include <algorithm>
+
 #include "tsk_internal.cuh"
 
 namespace tsk {
@@ -594,34 +596,40 @@ cudaError_t launch_gram(int in_type, const void* const* dA, long long D,
 
 // ---------------------------------------------------------------------------
 // Small dense GEMM for the eigensolver: C = alpha op(A) op(B) + beta C,
-// row-major, op = transpose when the flag is set.  64 x 64 tiles.
+// row-major, op = transpose when the flag is set.  64 x 64 tiles.  With a
+// workspace the K range is split over blockIdx.z (each split writes its
+// partial product to part[z]) and a second kernel sums the splits in order,
+// so that the thin products (80 x 80 over 2048 rows, 2048 x 80 over 2048)
+// fill the GPU; the result does not depend on timing.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool PART>
 __global__ void __launch_bounds__(256)
-gemm_kernel(int transA, int transB, long long M, long long N, long long K,
+gemm_kernel(int transA, int transB, long long M, long long N, long long K, long long kchunk,
             T alpha, const T* __restrict__ A, long long lda,
             const T* __restrict__ B, long long ldb, T beta, T* __restrict__ C,
-            long long ldc) {
+            long long ldc, T* __restrict__ part) {
   constexpr int TM = 64, TN = 64, KC = 16;
   __shared__ T As[KC][TM + 1];
   __shared__ T Bs[KC][TN + 1];
   const long long m0 = (long long)blockIdx.y * TM, n0 = (long long)blockIdx.x * TN;
+  const long long kb = (long long)blockIdx.z * kchunk;
+  const long long ke = min(K, kb + kchunk);
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   T acc[4][4];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int p = 0; p < 4; ++p) acc[q][p] = T(0);
-  for (long long k0 = 0; k0 < K; k0 += KC) {
+  for (long long k0 = kb; k0 < ke; k0 += KC) {
     for (int e = tid; e < KC * TM; e += 256) {
       const int kk = e / TM, a = e % TM;
       const long long gm = m0 + a, gk = k0 + kk;
       T v = T(0);
-      if (gm < M && gk < K) v = transA ? A[gk * lda + gm] : A[gm * lda + gk];
+      if (gm < M && gk < ke) v = transA ? A[gk * lda + gm] : A[gm * lda + gk];
       As[kk][a] = v;
       const long long gn = n0 + a;
       T w = T(0);
-      if (gn < N && gk < K) w = transB ? B[gn * ldb + gk] : B[gk * ldb + gn];
+      if (gn < N && gk < ke) w = transB ? B[gn * ldb + gk] : B[gk * ldb + gn];
       Bs[kk][a] = w;
     }
     __syncthreads();
@@ -647,27 +655,76 @@ gemm_kernel(int transA, int transB, long long M, long long N, long long K,
     for (int p = 0; p < 4; ++p) {
       const long long gn = n0 + tx * 4 + p;
       if (gn >= N) continue;
-      T* c = C + gm * ldc + gn;
-      *c = alpha * acc[q][p] + (beta == T(0) ? T(0) : beta * *c);
+      if (PART) {
+        part[((long long)blockIdx.z * M + gm) * N + gn] = acc[q][p];
+      } else {
+        T* c = C + gm * ldc + gn;
+        *c = alpha * acc[q][p] + (beta == T(0) ? T(0) : beta * *c);
+      }
     }
   }
+}
+
+// C = alpha sum_z part[z] + beta C, the splits summed in index order.
+template <typename T>
+__global__ void __launch_bounds__(256)
+splitk_reduce_kernel(const T* __restrict__ part, int S, long long M, long long N, T alpha,
+                     T beta, T* __restrict__ C, long long ldc) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * N) return;
+  const long long i = e / N, j = e - i * N;
+  T acc = T(0);
+  for (int z = 0; z < S; ++z) acc += part[(long long)z * M * N + e];
+  T* c = C + i * ldc + j;
+  *c = alpha * acc + (beta == T(0) ? T(0) : beta * *c);
+}
+
+template <typename T>
+static cudaError_t gemm_t(int transA, int transB, long long M, long long N, long long K,
+                          double alpha, const void* A, long long lda, const void* B,
+                          long long ldb, double beta, void* C, long long ldc, void* work,
+                          size_t work_bytes, cudaStream_t s) {
+  const long long tiles = ((N + 63) / 64) * ((M + 63) / 64);
+  long long S = 1;
+  if (work && M * N > 0) {
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    S = std::max<long long>(1, (2LL * nsm + tiles - 1) / tiles);  // about two CTAs per SM
+    S = std::min<long long>(S, (K + 63) / 64);                     // at least 64 of K each
+    S = std::min<long long>(S, (long long)(work_bytes / (sizeof(T) * M * N)));
+    S = std::min<long long>(S, 64);
+  }
+  if (S <= 1) {
+    dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64), 1);
+    gemm_kernel<T, false><<<grid, 256, 0, s>>>(transA, transB, M, N, K, K, (T)alpha,
+                                               (const T*)A, lda, (const T*)B, ldb, (T)beta,
+                                               (T*)C, ldc, nullptr);
+    return cudaGetLastError();
+  }
+  const long long kchunk = ((K + S - 1) / S + 15) / 16 * 16;
+  S = (K + kchunk - 1) / kchunk;
+  dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64), (unsigned)S);
+  gemm_kernel<T, true><<<grid, 256, 0, s>>>(transA, transB, M, N, K, kchunk, (T)alpha,
+                                            (const T*)A, lda, (const T*)B, ldb, (T)beta,
+                                            (T*)C, ldc, (T*)work);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  splitk_reduce_kernel<T><<<(unsigned)((M * N + 255) / 256), 256, 0, s>>>(
+      (const T*)work, (int)S, M, N, (T)alpha, (T)beta, (T*)C, ldc);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gemm(bool dbl, int transA, int transB, long long M,
                         long long N, long long K, double alpha, const void* A,
                         long long lda, const void* B, long long ldb,
-                        double beta, void* C, long long ldc, cudaStream_t s) {
-  dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
+                        double beta, void* C, long long ldc, cudaStream_t s, void* work,
+                        size_t work_bytes) {
   if (dbl)
-    gemm_kernel<double><<<grid, 256, 0, s>>>(transA, transB, M, N, K, alpha,
-                                             (const double*)A, lda,
-                                             (const double*)B, ldb, beta,
-                                             (double*)C, ldc);
-  else
-    gemm_kernel<float><<<grid, 256, 0, s>>>(
-        transA, transB, M, N, K, (float)alpha, (const float*)A, lda,
-        (const float*)B, ldb, (float)beta, (float*)C, ldc);
-  return cudaGetLastError();
+    return gemm_t<double>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, work,
+                          work_bytes, s);
+  return gemm_t<float>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, work,
+                       work_bytes, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1020,14 +1077,16 @@ __global__ void chol_upper_kernel(const T* __restrict__ Gm, int p, T* __restrict
   for (int a = 0; a < p; ++a) mx = A[a * ld + a] > mx ? A[a * ld + a] : mx;
   const T thr = T(1e-12) * mx;
   __syncthreads();
+  // step j: every entry (a, c), j < a <= c, of the trailing triangle is
+  // updated by one thread from row j (which step j does not change)
   for (int j = 0; j < p; ++j) {
     const T d = A[j * ld + j];
-    for (int c = j + 1 + tid; c < p; c += blockDim.x) {
-      if (d > thr) {
-        const T f = A[j * ld + c] / d;
-        for (int a = j + 1; a <= c; ++a) A[a * ld + c] -= A[j * ld + a] * f;
+    const int rem = p - 1 - j;
+    if (d > thr)
+      for (int e = tid; e < rem * rem; e += blockDim.x) {
+        const int a = j + 1 + e / rem, c = j + 1 + e % rem;
+        if (a <= c) A[a * ld + c] -= A[j * ld + a] * (A[j * ld + c] / d);
       }
-    }
     __syncthreads();
   }
   for (int e = tid; e < p * p; e += blockDim.x) {
@@ -1037,6 +1096,55 @@ __global__ void chol_upper_kernel(const T* __restrict__ Gm, int p, T* __restrict
     if (c >= a) v = (d > thr) ? A[a * ld + c] / sqrt(d) : (c == a ? T(1) : T(0));
     R[e] = v;
   }
+}
+
+// Ri = R^{-1} for the upper triangular R (p x p, row stride p): thread c
+// takes column c by back substitution, R and Ri in shared memory.
+template <typename T>
+__global__ void tri_inv_upper_kernel(const T* __restrict__ R, int p, T* __restrict__ Ri) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ld = p + 1;
+  T* Rs = (T*)smem_raw;  // p x (p + 1)
+  T* Is = Rs + p * ld;   // p x (p + 1)
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int a = e / p, c = e - a * p;
+    Rs[a * ld + c] = R[e];
+    Is[a * ld + c] = T(0);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < p; c += blockDim.x) {
+    const T dc = Rs[c * ld + c];
+    Is[c * ld + c] = dc != T(0) ? T(1) / dc : T(0);
+    for (int i = c - 1; i >= 0; --i) {
+      T t = T(0);
+      for (int q = i + 1; q <= c; ++q) t += Rs[i * ld + q] * Is[q * ld + c];
+      const T d = Rs[i * ld + i];
+      Is[i * ld + c] = d != T(0) ? -t / d : T(0);
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int a = e / p, c = e - a * p;
+    Ri[e] = Is[a * ld + c];
+  }
+}
+
+cudaError_t launch_tri_inv_upper(bool dbl, const void* R, int p, void* Ri, cudaStream_t s) {
+  const size_t sh = (size_t)2 * p * (p + 1) * (dbl ? sizeof(double) : sizeof(float));
+  const unsigned nt = (unsigned)std::max(32, (p + 31) / 32 * 32);
+  cudaError_t e;
+  if (dbl) {
+    e = cudaFuncSetAttribute(tri_inv_upper_kernel<double>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e != cudaSuccess) return e;
+    tri_inv_upper_kernel<double><<<1, nt, sh, s>>>((const double*)R, p, (double*)Ri);
+  } else {
+    e = cudaFuncSetAttribute(tri_inv_upper_kernel<float>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e != cudaSuccess) return e;
+    tri_inv_upper_kernel<float><<<1, nt, sh, s>>>((const float*)R, p, (float*)Ri);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_chol_upper(bool dbl, const void* Gm, int p, void* R, cudaStream_t s) {

@@ -421,8 +421,174 @@ sym_eig_kernel(const T* __restrict__ H, int p, T* __restrict__ theta,
   for (int c = threadIdx.x; c < p; c += blockDim.x) theta[c] = sig[order[c]];
 }
 
+// The same eigen-decomposition in FP32 with the columns in registers: thread
+// (j, qt) = (tid / 4, tid % 4) holds rows [qt QMAX, qt QMAX + QMAX) of
+// column j of M (H rotated) and of V.  Each round of the round-robin order
+// the threads store their parts to one of two planes, read the partner
+// column's parts after one barrier, sum the three dot products over the
+// column's four threads, and both columns' threads derive the same rotation
+// from the same sums (the rotation and the stopping rule are those of
+// jacobi_columns).  p <= 4 QMAX <= 96.
+__device__ __forceinline__ int rr_partner(int round, int j, int mm) {
+  if (j == mm) return round;
+  if (j == round) return mm;
+  int x = 2 * round - j;
+  if (x < 0) x += mm;
+  if (x >= mm) x -= mm;
+  return x;
+}
+
+template <int QMAX>
+__global__ void __launch_bounds__(384)
+sym_eig_reg_kernel(const float* __restrict__ H, int p, float* __restrict__ theta,
+                   float* __restrict__ Vout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int jl = 4 * QMAX + 4;  // column stride of a plane
+  float* PL = (float*)smem_raw;     // [2 buffers][M, V][p][jl]
+  float* lam = PL + 4 * p * jl;
+  int* order = (int*)(lam + p);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int j = tid >> 2, qt = tid & 3, i0 = qt * QMAX;
+  float m[QMAX], v[QMAX];
+#pragma unroll
+  for (int i = 0; i < QMAX; ++i) {
+    const int row = i0 + i;
+    const bool in = j < p && row < p;
+    m[i] = in ? 0.5f * (H[row * p + j] + H[j * p + row]) : 0.f;
+    v[i] = (in && row == j) ? 1.f : 0.f;
+  }
+  const unsigned gmask = 0xFu << (lane & 28);  // the column's four threads
+  const int kk = p + (p & 1), mm = kk - 1;
+  int t = 0;
+  for (int sweep = 0; sweep < 60 && mm > 0; ++sweep) {
+    int rot = 0;
+    for (int round = 0; round < mm; ++round, ++t) {
+      float* Bm = PL + (t & 1) * 2 * p * jl;
+      float* Bv = Bm + p * jl;
+      if (j < p) {
+#pragma unroll
+        for (int i = 0; i < QMAX; i += 4) {
+          *reinterpret_cast<float4*>(Bm + j * jl + i0 + i) =
+              make_float4(m[i], m[i + 1], m[i + 2], m[i + 3]);
+          *reinterpret_cast<float4*>(Bv + j * jl + i0 + i) =
+              make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        }
+      }
+      __syncthreads();
+      const int pj = j < p ? rr_partner(round, j, mm) : p;
+      if (pj < p) {  // the column's four threads take this branch together
+        float y[QMAX], w[QMAX];
+#pragma unroll
+        for (int i = 0; i < QMAX; i += 4) {
+          const float4 a = *reinterpret_cast<const float4*>(Bm + pj * jl + i0 + i);
+          const float4 b = *reinterpret_cast<const float4*>(Bv + pj * jl + i0 + i);
+          y[i] = a.x;
+          y[i + 1] = a.y;
+          y[i + 2] = a.z;
+          y[i + 3] = a.w;
+          w[i] = b.x;
+          w[i + 1] = b.y;
+          w[i + 2] = b.z;
+          w[i + 3] = b.w;
+        }
+        float aa = 0.f, pp = 0.f, ap = 0.f;
+#pragma unroll
+        for (int i = 0; i < QMAX; ++i) {
+          aa = fmaf(m[i], m[i], aa);
+          pp = fmaf(y[i], y[i], pp);
+          ap = fmaf(m[i], y[i], ap);
+        }
+        aa += __shfl_xor_sync(gmask, aa, 1);
+        pp += __shfl_xor_sync(gmask, pp, 1);
+        ap += __shfl_xor_sync(gmask, ap, 1);
+        aa += __shfl_xor_sync(gmask, aa, 2);
+        pp += __shfl_xor_sync(gmask, pp, 2);
+        ap += __shfl_xor_sync(gmask, ap, 2);
+        const bool low = j < pj;  // the lower index is the first column of the pair
+        const float alpha = low ? aa : pp, beta = low ? pp : aa, gamma = ap;
+        if (fabsf(gamma) > Eps<float>::jacobi * sqrtf(alpha * beta) &&
+            fabsf(gamma) > Eps<float>::tiny) {
+          const float zeta = (beta - alpha) / (2.f * gamma);
+          const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float c = 1.f / sqrtf(1.f + tt * tt), sn = c * tt;
+          // first column <- c first - s second; second <- s first + c second
+          if (low) {
+#pragma unroll
+            for (int i = 0; i < QMAX; ++i) {
+              m[i] = c * m[i] - sn * y[i];
+              v[i] = c * v[i] - sn * w[i];
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < QMAX; ++i) {
+              m[i] = sn * y[i] + c * m[i];
+              v[i] = sn * w[i] + c * v[i];
+            }
+          }
+          rot = 1;
+        }
+      }
+    }
+    if (!__syncthreads_or(rot)) break;
+  }
+  // theta_j = ||M[:, j]||; V columns to plane 0
+  float nn = 0.f;
+#pragma unroll
+  for (int i = 0; i < QMAX; ++i) nn = fmaf(m[i], m[i], nn);
+  nn += __shfl_xor_sync(0xffffffffu, nn, 1);
+  nn += __shfl_xor_sync(0xffffffffu, nn, 2);
+  float* Vs = PL + p * jl;
+  if (j < p) {
+    if (qt == 0) lam[j] = sqrtf(nn);
+#pragma unroll
+    for (int i = 0; i < QMAX; i += 4)
+      *reinterpret_cast<float4*>(Vs + j * jl + i0 + i) =
+          make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+  }
+  __syncthreads();
+  for (int c = tid; c < p; c += blockDim.x) {  // descending; NaN ranks last
+    const float lc = lam[c] == lam[c] ? lam[c] : -INFINITY;
+    int rank = 0;
+    for (int c2 = 0; c2 < p; ++c2) {
+      const float l2 = lam[c2] == lam[c2] ? lam[c2] : -INFINITY;
+      rank += (l2 > lc) || (l2 == lc && c2 < c);
+    }
+    order[rank] = c;
+  }
+  __syncthreads();
+  for (int e = tid; e < p * p; e += blockDim.x) {
+    const int i = e / p, c = e - i * p;
+    Vout[e] = Vs[order[c] * jl + i];
+  }
+  for (int c = tid; c < p; c += blockDim.x) theta[c] = lam[order[c]];
+}
+
+template <int QMAX>
+static cudaError_t launch_sym_eig_reg(const float* H, int p, float* theta, float* V,
+                                      cudaStream_t s) {
+  constexpr int jl = 4 * QMAX + 4;
+  const size_t sm = (size_t)4 * p * jl * sizeof(float) + (size_t)p * (sizeof(float) + sizeof(int));
+  cudaError_t e = cudaFuncSetAttribute(sym_eig_reg_kernel<QMAX>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const unsigned nt = (unsigned)((4 * p + 31) / 32 * 32);
+  sym_eig_reg_kernel<QMAX><<<1, nt, sm, s>>>(H, p, theta, V);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sym_eig(bool dbl, const void* H, int p, void* theta,
                            void* V, cudaStream_t s) {
+  if (!dbl && p >= 1 && p <= 96) {
+    const int q = ((p + 3) / 4 + 3) / 4 * 4;  // rows per thread, a multiple of 4
+    switch (q) {
+      case 4: return launch_sym_eig_reg<4>((const float*)H, p, (float*)theta, (float*)V, s);
+      case 8: return launch_sym_eig_reg<8>((const float*)H, p, (float*)theta, (float*)V, s);
+      case 12: return launch_sym_eig_reg<12>((const float*)H, p, (float*)theta, (float*)V, s);
+      case 16: return launch_sym_eig_reg<16>((const float*)H, p, (float*)theta, (float*)V, s);
+      case 20: return launch_sym_eig_reg<20>((const float*)H, p, (float*)theta, (float*)V, s);
+      default: return launch_sym_eig_reg<24>((const float*)H, p, (float*)theta, (float*)V, s);
+    }
+  }
   const size_t elt = dbl ? sizeof(double) : sizeof(float);
   const size_t sm = (size_t)2 * p * (p + 1) * elt + p * elt + p * sizeof(int) + 16;
   if (dbl) {

@@ -979,6 +979,10 @@ extern "C" tsk_status tsk_sketch_from_gram(tsk_handle h, const double* G,
   const size_t o_R = cv.take(cs * p * p);
   const size_t o_res = cv.take(sizeof(double) * k);
   const size_t o_pan = cv.take(sizeof(PanelDev));
+  // partial products of the split-K GEMMs (up to 8 splits of dim x p, 64 of
+  // p x p)
+  const size_t part_bytes = cs * (size_t)std::max<int64_t>(8 * dim * p, 64 * (int64_t)p * p);
+  const size_t o_part = cv.take(part_bytes);
   void* ws = nullptr;
   TSK_CUDA(h, cudaMallocAsync(&ws, cv.off, s));
   unsigned char* b = (unsigned char*)ws;
@@ -987,6 +991,7 @@ extern "C" tsk_status tsk_sketch_from_gram(tsk_handle h, const double* G,
        *V = b + o_V, *th = b + o_th, *R = b + o_R;
   double* res = (double*)(b + o_res);
   PanelDev* dpan = (PanelDev*)(b + o_pan);
+  void* part = b + o_part;
   tsk_status result = TSK_OK;
 #define TSK_E(call)                                                            \
   do {                                                                         \
@@ -1014,15 +1019,20 @@ extern "C" tsk_status tsk_sketch_from_gram(tsk_handle h, const double* G,
   };
   // FP32: CholeskyQR2 of the block (its Gram, Cholesky, Z <- Z R^{-1}, twice),
   // after scaling column c of G U by 1/theta_c, which leaves it close to
-  // orthonormal (G u_c ~ theta_c u_c), so the Gram is well conditioned.  FP64
-  // keeps the blockwise Householder factorisation.
+  // orthonormal (G u_c ~ theta_c u_c), so the Gram is well conditioned; R is
+  // then close to the identity and Z R^{-1} is taken as a GEMM with the
+  // explicit inverse (into U, which is free here, then back).  FP64 keeps the
+  // blockwise Householder factorisation.
   auto orth2 = [&](void* P, const void* theta) -> cudaError_t {
     cudaError_t e = cudaSuccess;
     if (theta) e = launch_scale_cols(dbl, P, dim, p, theta, s);
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-      e = launch_gemm(dbl, 1, 0, p, p, dim, 1.0, P, p, P, p, 0.0, H, p, s);
+      e = launch_gemm(dbl, 1, 0, p, p, dim, 1.0, P, p, P, p, 0.0, H, p, s, part, part_bytes);
       if (e == cudaSuccess) e = launch_chol_upper(dbl, H, p, R, s);
-      if (e == cudaSuccess) e = launch_apply_rinv(dbl, P, R, P, dim, p, s);
+      if (e == cudaSuccess) e = launch_tri_inv_upper(dbl, R, p, H, s);
+      if (e == cudaSuccess) e = launch_gemm(dbl, 0, 0, dim, p, p, 1.0, P, p, H, p, 0.0, U, p, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P, U, cs * (size_t)dim * p, cudaMemcpyDeviceToDevice, s);
     }
     return e;
   };
@@ -1034,8 +1044,9 @@ extern "C" tsk_status tsk_sketch_from_gram(tsk_handle h, const double* G,
   int stall = 0;
   bool converged = false;
   for (int it = 0; it < h->opts.max_iter; ++it) {
-    TSK_E(launch_gemm(dbl, 0, 0, dim, p, dim, 1.0, Gm, dim, Z, p, 0.0, W, p, s));
-    TSK_E(launch_gemm(dbl, 1, 0, p, p, dim, 1.0, Z, p, W, p, 0.0, H, p, s));
+    TSK_E(launch_gemm(dbl, 0, 0, dim, p, dim, 1.0, Gm, dim, Z, p, 0.0, W, p, s, part,
+                      part_bytes));
+    TSK_E(launch_gemm(dbl, 1, 0, p, p, dim, 1.0, Z, p, W, p, 0.0, H, p, s, part, part_bytes));
     TSK_E(launch_sym_eig(dbl, H, p, th, V, s));
     TSK_E(launch_gemm(dbl, 0, 0, dim, p, p, 1.0, Z, p, V, p, 0.0, U, p, s));
     TSK_E(launch_gemm(dbl, 0, 0, dim, p, p, 1.0, W, p, V, p, 0.0, GU, p, s));

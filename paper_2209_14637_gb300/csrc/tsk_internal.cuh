@@ -106,10 +106,16 @@ cudaError_t launch_sketch_y(int in_type, int kp, const MatDev* mats,
 cudaError_t launch_gram(int in_type, const void* const* dA, long long D,
                         long long m, long long n, long long lda, int mode,
                         double* G, cudaStream_t s);
+// C = alpha op(A) op(B) + beta C (row-major); with a workspace of
+// work_bytes the K range is split over CTAs and summed in a second kernel.
 cudaError_t launch_gemm(bool dbl, int transA, int transB, long long M,
                         long long N, long long K, double alpha, const void* A,
                         long long lda, const void* B, long long ldb,
-                        double beta, void* C, long long ldc, cudaStream_t s);
+                        double beta, void* C, long long ldc, cudaStream_t s,
+                        void* work = nullptr, size_t work_bytes = 0);
+// Ri = R^{-1} (p x p, row stride p, upper; a zero diagonal entry gives a
+// zero row of Ri), one CTA.
+cudaError_t launch_tri_inv_upper(bool dbl, const void* R, int p, void* Ri, cudaStream_t s);
 cudaError_t launch_project_out(bool dbl, int kp, const MatDev* mats,
                                const int4* items, int nitems, const void* X,
                                const void* Y, const void* Wm, cudaStream_t s);
