@@ -1058,111 +1058,92 @@ cudaError_t launch_apply_rinv(bool dbl, const void* P, const void* R, void* Q,
   return cudaGetLastError();
 }
 
-// R (upper, p x p, row stride p) with R^T R = Gm (p x p, row stride p):
-// right-looking Cholesky in shared memory, one CTA, thread c updating column
-// c of the trailing triangle (one barrier per step).  A pivot at or below
-// 1e-12 of the largest diagonal entry makes that row of R the unit row e_j
-// (the column then passes through unchanged).
+// Ri = R^{-1} where R (upper) has R^T R = Gm (p x p, row stride p, p <= 96),
+// in one CTA of 1024 threads.  Cholesky right-looking in shared memory, the
+// trailing updates of a step spread over a 32 x 32 grid of threads, one
+// barrier per step; a pivot at or below 1e-12 of the largest diagonal entry
+// makes that row of R the unit row e_j.  Then column c of R^{-1} by back
+// substitution in the four threads 4c .. 4c + 3, each summing every fourth
+// term.  Gm and Ri may be the same array.
 template <typename T>
-__global__ void chol_upper_kernel(const T* __restrict__ Gm, int p, T* __restrict__ R) {
+__global__ void __launch_bounds__(1024)
+chol_inv_kernel(const T* Gm, int p, T* Ri) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* A = (T*)smem_raw;  // p x (p + 1)
   const int ld = p + 1, tid = threadIdx.x;
+  T* A = (T*)smem_raw;  // p x (p + 1): Gm, then R
+  T* I = A + p * ld;    // p x (p + 1): R^{-1}
+  T* dg = I + p * ld;   // p: the pivots
   for (int e = tid; e < p * p; e += blockDim.x) {
     const int a = e / p, c = e - a * p;
     A[a * ld + c] = Gm[e];
+    I[a * ld + c] = T(0);
   }
   __syncthreads();
   T mx = T(0);
   for (int a = 0; a < p; ++a) mx = A[a * ld + a] > mx ? A[a * ld + a] : mx;
   const T thr = T(1e-12) * mx;
-  __syncthreads();
-  // step j: every entry (a, c), j < a <= c, of the trailing triangle is
-  // updated by one thread from row j (which step j does not change)
+  const int ty = tid >> 5, tx = tid & 31;
   for (int j = 0; j < p; ++j) {
     const T d = A[j * ld + j];
-    const int rem = p - 1 - j;
     if (d > thr)
-      for (int e = tid; e < rem * rem; e += blockDim.x) {
-        const int a = j + 1 + e / rem, c = j + 1 + e % rem;
-        if (a <= c) A[a * ld + c] -= A[j * ld + a] * (A[j * ld + c] / d);
+      for (int c = j + 1 + tx; c < p; c += 32) {
+        const T f = A[j * ld + c] / d;
+        for (int a = j + 1 + ty; a <= c; a += 32) A[a * ld + c] -= A[j * ld + a] * f;
       }
     __syncthreads();
   }
+  for (int a = tid; a < p; a += blockDim.x) dg[a] = A[a * ld + a];
+  __syncthreads();
   for (int e = tid; e < p * p; e += blockDim.x) {
     const int a = e / p, c = e - a * p;
-    const T d = A[a * ld + a];
+    const T d = dg[a];
     T v = T(0);
     if (c >= a) v = (d > thr) ? A[a * ld + c] / sqrt(d) : (c == a ? T(1) : T(0));
-    R[e] = v;
-  }
-}
-
-// Ri = R^{-1} for the upper triangular R (p x p, row stride p): thread c
-// takes column c by back substitution, R and Ri in shared memory.
-template <typename T>
-__global__ void tri_inv_upper_kernel(const T* __restrict__ R, int p, T* __restrict__ Ri) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ld = p + 1;
-  T* Rs = (T*)smem_raw;  // p x (p + 1)
-  T* Is = Rs + p * ld;   // p x (p + 1)
-  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-    const int a = e / p, c = e - a * p;
-    Rs[a * ld + c] = R[e];
-    Is[a * ld + c] = T(0);
+    A[a * ld + c] = v;
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < p; c += blockDim.x) {
-    const T dc = Rs[c * ld + c];
-    Is[c * ld + c] = dc != T(0) ? T(1) / dc : T(0);
+  const int c = tid >> 2, q4 = tid & 3;
+  const unsigned m4 = 0xFu << (tid & 28);
+  if (c < p) {  // the column's four threads together
+    const T dc = A[c * ld + c];
+    if (q4 == 0) I[c * ld + c] = dc != T(0) ? T(1) / dc : T(0);
+    __syncwarp(m4);
     for (int i = c - 1; i >= 0; --i) {
       T t = T(0);
-      for (int q = i + 1; q <= c; ++q) t += Rs[i * ld + q] * Is[q * ld + c];
-      const T d = Rs[i * ld + i];
-      Is[i * ld + c] = d != T(0) ? -t / d : T(0);
+      for (int q = i + 1 + q4; q <= c; q += 4) t += A[i * ld + q] * I[q * ld + c];
+      t += __shfl_xor_sync(m4, t, 1);
+      t += __shfl_xor_sync(m4, t, 2);
+      const T d = A[i * ld + i];
+      if (q4 == 0) I[i * ld + c] = d != T(0) ? -t / d : T(0);
+      __syncwarp(m4);
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-    const int a = e / p, c = e - a * p;
-    Ri[e] = Is[a * ld + c];
+  for (int e = tid; e < p * p; e += blockDim.x) {
+    const int a = e / p, cc = e - a * p;
+    Ri[e] = I[a * ld + cc];
   }
 }
 
-cudaError_t launch_tri_inv_upper(bool dbl, const void* R, int p, void* Ri, cudaStream_t s) {
-  const size_t sh = (size_t)2 * p * (p + 1) * (dbl ? sizeof(double) : sizeof(float));
-  const unsigned nt = (unsigned)std::max(32, (p + 31) / 32 * 32);
+cudaError_t launch_chol_inv(bool dbl, const void* Gm, int p, void* Ri, cudaStream_t s) {
+  if (p < 1 || p > 96) return cudaErrorInvalidValue;
+  const size_t es = dbl ? sizeof(double) : sizeof(float);
+  const size_t sh = ((size_t)2 * p * (p + 1) + p) * es;
   cudaError_t e;
   if (dbl) {
-    e = cudaFuncSetAttribute(tri_inv_upper_kernel<double>,
+    e = cudaFuncSetAttribute(chol_inv_kernel<double>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     if (e != cudaSuccess) return e;
-    tri_inv_upper_kernel<double><<<1, nt, sh, s>>>((const double*)R, p, (double*)Ri);
+    chol_inv_kernel<double><<<1, 1024, sh, s>>>((const double*)Gm, p, (double*)Ri);
   } else {
-    e = cudaFuncSetAttribute(tri_inv_upper_kernel<float>,
+    e = cudaFuncSetAttribute(chol_inv_kernel<float>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     if (e != cudaSuccess) return e;
-    tri_inv_upper_kernel<float><<<1, nt, sh, s>>>((const float*)R, p, (float*)Ri);
+    chol_inv_kernel<float><<<1, 1024, sh, s>>>((const float*)Gm, p, (float*)Ri);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_chol_upper(bool dbl, const void* Gm, int p, void* R, cudaStream_t s) {
-  const size_t sh = (size_t)p * (p + 1) * (dbl ? sizeof(double) : sizeof(float));
-  cudaError_t e;
-  if (dbl) {
-    e = cudaFuncSetAttribute(chol_upper_kernel<double>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-    if (e != cudaSuccess) return e;
-    chol_upper_kernel<double><<<1, 256, sh, s>>>((const double*)Gm, p, (double*)R);
-  } else {
-    e = cudaFuncSetAttribute(chol_upper_kernel<float>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-    if (e != cudaSuccess) return e;
-    chol_upper_kernel<float><<<1, 256, sh, s>>>((const float*)Gm, p, (float*)R);
-  }
-  return cudaGetLastError();
-}
 
 // P[:, c] /= |theta_c| (theta_c != 0): a subspace-iteration block G U whose
 // columns are close to theta_c u_c becomes close to orthonormal.

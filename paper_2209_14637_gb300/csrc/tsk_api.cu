@@ -1028,8 +1028,7 @@ extern "C" tsk_status tsk_sketch_from_gram(tsk_handle h, const double* G,
     if (theta) e = launch_scale_cols(dbl, P, dim, p, theta, s);
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
       e = launch_gemm(dbl, 1, 0, p, p, dim, 1.0, P, p, P, p, 0.0, H, p, s, part, part_bytes);
-      if (e == cudaSuccess) e = launch_chol_upper(dbl, H, p, R, s);
-      if (e == cudaSuccess) e = launch_tri_inv_upper(dbl, R, p, H, s);
+      if (e == cudaSuccess) e = launch_chol_inv(dbl, H, p, H, s);
       if (e == cudaSuccess) e = launch_gemm(dbl, 0, 0, dim, p, p, 1.0, P, p, H, p, 0.0, U, p, s);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(P, U, cs * (size_t)dim * p, cudaMemcpyDeviceToDevice, s);

@@ -113,9 +113,9 @@ cudaError_t launch_gemm(bool dbl, int transA, int transB, long long M,
                         long long lda, const void* B, long long ldb,
                         double beta, void* C, long long ldc, cudaStream_t s,
                         void* work = nullptr, size_t work_bytes = 0);
-// Ri = R^{-1} (p x p, row stride p, upper; a zero diagonal entry gives a
-// zero row of Ri), one CTA.
-cudaError_t launch_tri_inv_upper(bool dbl, const void* R, int p, void* Ri, cudaStream_t s);
+// Ri = R^{-1} with R the upper Cholesky factor of Gm (R^T R = Gm), p <= 96,
+// one CTA; Gm and Ri may be the same array.
+cudaError_t launch_chol_inv(bool dbl, const void* Gm, int p, void* Ri, cudaStream_t s);
 cudaError_t launch_project_out(bool dbl, int kp, const MatDev* mats,
                                const int4* items, int nitems, const void* X,
                                const void* Y, const void* Wm, cudaStream_t s);
@@ -133,8 +133,7 @@ cudaError_t launch_random_fill(bool dbl, void* Z, long long count,
                                unsigned long long seed, cudaStream_t s);
 cudaError_t launch_apply_rinv(bool dbl, const void* P, const void* R,
                               void* Q, long long rows, int p, cudaStream_t s);
-// R^T R = Gm (p x p), R upper (one CTA); P[:, c] /= |theta_c|.
-cudaError_t launch_chol_upper(bool dbl, const void* Gm, int p, void* R, cudaStream_t s);
+// P[:, c] /= |theta_c| (theta_c != 0).
 cudaError_t launch_scale_cols(bool dbl, void* P, long long rows, int p, const void* theta,
                               cudaStream_t s);
 cudaError_t launch_ritz_residual(bool dbl, const void* U, const void* GU,
