@@ -565,11 +565,15 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
   }
   std::vector<int> fids;
   std::vector<int3> fcls;
-  // the widest class first: its CTAs run longest, so they start first
+  // the widest class first, and within a class the longest panels (m + n)
+  // first: the CTAs that run longest start first
   for (int kc = TSK_MAX_K; kc >= 8; kc -= 8) {
     const int first = (int)fids.size();
     for (int64_t i = 0; i < count; ++i)
       if (((mats[i].k + 7) & ~7) == kc) fids.push_back((int)i);
+    std::stable_sort(fids.begin() + first, fids.end(), [&](int a, int b) {
+      return mats[a].m + mats[a].n > mats[b].m + mats[b].n;
+    });
     if ((int)fids.size() > first) fcls.push_back(make_int3(kc, first, (int)fids.size() - first));
   }
   const size_t o_fids = cv.take(sizeof(int) * fids.size());
