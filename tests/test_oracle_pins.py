@@ -286,6 +286,27 @@ def test_theorem_2(rng):
         assert err2 - opt2 <= gap ** 2 * np.sum(A ** 2) + 1e-12
 
 
+def test_scw_batch_coordinate_sketch_closed_form():
+    """Problem 1.1 per matrix, in batch order.  With S = the first k rows of
+    the identity and a diagonal A, S A keeps the first k rows, so Q spans
+    e_1 .. e_k, A Q holds a_1 .. a_k on its diagonal and [A Q]_r keeps the r
+    largest of them: err^2 = ||A||^2 - (sum of the r largest a_i^2, i <= k).
+    Three matrices with different diagonals (one with its largest entries
+    outside the first k) must come back in order; an empty batch gives an
+    empty list."""
+    n, k, r = 7, 4, 2
+    diags = [np.array([5.0, 1.0, 3.0, 2.0, 0.5, 0.25, 0.1]),
+             np.array([0.2, 0.3, 0.1, 0.4, 9.0, 8.0, 7.0]),
+             np.array([1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0])]
+    S = np.eye(n)[:k]
+    errs = oracle.scw_batch([np.diag(d) for d in diags], S, r)
+    assert len(errs) == 3
+    for e, d in zip(errs, diags):
+        top = np.sort(d[:k] ** 2)[::-1][:r].sum()
+        assert e == pytest.approx(np.sqrt(np.sum(d ** 2) - top), rel=1e-12)
+    assert oracle.scw_batch([], S, r) == []
+
+
 def test_test_error_definition():
     # Eq. 4.1 on numbers checked by hand: mean of (1.1-1)/1 and (2.4-2)/2.
     assert abs(oracle.test_error([1.1, 2.4], [1.0, 2.0]) - 0.15) < 1e-15
