@@ -80,3 +80,36 @@ def test_refiner_is_never_worse_on_validation(tsk):
                     / np.sum(_np(val) ** 2, axis=(1, 2)))
     assert vloss <= hist[0] * (1 + 1e-6)
     h.close()
+
+
+def test_c5_refined_sketch_is_not_worse_on_held_out_matrices(tsk):
+    """The C5 workload as stated: 1024 x 768 FP32 matrices, k = 20, r = 10,
+    the tensor sketch trained on the 400 training matrices, then refined by
+    SGD (batch 16, lr 1e-3, 2000 steps) on 350 of them with the other 50 for
+    validation.  On 50 held-out matrices the refined sketch's test error
+    (Eq. 4.1, against the oracle's optimal rank-r errors) is not above the
+    plain tensor sketch's, and its GPU errors match the oracle's SCW with
+    the same (dense, non-orthonormal) sketch on a sample."""
+    spec = synth.C5
+    tr = synth.stream(spec, "train", device="cuda")
+    te = synth.stream(spec, "test", device="cuda")[:50]
+    h = tsk.Handle()
+    S, _, _, st = h.train_sketch(tr, spec.k)
+    assert st == 0
+    dS, hist = h.refine_sketch(tr[:350], tr[350:], S, spec.r, steps=2000, batch=16,
+                               lr=1e-3, eval_every=100)
+    assert np.isfinite(hist).all() and min(hist) <= hist[0]
+    S_ref = S + dS
+    plain = _np(h.approx_batch(te, S, spec.r)["err"])
+    ref = _np(h.approx_batch(te, S_ref, spec.r)["err"])
+    A = _np(te)
+    opt = [oracle.optimal_error(a, spec.r) for a in A]
+    e_plain = oracle.test_error(plain, opt)
+    e_ref = oracle.test_error(ref, opt)
+    print(f"\nC5 held-out test error: tensor {e_plain:.5f}, refined {e_ref:.5f}")
+    assert e_ref <= e_plain, (e_ref, e_plain)
+    Sr = _np(S_ref)
+    for i in (0, 17, 49):
+        o = oracle.scw(A[i], Sr, spec.r, dense=False)
+        assert abs(ref[i] - o["err"]) <= 1e-3 * o["err"], i
+    h.close()
