@@ -15,7 +15,8 @@
 //   1. TMA loads the CTA's MC x 64 tile (128-byte swizzle) into a stage.
 //   2. MMA-X:  D_x(c, j) = sum_i S(c, i) A(i, j) over the CTA's rows
 //      (A operand: the CTA's slice of S as BF16, K-major; B operand: the A
-//      tile read MN-major), accumulated in TMEM (M = 128 lanes, N = 64).
+//      tile read MN-major), accumulated in TMEM with M = 64 (k <= 48 rows
+//      are real; row c lands in lane 32 floor(c / 16) + c mod 16) and N = 64.
 //   3. The partial D_x rows go to their owners by st.async (bytes counted
 //      on the owner's barrier); each owner sums the C partials of its rows,
 //      rounds them to X~ = X_hi + X_lo (two BF16 terms) and a signalling
@@ -86,10 +87,10 @@ struct Lay {
   static constexpr int OFF_RECV = OFF_XB + 2 * XB_BYTES;
   static constexpr int OFF_BAR = OFF_RECV + 2 * RECV_BYTES;
   static constexpr int SMEM_BYTES = OFF_BAR + BAR_BYTES;
-  // MMA-X reads 128 rows of S per 64-row chunk although only kpad rows are
+  // MMA-X reads 64 rows of S per 64-row chunk although only kpad rows are
   // real; the extra rows (whose results are never used) must stay inside the
-  // allocation: from the last chunk they reach at most 16 KB past its start.
-  static_assert(OFF_S + (MC / 64 - 1) * KPS * 128 + 128 * 128 <= OFF_BAR,
+  // allocation: from the last chunk they reach at most 8 KB past its start.
+  static_assert(OFF_S + (MC / 64 - 1) * KPS * 128 + 64 * 128 <= OFF_BAR,
                 "S over-read leaves the shared-memory allocation");
   static_assert(MC % BOX == 0 && MC % 128 == 0, "whole boxes and MMA tiles");
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
@@ -413,10 +414,11 @@ __device__ __forceinline__ void peer_wait(uint32_t bar, uint32_t parity, const P
   }
 }
 
-// Sum of squares of one A stage (MC x 64 BF16, SB bytes), shared by 128
-// threads (t = 0..127).  Eight independent FP32 accumulators per thread,
-// each summing at most 32 squares per stage, keep the dependent chains
-// short; stages are summed in FP64.
+// Sum of squares of one A stage (MC x 64 BF16, SB bytes), shared by the 96
+// threads of the three norm warps (t = 0..95).  Eight independent FP32
+// accumulators per thread, each summing at most 43 squares per stage, keep
+// the dependent chains short; stages are summed in FP64.
+constexpr int NORM_THREADS = 96;
 template <int SB>
 __device__ __forceinline__ double stage_sumsq(const unsigned char* stage, int t) {
   const uint4* st = reinterpret_cast<const uint4*>(stage);
@@ -424,7 +426,7 @@ __device__ __forceinline__ double stage_sumsq(const unsigned char* stage, int t)
 #pragma unroll
   for (int i = 0; i < 8; ++i) a[i] = 0.f;
 #pragma unroll 4
-  for (int e = t; e < SB / 16; e += 128) {
+  for (int e = t; e < SB / 16; e += NORM_THREADS) {
     const uint4 w = st[e];
     const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -473,11 +475,11 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(bar(B_AFULL + s), 1);
-      mbar_init(bar(B_AEMPTY + s), 5);  // MMA-Y commit + four norm warps
+      mbar_init(bar(B_AEMPTY + s), 4);  // MMA-Y commit + three norm warps
     }
     for (int h = 0; h < 2; ++h) {
       mbar_init(bar(B_XFULL + h), 1);
-      mbar_init(bar(B_XTEMPTY + h), 2);
+      mbar_init(bar(B_XTEMPTY + h), 3);  // the three sending warps
       mbar_init(bar(B_RFULL + h), 1);    // own expect-tx; senders' bytes by st.async
       mbar_init(bar(B_PEMPTY + h), C);   // every owner consumed this CTA's rows
       mbar_init(bar(B_XBFULL + h), 1);   // own rows written (+ bytes from peers)
@@ -510,7 +512,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
   if (C > 1) cluster_sync();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t idesc_x = idesc_bf16(128, NB, 0, 1);
+  const uint32_t idesc_x = idesc_bf16(64, NB, 0, 1);  // M = 64 >= kpad
   const uint32_t idesc_y = idesc_bf16(128, 2 * kq, 0, 0);
 
   if (warp == 0) {
@@ -674,12 +676,16 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
       tc_commit(bar(B_DRAIN2));
       drain_wait(bar(B_DRAIN2), 0, P);
     }
-  } else if (warp >= 2 && warp <= 5) {
-    // ------- X exchange (warps 4, 5) or ||A||^2 (warps 2, 3), then Y out (all four)
-    const int lane_base = (warp & 3) * 32;
-    const bool xwarp = (warp >= 4);
+  } else if (warp >= 2 && warp <= 6) {
+    // ------- X exchange (warps 4, 5; warp 6 sends only) or ||A||^2 (warps 2,
+    // 3, with warp 7 below), then Y out (warps 2-5)
+    const int lane_base = (warp & 3) * 32;  // this warp's TMEM lane quarter
+    const bool xwarp = (warp == 4 || warp == 5);
+    const bool sendonly = (warp == 6);
     double tot = 0.0;
-    const int c = lane_base + lane;  // TMEM lane = row c of D_x / row of D_y tile
+    // row of D_x in this lane (M = 64: rows 16q .. 16q + 15 in lanes 0-15 of
+    // quarter q); lanes 16-31 hold no row
+    const int c = 16 * (warp & 3) + lane;
     long long g = 0;
     int mi = 0;
     for (int wi = w0; wi < w1; ++wi, ++mi) {
@@ -688,7 +694,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
       const long long n = md.n, m = md.m;
       const int nblk = (int)((n + NB - 1) / NB);
       for (int q = 0; q < nblk; ++q, ++g) {
-        if (!xwarp) {
+        if (!xwarp && !sendonly) {
           const int s = (int)(g % NST);
           const uint32_t u = (uint32_t)(g / NST);
           if (bwait_warp(bar(B_AFULL + s), u & 1, ctl, P))
@@ -720,7 +726,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
           tmem_wait_ld();
 #pragma unroll
           for (int j = 0; j < NB; j += 8) tmem_regs8(xr + j);
-          if (c < kq && !ctl->abort) {
+          if (lane < 16 && c < kq && !ctl->abort) {
             // rows k <= c < kq are zero in X (the S image may be narrower
             // than kq, and then its rows there are another chunk's)
             const uint32_t keep = c < md.k ? 0xFFFFFFFFu : 0u;
@@ -734,6 +740,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_XTEMPTY + h));
+        if (sendonly) continue;
         // The owner expects R rows of 256 bytes from each of the C CTAs.
         // After a timeout no bytes are sent, so the phase of RFULL can never
         // complete: a further arrive on it would take its pending count below
@@ -808,6 +815,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
         fence_proxy_async_cta();
         if (got) mbar_arrive(bar(B_XREADY + h));
       }
+      if (sendonly) continue;  // the Y epilogue belongs to warps 2-5
       if (!xwarp) {
         tot = warp_sum(tot);
         if (lane == 0) atomicAdd(P.normA2 + d, tot);
@@ -939,7 +947,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
       }
     }
   } else {
-    // ------------------------------------------------ ||A||_F^2 (warps 6, 7)
+    // ------------------------------------------------ ||A||_F^2 (warp 7)
     long long g = 0;
     for (int wi = w0; wi < w1; ++wi) {
       const int d = P.work[wi];
@@ -950,7 +958,7 @@ sketch_tc_kernel(const __grid_constant__ TcParams P) {
         const int s = (int)(g % NST);
         const uint32_t u = (uint32_t)(g / NST);
         if (bwait_warp(bar(B_AFULL + s), u & 1, ctl, P))
-          tot += stage_sumsq<STAGE_BYTES>(sm + OFF_A + s * STAGE_BYTES, tid - 128);
+          tot += stage_sumsq<STAGE_BYTES>(sm + OFF_A + s * STAGE_BYTES, tid - 224 + 64);
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_AEMPTY + s));
       }
