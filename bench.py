@@ -34,9 +34,9 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0,
 
 
 # DRAM bytes (read + write) per 2048 x 2048 BF16 matrix of the tcgen05 sketch
-# kernel with k = 40, from ncu on a 64-matrix launch (537.21 MB read, 33.06 MB
+# kernel with k = 40, from ncu on a 64-matrix launch (537.21 MB read, 33.25 MB
 # written); re-measure whenever that kernel changes.
-SKETCH_TRAFFIC_PER_MATRIX = (537.21e6 + 33.06e6) / 64
+SKETCH_TRAFFIC_PER_MATRIX = (537.21e6 + 33.25e6) / 64
 
 def load_peaks():
     try:
