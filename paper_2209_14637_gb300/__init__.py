@@ -515,4 +515,4 @@ def header_functions(path: Optional[str] = None) -> List[str]:
     path = path or os.path.join(os.path.dirname(_PKG), "include", "tsk.h")
     text = open(path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(tsk_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(tsk_[a-z0-9_]+)\s*\(", text)))
