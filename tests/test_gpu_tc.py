@@ -264,11 +264,12 @@ def test_mixed_batch_routes_by_k_and_copies_unaligned_rows(tsk):
     """A BF16 batch with rows TMA cannot move as they are (2n not a multiple
     of 16 bytes: copied to aligned rows, then the tensor-core kernel),
     aligned rows (tensor-core kernel directly) and k = 56 > 48 (CUDA-core
-    kernels), in one plan: every error, ||A||^2 and factor matches the
-    oracle, and asking for the tensor-core kernel alone is refused because
-    of the k = 56 matrix only."""
+    kernels), in one plan (217 x 181 is the MRI slice shape, below the C4
+    size range): every error, ||A||^2 and factor matches the oracle, and
+    asking for the tensor-core kernel alone is refused because of the
+    k = 56 matrix only."""
     sizes = [(300, 77, 16), (512, 200, 20), (257, 131, 10), (1024, 64, 40),
-             (129, 333, 12), (700, 520, 24), (400, 300, 56)]
+             (129, 333, 12), (700, 520, 24), (217, 181, 20), (400, 300, 56)]
     As, Ss, rs = [], [], []
     for i, (m, n, k) in enumerate(sizes):
         A, S = _case(m, n, k, 500 + i)
