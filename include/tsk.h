@@ -191,9 +191,10 @@ tsk_status tsk_gram(tsk_handle h, const void* const* A, int64_t D, int64_t m,
    power-of-two scale per row and per group of eight consecutive matrices,
    scales[(d / 8) * m + i] (device, ceil(D / 8) * m floats), the smallest
    that keeps max_{d in group, j} |A_d[i, j]| / scale <= 448, each byte is
-   E4M3(A_d[i, j] / scale) rounded to nearest.  E4M3 keeps 3 mantissa bits:
-   the stored values are within 2^-4 of A relative to each element (rounding
-   is to nearest, so the error is at most half that).  D <= 65535.
+   E4M3(A_d[i, j] / scale) rounded to nearest (ties to even).  E4M3 keeps 3
+   mantissa bits: an element with |A| >= 2^-6 scale (the normal range) is
+   stored within 2^-4 of itself, relatively; a smaller one within 2^-10 scale
+   absolutely (subnormals, and zero below 2^-10 scale).  D <= 65535.
    tsk_gram_e4m3 then forms the mode-1 Gram of the stored values,
    G (device, m x m, double) = sum_d S_d A8_d A8_d^T S_d (S_d the diagonal of
    the group's scales), on the tensor cores (tcgen05 kind::f8f6f4, CTA pairs,
