@@ -286,7 +286,7 @@ def fp8_training_gram(tsk, h, tr, G_bf16, k, peaks, peak_src):
     captured energy trace(S G S^T) (Eq. 3.2) that it keeps."""
     import torch
     D, m, n = tr.shape
-    mats = [tr[i] for i in range(D)]
+    mats = tr  # (D, m, n): the binding computes the matrices' addresses
     A8, scales = h.quantize_e4m3(mats)
     G8 = h.gram_e4m3(A8, scales, n)  # encodes and caches the tensor maps
     torch.cuda.synchronize()
@@ -350,7 +350,7 @@ def run_tsk(args):
     t0 = time.perf_counter()
     # mode-1 Gram of this rank's shard, summed over ranks (the one exchange
     # of the training side), then the leading eigenvectors on every rank
-    G = h.gram([tr[i] for i in range(tr.shape[0])], mode=1)
+    G = h.gram(tr, mode=1)
     allreduce_gram(G)
     S, eig, st = h.sketch_from_gram(G, spec.k, prec=tsk.BF16)
     torch.cuda.synchronize()
@@ -358,7 +358,7 @@ def run_tsk(args):
     # the Gram (T1) once more, timed on the device (its tensor maps are
     # cached by the handle, so this is the kernel's time): a tensor-bound
     # SYRK of m^2 n multiply-adds' worth of flops per matrix (half of 2 m^2 n)
-    mats = [tr[i] for i in range(tr.shape[0])]
+    mats = tr
     gram_ms = device_median_ms(lambda: h.gram(mats, mode=1, out=G), 3)
     gram_flops = float(spec.m) ** 2 * spec.n * (b - a)
     gram_tf = gram_flops / (gram_ms / 1e3) / 1e12
@@ -371,6 +371,19 @@ def run_tsk(args):
                                "flops": gram_flops}}
     if args.kernel != tsk.KERNEL_SIMT:
         train_info["fp8"] = fp8_training_gram(tsk, h, tr, G, spec.k, peaks, peak_src)
+        # T1' (the mode-2 Gram sum_d A_d^T A_d, n x n, Eq. 3.6) on the same
+        # matrices: the tensor-core kernel with MN-major operands
+        G2 = h.gram(mats, mode=2)
+        torch.cuda.synchronize()
+        g2_ms = device_median_ms(lambda: h.gram(mats, mode=2, out=G2), 3)
+        g2_flops = float(spec.n) ** 2 * spec.m * (b - a)
+        g2_tf = g2_flops / (g2_ms / 1e3) / 1e12
+        train_info["mode2"] = {"gram_ms": g2_ms,
+                               "roofline": {"bound": "tensor", "achieved": g2_tf, "peak": gpeak,
+                                            "unit": "TFLOP/s", "frac": g2_tf / gpeak,
+                                            "peak_source": "bf16_tflops (burst) of " + peak_src,
+                                            "flops": g2_flops}}
+        del G2
     stage(f"training Gram: {train_info}")
     del tr, G
     torch.cuda.empty_cache()

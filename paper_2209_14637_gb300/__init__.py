@@ -195,21 +195,18 @@ class Handle:
         return self._lib.tsk_sync_status(self._h, _stream(stream))
 
     # ---- training side -------------------------------------------------
-    def gram(self, As: Sequence[torch.Tensor], mode: int = 1,
-             out: Optional[torch.Tensor] = None, accumulate: bool = False,
-             stream=None) -> torch.Tensor:
-        """Mode-1 (sum A A^T) or mode-2 (sum A^T A) Gram matrix, float64."""
-        As = list(As)
-        _require_cuda(*As)
-        m, n = As[0].shape
-        prec = _DTYPE_PREC[As[0].dtype]
+    def gram(self, As, mode: int = 1, out: Optional[torch.Tensor] = None,
+             accumulate: bool = False, stream=None) -> torch.Tensor:
+        """Mode-1 (sum A A^T) or mode-2 (sum A^T A) Gram matrix, float64.
+        As: a (D, m, n) CUDA tensor (its matrices' addresses are computed,
+        not looked up one by one) or a sequence of (m, n) CUDA tensors."""
+        ptrs, D, m, n, ld, dtype, dev = _matrix_pointers(As)
+        prec = _DTYPE_PREC[dtype]
         dim = m if mode == 1 else n
         if out is None:
-            out = torch.zeros(dim, dim, dtype=torch.float64, device=As[0].device)
-        ptrs = (C.c_void_p * len(As))(*[a.data_ptr() for a in As])
-        self._check(self._lib.tsk_gram(self._h, ptrs, len(As), m, n, As[0].stride(0),
-                                       prec, mode, _ptr(out), int(accumulate),
-                                       _stream(stream)))
+            out = torch.zeros(dim, dim, dtype=torch.float64, device=dev)
+        self._check(self._lib.tsk_gram(self._h, ptrs, D, m, n, ld, prec, mode, _ptr(out),
+                                       int(accumulate), _stream(stream)))
         return out
 
     def quantize_e4m3(self, As, out=None, stream=None):
@@ -218,23 +215,20 @@ class Handle:
         shape (D, m, ld8) with ld8 = n rounded up to 16, scales float32 of
         shape (ceil(D / 8), m)); `out` = such a pair from an earlier call
         with the same shapes is written in place."""
-        mats = [As[i] for i in range(As.shape[0])] if isinstance(As, torch.Tensor) else list(As)
-        _require_cuda(*mats)
-        m, n = mats[0].shape
-        D = len(mats)
+        src, D, m, n, lda, dtype, dev = _matrix_pointers(As)
         ld8 = (n + 15) // 16 * 16
         if out is None:
-            A8 = torch.zeros(D, m, ld8, dtype=torch.uint8, device=mats[0].device)
-            scales = torch.empty((D + 7) // 8, m, dtype=torch.float32, device=mats[0].device)
+            A8 = torch.zeros(D, m, ld8, dtype=torch.uint8, device=dev)
+            scales = torch.empty((D + 7) // 8, m, dtype=torch.float32, device=dev)
         else:
             A8, scales = out
             if tuple(A8.shape) != (D, m, ld8) or tuple(scales.shape) != ((D + 7) // 8, m):
                 raise ValueError("out does not have the shapes of these matrices")
-        src = (C.c_void_p * D)(*[a.data_ptr() for a in mats])
-        dst = (C.c_void_p * D)(*[A8[d].data_ptr() for d in range(D)])
-        self._check(self._lib.tsk_quantize_e4m3(self._h, src, D, m, n, mats[0].stride(0),
-                                                _DTYPE_PREC[mats[0].dtype], dst, ld8,
-                                                _ptr(scales), _stream(stream)))
+        if not A8.is_contiguous():
+            raise ValueError("A8 must be contiguous")
+        dst, _, _, _, _, _, _ = _matrix_pointers(A8)
+        self._check(self._lib.tsk_quantize_e4m3(self._h, src, D, m, n, lda, _DTYPE_PREC[dtype],
+                                                dst, ld8, _ptr(scales), _stream(stream)))
         return A8, scales
 
     def gram_e4m3(self, A8: torch.Tensor, scales: torch.Tensor, n: int,
@@ -245,7 +239,7 @@ class Handle:
         D, m, ld8 = A8.shape
         if out is None:
             out = torch.zeros(m, m, dtype=torch.float64, device=A8.device)
-        ptrs = (C.c_void_p * D)(*[A8[d].data_ptr() for d in range(D)])
+        ptrs, _, _, _, _, _, _ = _matrix_pointers(A8)
         self._check(self._lib.tsk_gram_e4m3(self._h, ptrs, _ptr(scales), D, m, n, ld8, _ptr(out),
                                             int(accumulate), _stream(stream)))
         return out
@@ -507,6 +501,31 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def _matrix_pointers(As):
+    """(ctypes array of device pointers, D, m, n, row stride, dtype, device)
+    for a (D, m, n) CUDA tensor with unit column stride (addresses computed
+    from its strides) or a sequence of equally shaped (m, n) CUDA tensors."""
+    if isinstance(As, torch.Tensor):
+        if As.dim() != 3:
+            raise ValueError("expected a (D, m, n) tensor or a sequence of (m, n) tensors")
+        _require_cuda(As)
+        D, m, n = As.shape
+        if As.stride(2) != 1:
+            raise ValueError("the matrices' rows must be contiguous")
+        step = As.stride(0) * As.element_size()
+        base = As.data_ptr()
+        ptrs = (C.c_void_p * D)(*range(base, base + D * step, step)) if step else \
+            (C.c_void_p * D)(*([base] * D))
+        return ptrs, D, m, n, As.stride(1), As.dtype, As.device
+    mats = list(As)
+    if not mats:
+        raise ValueError("no matrices")
+    _require_cuda(*mats)
+    m, n = mats[0].shape
+    ptrs = (C.c_void_p * len(mats))(*[a.data_ptr() for a in mats])
+    return ptrs, len(mats), m, n, mats[0].stride(0), mats[0].dtype, mats[0].device
 
 
 def header_functions(path: Optional[str] = None) -> List[str]:
