@@ -116,10 +116,10 @@ typedef struct {
                          R_Y R_X^{-1}, as on the TSK_FP64 path.  Slower (the
                          Householder steps are serial); it exists to run the
                          k x k steps in FP64 where a configuration asks.     */
-  int32_t gram_tile;  /* tiles of the BF16 mode-1 Gram on the tensor cores:
-                         0 (default) 256 x 256 tiles, each on a pair of CTAs
-                         whose tensor cores work as one (M = N = 256 MMAs);
-                         1: 128 x 128 tiles on single CTAs                 */
+  int32_t gram_tile;  /* tiles of the BF16 Grams (both modes) on the tensor
+                         cores: 0 (default) 256 x 256 tiles, each on a pair
+                         of CTAs whose tensor cores work as one (M = N = 256
+                         MMAs); 1: 128 x 128 tiles on single CTAs          */
 } tsk_options;
 
 /* One test-side matrix.  A: device, m x n, leading dimension lda >= n.
@@ -175,10 +175,13 @@ tsk_status tsk_sync_status(tsk_handle h, tsk_stream stream);
    training side).  Products are accumulated in the precision's compute type
    (double for TSK_FP64, float otherwise) and summed into G in double.
    TSK_BF16 with 16-byte aligned rows (lda * 2 a multiple of 16, 16-byte
-   aligned A[d]) runs on the tensor cores (FP32 accumulation over eight
-   matrices at a time; mode 1 on 256 x 256 tiles of CTA pairs unless
-   gram_tile = 1, mode 2 on 128 x 128 tiles reading A's columns) and leaves
-   G exactly symmetric.  The tensor maps of the last training set are kept
+   aligned A[d]) runs on the tensor cores and leaves G exactly symmetric:
+   256 x 256 tiles on CTA pairs unless gram_tile = 1 (128 x 128 tiles on
+   single CTAs); mode 2 reads A's columns as MN-major operands.  Products are
+   summed in FP32 over eight matrices at a time, on the CTA pairs in chains
+   of at most 128 MMAs (K = 16 each; whole matrices) whose FP32 results are
+   added, rounded to nearest, over the eight; each eight then into G in
+   double.  The tensor maps of the last training set are kept
    in the handle, so a repeated call on the same matrices skips encoding
    them. */
 tsk_status tsk_gram(tsk_handle h, const void* const* A, int64_t D, int64_t m,

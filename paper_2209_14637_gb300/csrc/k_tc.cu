@@ -1403,12 +1403,16 @@ __global__ void __launch_bounds__(GNT, 1) gram_tc_kernel(const __grid_constant__
 // Roles: in both CTAs warp 0 issues the TMA loads of its own halves, which
 // count their bytes on the even CTA's FULL barrier (.cta_group::2 loads);
 // warp 1 of the even CTA issues the MMAs and commits them to the EMPTY and
-// TFULL barriers of both CTAs; warps 2-5 of each CTA add its 128 TMEM lanes
-// to G and arrive on the even CTA's TEMPTY barrier.
+// TFULL barriers of both CTAs; warps 2-9 of each CTA read its 128 TMEM lanes
+// into registers, arrive on the even CTA's TEMPTY barrier, and add their
+// sums into G once per group of GFL matrices.
 // ---------------------------------------------------------------------------
 struct Gram2Params {
-  const CUtensorMap* tmaps;  // one per matrix: box 128 bytes x 128 rows
-  long long D, m, n;
+  const CUtensorMap* tmaps;  // one per matrix: box 128 bytes x 128 rows (mode 1) or
+                             // 128 bytes x 64 rows (mode 2)
+  long long D, m, n;         // m: rows of G; n: the summed length (n, or m in mode 2)
+  int mode2;                 // G = sum A^T A: operands MN-major
+  int fl;                    // matrices per TMEM flush (1, 2, 4 or 8; divides GFL)
   double* G;
   const float* scales;  // FP8 operands: per group of GFL matrices, m row scales
   int ntile;   // ceil(m / 256)
@@ -1423,7 +1427,14 @@ constexpr int G2STAGE = 2 * G2HALF;     // A half, B half
 constexpr int G2_OFF_BAR = G2STG * G2STAGE;
 enum { G2_FULL = 0, G2_EMPTY = G2STG, G2_TFULL = 2 * G2STG, G2_TEMPTY = 2 * G2STG + 2,
        G2_DRAIN = 2 * G2STG + 4, G2_COUNT = 2 * G2STG + 5 };
-constexpr int G2_SMEM = G2_OFF_BAR + 256;
+// 10 warps: TMA, MMA, and eight epilogue warps; epilogue warp w holds TMEM
+// lanes 32 (w % 4) .. +31 and the tile's columns 128 ((w - 2) / 4) .. +127
+constexpr int G2NT = 320;
+// epilogue staging: each epilogue warp turns its 32 rows x 16 columns of a
+// chunk around, so that its additions to G are coalesced
+constexpr int G2_STG_LD = 17;
+constexpr int G2_OFF_STG = G2_OFF_BAR + 256;
+constexpr int G2_SMEM = G2_OFF_STG + 8 * 32 * G2_STG_LD * 4;
 static_assert(G2_COUNT * 8 + 16 <= 256, "gram2 barrier area");
 static_assert(G2_SMEM <= 227 * 1024, "gram2 shared memory");
 
@@ -1506,8 +1517,10 @@ __device__ __forceinline__ bool bwait_cluster(uint32_t bar, uint32_t parity, vol
 // F8: E4M3 operands with per-(group, row) scales applied at each flush;
 // otherwise BF16.  A stage row is 128 bytes either way: 64 BF16 or 128 E4M3
 // values of K, consumed by four MMAs of 32 bytes.
+// Ten warps put three on some of the SM's four register files of 16,384:
+// 168 registers a thread, enough for the epilogue's 128 sums and a chunk.
 template <bool F8>
-__global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant__ Gram2Params P) {
+__global__ void __launch_bounds__(G2NT, 1) gram2_tc_kernel(const __grid_constant__ Gram2Params P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw;
   const uint32_t sb = smem_u32(sm);
@@ -1539,7 +1552,11 @@ __global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant_
   const long long d1 = d1e < P.D ? d1e : P.D;
   constexpr int KB = F8 ? 128 : 64;  // K values per 128-byte stage row
   const int nkb = (int)((P.n + KB - 1) / KB);
-  const int ngroups = d1 > d0 ? (int)((d1 - d0 + GFL - 1) / GFL) : 0;
+  // flushes of P.fl matrices each: the paired MMAs' FP32 accumulation
+  // errs in one direction, so long chains of accumulations are cut short;
+  // the epilogue sums the GFL / FL flushes of a group in registers
+  const int FL = P.fl;
+  const int ngroups = d1 > d0 ? (int)((d1 - d0 + FL - 1) / FL) : 0;
   if (tid == 0) {
     for (int s = 0; s < G2STG; ++s) {
       mbar_init(bar(G2_FULL + s), 1);   // the even CTA's expect-tx; bytes of both
@@ -1547,7 +1564,7 @@ __global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant_
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(bar(G2_TFULL + b), 1);   // the pair's MMA commit
-      mbar_init(bar(G2_TEMPTY + b), 8);  // epilogue warps of both CTAs
+      mbar_init(bar(G2_TEMPTY + b), 16);  // epilogue warps of both CTAs
     }
     mbar_init(bar(G2_DRAIN), 1);
     ctl->abort = 0;
@@ -1583,8 +1600,21 @@ __global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant_
           }
           const uint32_t full = mapa(bar(G2_FULL + s), 0);
           if (lead) mbar_expect_tx(bar(G2_FULL + s), diag ? 2 * G2HALF : 2 * G2STAGE);
-          tma_load_2d_pair(sb + s * G2STAGE, map, kb * KB, rowA, full);
-          if (!diag) tma_load_2d_pair(sb + s * G2STAGE + G2HALF, map, kb * KB, rowB, full);
+          if (!P.mode2) {
+            tma_load_2d_pair(sb + s * G2STAGE, map, kb * KB, rowA, full);
+            if (!diag) tma_load_2d_pair(sb + s * G2STAGE + G2HALF, map, kb * KB, rowB, full);
+          } else {
+            // 64 rows of A (K) x this CTA's 128 columns (M or N): two 64 x 64
+            // boxes, the 128-byte swizzle atoms of an MN-major operand
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              tma_load_2d_pair(sb + s * G2STAGE + hh * (G2HALF / 2), map, rowA + hh * 64,
+                               kb * 64, full);
+              if (!diag)
+                tma_load_2d_pair(sb + s * G2STAGE + G2HALF + hh * (G2HALF / 2), map,
+                                 rowB + hh * 64, kb * 64, full);
+            }
+          }
         }
         if (stop) break;
       }
@@ -1595,7 +1625,8 @@ __global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant_
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lead && lane == 0) {
-      const uint32_t idesc = F8 ? idesc_e4m3(256, 256) : idesc_bf16(256, 256, 0, 0);
+      const uint32_t idesc = F8 ? idesc_e4m3(256, 256)
+                                : (P.mode2 ? idesc_bf16(256, 256, 1, 1) : idesc_bf16(256, 256, 0, 0));
       long long q = 0;
       bool ok = true;
       for (int grp = 0; grp < ngroups && ok; ++grp) {
@@ -1603,8 +1634,8 @@ __global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant_
         const uint32_t v = (uint32_t)(grp >> 1);
         if (!bwait_cluster(bar(G2_TEMPTY + buf), (v & 1) ^ 1, ctl, P)) break;
         tc_fence_after();
-        const long long dlo = d0 + (long long)grp * GFL;
-        const long long dhi = dlo + GFL < d1 ? dlo + GFL : d1;
+        const long long dlo = d0 + (long long)grp * FL;
+        const long long dhi = dlo + FL < d1 ? dlo + FL : d1;
         bool first = true;
         for (long long d = dlo; d < dhi && ok; ++d) {
           for (int kb = 0; kb < nkb; ++kb, ++q) {
@@ -1622,6 +1653,10 @@ __global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant_
                 tc_mma_pair_f8(tmem + buf * 256, sdesc(a0 + kk * 32, 16, 1024),
                                sdesc(b0 + kk * 32, 16, 1024), idesc,
                                (first && kk == 0) ? 0u : 1u);
+              else if (P.mode2)  // MN-major: 16 rows of K = 2 KB, the two atoms 8 KB apart
+                tc_mma_pair(tmem + buf * 256, sdesc(a0 + kk * 2048, G2HALF / 2, 1024),
+                            sdesc(b0 + kk * 2048, G2HALF / 2, 1024), idesc,
+                            (first && kk == 0) ? 0u : 1u);
               else
                 tc_mma_pair(tmem + buf * 256, sdesc(a0 + kk * 32, 16, 1024),
                             sdesc(b0 + kk * 32, 16, 1024), idesc, (first && kk == 0) ? 0u : 1u);
@@ -1636,41 +1671,35 @@ __global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant_
       drain_wait(bar(G2_DRAIN), 0, P);
     }
   } else {
-    // ------------------------------------- epilogue (warps 2-5): TMEM -> G
-    const int lane_base = (warp & 3) * 32;
-    const long long row = (long long)ti * 256 + rank * 128 + lane_base + lane;
+    // ------------------------ epilogue (warps 2-9): TMEM -> registers -> G
+    // A flush's FP32 sums are added, rounded to nearest, into registers; at
+    // the end of each group of GFL matrices (one FP8 scale group) the
+    // registers are added into G in FP64, times the group's scales for FP8.
+    const int q4 = warp & 3, hcol = (warp - 2) >> 2;
+    const long long row0 = (long long)ti * 256 + rank * 128 + q4 * 32;  // the warp's rows
+    const long long col0 = (long long)tj * 256 + hcol * 128;            // and columns
+    const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + hcol * 128;
+    float* stg = (float*)(sm + G2_OFF_STG) + (warp - 2) * 32 * G2_STG_LD;
     const bool atomic = P.splits > 1;
     const uint32_t tempty0 = lead ? 0u : mapa(bar(G2_TEMPTY), 0);
+    const int fpg = GFL / FL;  // flushes per group
+    float acc[128];
+#pragma unroll
+    for (int i = 0; i < 128; ++i) acc[i] = 0.f;
     for (int grp = 0; grp < ngroups; ++grp) {
       const int buf = grp & 1;
       const uint32_t v = (uint32_t)(grp >> 1);
       if (!bwait_warp(bar(G2_TFULL + buf), v & 1, ctl, P)) break;
       tc_fence_after();
-#pragma unroll 1
-      for (int c0 = 0; c0 < 256; c0 += 16) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
         uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)lane_base << 16) + buf * 256 + c0, r);
+        tmem_ld16(taddr + buf * 256 + c * 16, r);
         tmem_wait_ld();
         tmem_regs8(r);
         tmem_regs8(r + 8);
-        if (row < P.m) {
-          double* g = P.G + row * P.m + (long long)tj * 256 + c0;
-          const long long cmax = P.m - ((long long)tj * 256 + c0);
-          // FP8: the group's row scale times the column's (powers of two)
-          const float* sc = F8 ? P.scales + (g0 + grp) * P.m : nullptr;
-          const double srow = F8 ? (double)sc[row] : 1.0;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            if (i < cmax) {
-              double x = (double)__uint_as_float(r[i]);
-              if (F8) x *= srow * (double)sc[(long long)tj * 256 + c0 + i];
-              if (atomic)
-                atomicAdd(g + i, x);
-              else
-                g[i] += x;
-            }
-          }
-        }
+        for (int i = 0; i < 16; ++i) acc[c * 16 + i] += __uint_as_float(r[i]);
       }
       tc_fence_before();
       __syncwarp();
@@ -1679,6 +1708,40 @@ __global__ void __launch_bounds__(GNT, 1) gram2_tc_kernel(const __grid_constant_
           mbar_arrive(bar(G2_TEMPTY + buf));
         else
           mbar_arrive_remote(tempty0 + 8 * buf);
+      }
+      if ((grp + 1) % fpg != 0 && grp != ngroups - 1) continue;
+      // the group's sums into G: lane l of the turned-around chunk takes
+      // column l % 16 of rows 2 it + l / 16, so one instruction adds two
+      // runs of 16 consecutive columns
+      const float* sc = F8 ? P.scales + ((d0 + (long long)grp * FL) / GFL) * P.m : nullptr;
+      const int cc = lane & 15;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          stg[lane * G2_STG_LD + i] = acc[c * 16 + i];
+          acc[c * 16 + i] = 0.f;
+        }
+        __syncwarp();
+        const long long col = col0 + c * 16 + cc;
+        if (col < P.m) {
+          const double scol = F8 ? (double)sc[col] : 1.0;
+#pragma unroll 4
+          for (int it = 0; it < 16; ++it) {
+            const int rr = 2 * it + (lane >> 4);
+            const long long grow = row0 + rr;
+            if (grow < P.m) {
+              double x = (double)stg[rr * G2_STG_LD + cc];
+              if (F8) x *= (double)sc[grow] * scol;
+              double* gp = P.G + grow * P.m + col;
+              if (atomic)
+                atomicAdd(gp, x);
+              else
+                *gp += x;
+            }
+          }
+        }
+        __syncwarp();
       }
     }
   }
@@ -1777,8 +1840,7 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
   PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
   const bool f8 = f8_scales != nullptr;
   if (!enc || !cache || (mode != 1 && mode != 2) || (f8 && mode != 1)) return cudaErrorNotSupported;
-  if (mode == 2) pairs = false;  // the pair tiles read K-major rows only
-  if (f8) pairs = true;          // E4M3 operands: the pair kernel only
+  if (f8) pairs = true;  // E4M3 operands: the pair kernel only
   const int box_rows = mode == 1 ? 128 : 64;
   const long long dim = mode == 1 ? m : n;
   const bool hit = cache->dmaps && cache->m == m && cache->n == n && cache->lda == lda &&
@@ -1828,7 +1890,7 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
   if (pairs) {
     // 256 x 256 tiles on CTA pairs; the matrices are split over pairs so
     // that the grid fills the SMs
-    const int ntile2 = (int)((m + 255) / 256);
+    const int ntile2 = (int)((dim + 255) / 256);
     const long long ntp2 = (long long)ntile2 * (ntile2 + 1) / 2;
     if (2 * ntp2 > 2147483647ll) return cudaErrorNotSupported;
     long long splits2 = nsm / (2 * ntp2);
@@ -1839,8 +1901,20 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
     Gram2Params q;
     q.tmaps = cache->dmaps;
     q.D = D;
-    q.m = m;
-    q.n = n;
+    q.m = dim;                   // rows of G
+    q.n = mode == 1 ? n : m;     // the summed length
+    q.mode2 = mode == 2 ? 1 : 0;
+    // matrices per TMEM flush: for BF16 at most 128 MMAs of the pair
+    // accumulate into one FP32 sum before the epilogue adds it, rounded to
+    // nearest, into its registers (a stage of 64 values of K is four MMAs).
+    // E4M3 operands are rounded to 2^-4 relatively, far above what the
+    // group's chain adds: their flush is the whole group.
+    {
+      const long long nkb = (q.n + 63) / 64;
+      int fl = GFL;
+      while (!f8 && fl > 1 && (long long)fl * 4 * nkb > 128) fl >>= 1;
+      q.fl = fl;
+    }
     q.G = G;
     q.scales = f8_scales;
     q.ntile = ntile2;
@@ -1853,7 +1927,7 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute attr[1];
       cfg.gridDim = dim3((unsigned)(2 * ntp2), (unsigned)splits2, 1);
-      cfg.blockDim = dim3(GNT, 1, 1);
+      cfg.blockDim = dim3(G2NT, 1, 1);
       cfg.dynamicSmemBytes = G2_SMEM;
       cfg.stream = s;
       attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1865,8 +1939,8 @@ cudaError_t launch_gram_tc(const void* const* A, long long D, long long m, long 
       e = cudaLaunchKernelEx(&cfg, kern, q);
     }
     if (e == cudaSuccess) {
-      const long long tot = m * m;
-      mirror_upper_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(G, m);
+      const long long tot = dim * dim;
+      mirror_upper_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(G, dim);
       e = cudaGetLastError();
     }
     return e;

@@ -929,9 +929,9 @@ extern "C" tsk_status tsk_gram(tsk_handle h, const void* const* A, int64_t D,
   const int64_t dim = (mode == 1) ? m : n;
   if (!accumulate) TSK_CUDA(h, cudaMemsetAsync(G, 0, sizeof(double) * dim * dim, s));
   if (h->opts.kernel != TSK_KERNEL_SIMT && gram_tc_eligible((int)prec, mode, A, D, m, n, lda)) {
-    // BF16: tcgen05 SYRK (FP32 in TMEM, FP64 in G), mode 1 on CTA pairs
-    // (or single CTAs with gram_tile = 1), mode 2 on single CTAs; shapes
-    // whose tensor maps cannot be encoded go to the CUDA-core kernel below
+    // BF16: tcgen05 SYRK (FP32 in TMEM, FP64 in G) on CTA pairs (or single
+    // CTAs with gram_tile = 1), both modes; shapes whose tensor maps cannot
+    // be encoded go to the CUDA-core kernel below
     const cudaError_t ge =
         launch_gram_tc(A, D, m, n, lda, mode, G, h->d_status, h->opts.spin_limit,
                        h->gram_cache ? h->gram_cache : (h->gram_cache = gram_cache_create()),

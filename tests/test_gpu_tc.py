@@ -230,17 +230,20 @@ def test_tc_gram_mode1(tsk, m, n, D, tile):
     h.close()
 
 
+@pytest.mark.parametrize("tile", [0, 1])
 @pytest.mark.parametrize("m,n,D", [(200, 320, 11), (2048, 256, 20), (64, 128, 3),
                                    (72, 300, 40), (96, 2048, 3)])
-def test_tc_gram_mode2(tsk, m, n, D):
+def test_tc_gram_mode2(tsk, m, n, D, tile):
     """T1' on the tensor cores: G2 = sum A_d^T A_d (n x n) with MN-major
     operands (columns of A along M, rows along K) against the FP64 oracle
-    on the same stored values, entrywise: ragged n (partial 128-wide tiles)
-    and m (a partial 64-row K slice), splits over CTAs or not, several flush
-    groups, n = 2048 (many tiles)."""
+    on the same stored values, entrywise, on 256 x 256 tiles of CTA pairs
+    (tile 0) and 128 x 128 tiles of single CTAs (tile 1): ragged n (partial
+    tiles, pairs whose second CTA holds only columns past n) and m (a
+    partial 64-row K slice), splits over CTAs or not, several flush groups,
+    n = 2048 (many tiles)."""
     g = torch.Generator(device="cuda").manual_seed(7 * m + n + D)
     T = [torch.randn(m, n, generator=g, device="cuda").to(torch.bfloat16) for _ in range(D)]
-    h = tsk.Handle()
+    h = tsk.Handle(gram_tile=tile)
     G = _np(h.gram(T, mode=2))
     assert h.sync_status() == 0
     R = oracle.gram_mode2([_np(t) for t in T])
