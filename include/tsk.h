@@ -391,6 +391,78 @@ tsk_status tsk_refine_sketch(tsk_handle h, const tsk_mat_desc* train,
                              const tsk_refine_opts* opts, const void* S_tensor,
                              void* dS, double* history, tsk_stream stream);
 
+/* The same SGD run taken in pieces, so that it can stop and resume (with the
+   checkpoint files below in between).  The run is the one opts describes:
+   opts->steps steps in all, its batches drawn for all of them (from
+   opts->order, or from opts->seed), so step t takes the same batch whether
+   or not the run stopped before it.  This call takes steps state->step ..
+   stop - 1 (0 <= state->step <= stop <= opts->steps).
+   dS (device, k x m, in/out): the current SGD iterate, not the best one.
+   state->best (device, k x m): the best validated dS so far; state->best_loss
+   its validation loss.  With state->step == 0 the call first validates dS
+   as given and sets both (the "never worse" reference).  After the call
+   state->step is stop (or the step where an error stopped it).
+   history (host, nullable): the whole run's steps/eval_every + 1 entries;
+   the call writes only those of the validations it makes (entry t /
+   eval_every after step t, entry 0 for the starting dS).
+   tsk_refine_sketch is this call from step 0 to opts->steps followed by
+   copying best into dS.  A resumed run equals the uninterrupted one up to
+   the order of the FP64 atomic sums of ||A||^2 in the gradient (a relative
+   difference near 1e-16 per step).  Blocks until done. */
+typedef struct {
+  int32_t step;      /* SGD steps taken so far                               */
+  int32_t reserved;
+  double best_loss;  /* validation loss of best                              */
+  void* best;        /* device, k x m: the best validated dS so far          */
+} tsk_refine_state;
+
+tsk_status tsk_refine_sketch_steps(tsk_handle h, const tsk_mat_desc* train,
+                                   int64_t ntrain, const tsk_mat_desc* val,
+                                   int64_t nval, tsk_prec prec,
+                                   const tsk_refine_opts* opts,
+                                   const void* S_tensor, void* dS,
+                                   tsk_refine_state* state, int32_t stop,
+                                   double* history, tsk_stream stream);
+
+/* ---- checkpoint files (no counterpart in the paper; host only) --------- */
+
+/* Array file: the 8 bytes "TSKARR1\0", int32 precision (tsk_prec), int32 0,
+   int64 rows, int64 cols, then rows x cols elements row-major; every number
+   little-endian, whatever the host's byte order.  For S (k x m), W (l x n),
+   a refiner's dS.  tsk_array_save writes host (rows x cols elements of the
+   precision's type: double, float or BF16 bits) to path, through path.tmp
+   renamed into place when complete.  tsk_array_load reads the header into
+   *prec, *rows, *cols and, when host is non-NULL, the elements into host,
+   which must hold capacity >= rows * cols * element size bytes.  Both return
+   TSK_EINVAL (tsk_last_error(NULL) has the text) on bad arguments, a file
+   that cannot be opened or written, a header not of this format, or a file
+   shorter than its header says. */
+tsk_status tsk_array_save(const char* path, const void* host, tsk_prec prec,
+                          int64_t rows, int64_t cols);
+tsk_status tsk_array_load(const char* path, void* host, int64_t capacity,
+                          tsk_prec* prec, int64_t* rows, int64_t* cols);
+
+/* Refiner checkpoint: "TSKREF1\0", int32 precision (TSK_FP64 or TSK_FP32),
+   int32 state->step, int64 k, int64 m, double state->best_loss, double lr,
+   uint64 seed, int32 steps, int32 batch, int32 eval_every, int32 1 if the
+   run's batches came from an explicit order (else 0), then dS and best
+   (k x m each, row-major), little-endian; written through path.tmp.
+   dS_host, best_host: host copies of dS and state->best.  tsk_refine_load
+   fills *prec, *k, *m, the run's options (opts->order NULL: a run with an
+   explicit order, *order_given = 1, needs it passed again), state->step and
+   state->best_loss (state->best is left as it is: the caller copies
+   best_host to its device buffer), and, when dS_host and best_host are both
+   non-NULL, the two arrays (capacity bytes each, at least k * m elements).
+   Errors as for the array files. */
+tsk_status tsk_refine_save(const char* path, tsk_prec prec, int64_t k, int64_t m,
+                           const tsk_refine_opts* opts,
+                           const tsk_refine_state* state, const void* dS_host,
+                           const void* best_host);
+tsk_status tsk_refine_load(const char* path, tsk_prec* prec, int64_t* k,
+                           int64_t* m, tsk_refine_opts* opts,
+                           int32_t* order_given, tsk_refine_state* state,
+                           void* dS_host, void* best_host, int64_t capacity);
+
 /* ---- allocation-free SCW (no counterpart in the paper) ------------------ */
 
 /* Bytes of the static device array that tsk_approx_noalloc works in. */

@@ -72,6 +72,19 @@ class RefineOpts(C.Structure):
                 ("seed", C.c_uint64), ("order", C.POINTER(C.c_int32))]
 
 
+class _RefineStateC(C.Structure):
+    _fields_ = [("step", C.c_int32), ("reserved", C.c_int32),
+                ("best_loss", C.c_double), ("best", C.c_void_p)]
+
+
+class RefineState:
+    """Where a resumable refiner run stands: the SGD steps taken, the best
+    validated dS so far (a device tensor, k x m) and its validation loss."""
+
+    def __init__(self, best: torch.Tensor, step: int = 0, best_loss: float = 0.0):
+        self.best, self.step, self.best_loss = best, int(step), float(best_loss)
+
+
 _lib = None
 
 
@@ -120,6 +133,17 @@ def load_library(path: str = LIB_PATH):
         "tsk_default_refine_options": ([C.POINTER(RefineOpts)], None),
         "tsk_refine_sketch": ([P, C.POINTER(MatDesc), I64, C.POINTER(MatDesc), I64, I32,
                                C.POINTER(RefineOpts), P, P, C.POINTER(D), P], I32),
+        "tsk_refine_sketch_steps": ([P, C.POINTER(MatDesc), I64, C.POINTER(MatDesc), I64,
+                                     I32, C.POINTER(RefineOpts), P, P,
+                                     C.POINTER(_RefineStateC), I32, C.POINTER(D), P], I32),
+        "tsk_array_save": ([C.c_char_p, P, I32, I64, I64], I32),
+        "tsk_array_load": ([C.c_char_p, P, I64, C.POINTER(I32), C.POINTER(I64),
+                            C.POINTER(I64)], I32),
+        "tsk_refine_save": ([C.c_char_p, I32, I64, I64, C.POINTER(RefineOpts),
+                             C.POINTER(_RefineStateC), P, P], I32),
+        "tsk_refine_load": ([C.c_char_p, C.POINTER(I32), C.POINTER(I64), C.POINTER(I64),
+                             C.POINTER(RefineOpts), C.POINTER(I32),
+                             C.POINTER(_RefineStateC), P, P, I64], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -437,10 +461,8 @@ class Handle:
                                            _ptr(grad), _ptr(loss), _stream(stream)))
         return grad, float(loss.item())
 
-    def refine_sketch(self, train, val, S_tensor, r: int, steps: int = 2000,
-                      batch: int = 16, lr: float = 1e-3, eval_every: int = 100,
-                      seed: int = 20220929, order=None, dS=None, stream=None):
-        """SGD on S_theta = S_tensor + dS; returns (dS, validation history)."""
+    def _refine_args(self, train, val, S_tensor, r, steps, batch, lr, eval_every, seed,
+                     order):
         train = [train[i] for i in range(train.shape[0])] if isinstance(train, torch.Tensor) else list(train)
         val = [val[i] for i in range(val.shape[0])] if isinstance(val, torch.Tensor) else list(val)
         _require_cuda(*train, *val, S_tensor)
@@ -448,19 +470,47 @@ class Handle:
         k = S_tensor.shape[0]
         td = self._descs(train, [S_tensor] * len(train), [k] * len(train), [r] * len(train))
         vd = self._descs(val, [S_tensor] * len(val), [k] * len(val), [r] * len(val))
-        o = RefineOpts()
-        self._lib.tsk_default_refine_options(C.byref(o))
-        o.steps, o.batch, o.lr, o.eval_every, o.seed = steps, batch, lr, eval_every, seed
-        keep = None
-        if order is not None:
-            keep = (C.c_int32 * len(order))(*[int(x) for x in order])
-            o.order = C.cast(keep, C.POINTER(C.c_int32))
+        o = _refine_opts(steps, batch, lr, eval_every, seed, order)
+        return td, len(train), vd, len(val), prec, o
+
+    def refine_sketch(self, train, val, S_tensor, r: int, steps: int = 2000,
+                      batch: int = 16, lr: float = 1e-3, eval_every: int = 100,
+                      seed: int = 20220929, order=None, dS=None, stream=None):
+        """SGD on S_theta = S_tensor + dS; returns (dS, validation history)."""
+        td, nt, vd, nv, prec, o = self._refine_args(train, val, S_tensor, r, steps, batch,
+                                                    lr, eval_every, seed, order)
         dS = torch.zeros_like(S_tensor) if dS is None else dS
         hist = (C.c_double * (steps // eval_every + 1))()
-        self._check(self._lib.tsk_refine_sketch(self._h, td, len(train), vd, len(val), prec,
-                                                C.byref(o), _ptr(S_tensor), _ptr(dS), hist,
+        self._check(self._lib.tsk_refine_sketch(self._h, td, nt, vd, nv, prec, C.byref(o),
+                                                _ptr(S_tensor), _ptr(dS), hist,
                                                 _stream(stream)))
         return dS, list(hist)
+
+    def refine_sketch_steps(self, train, val, S_tensor, r: int, dS, state: RefineState,
+                            stop: int, steps: int = 2000, batch: int = 16, lr: float = 1e-3,
+                            eval_every: int = 100, seed: int = 20220929, order=None,
+                            history=None, stream=None):
+        """Steps state.step .. stop - 1 of the SGD run that the options
+        describe (the same batches whether or not the run was stopped before):
+        dS, the current iterate, is updated in place and state advanced.
+        history: the run's steps // eval_every + 1 validation losses, NaN
+        where not yet computed; the entries this call computes are filled in
+        and the list is returned."""
+        td, nt, vd, nv, prec, o = self._refine_args(train, val, S_tensor, r, steps, batch,
+                                                    lr, eval_every, seed, order)
+        _require_cuda(dS, state.best)
+        nh = steps // eval_every + 1
+        hist = list(history) if history is not None else [float("nan")] * nh
+        if len(hist) != nh:
+            raise ValueError(f"history must have {nh} entries")
+        ch = (C.c_double * nh)(*hist)
+        sc = _RefineStateC(state.step, 0, state.best_loss, state.best.data_ptr())
+        st = self._lib.tsk_refine_sketch_steps(self._h, td, nt, vd, nv, prec, C.byref(o),
+                                               _ptr(S_tensor), _ptr(dS), C.byref(sc),
+                                               int(stop), ch, _stream(stream))
+        state.step, state.best_loss = int(sc.step), float(sc.best_loss)
+        self._check(st)
+        return list(ch)
 
 
 class Plan:
@@ -526,6 +576,84 @@ def _matrix_pointers(As):
     m, n = mats[0].shape
     ptrs = (C.c_void_p * len(mats))(*[a.data_ptr() for a in mats])
     return ptrs, len(mats), m, n, mats[0].stride(0), mats[0].dtype, mats[0].device
+
+
+def _refine_opts(steps, batch, lr, eval_every, seed, order):
+    o = RefineOpts()
+    load_library().tsk_default_refine_options(C.byref(o))
+    o.steps, o.batch, o.lr, o.eval_every, o.seed = steps, batch, lr, eval_every, seed
+    if order is not None:
+        o._keep = (C.c_int32 * max(1, len(order)))(*[int(x) for x in order])
+        o.order = C.cast(o._keep, C.POINTER(C.c_int32))
+    return o
+
+
+def _check_host(st: int):
+    if st != 0:
+        raise TskError(st, load_library().tsk_last_error(None).decode())
+
+
+def save_array(path: str, t: torch.Tensor) -> None:
+    """Writes a 2-D tensor (S, W, a refiner's dS; float64, float32 or
+    bfloat16) to a tsk array file (tsk_array_save: little-endian, with a
+    header giving the precision and shape)."""
+    if t.dim() != 2 or t.dtype not in _DTYPE_PREC:
+        raise ValueError("save_array takes a 2-D float64, float32 or bfloat16 tensor")
+    h = t.detach().to("cpu").contiguous()
+    _check_host(load_library().tsk_array_save(os.fsencode(path), C.c_void_p(h.data_ptr()),
+                                              _DTYPE_PREC[h.dtype], h.shape[0], h.shape[1]))
+
+
+def load_array(path: str, device="cpu") -> torch.Tensor:
+    """Reads a tsk array file into a tensor on `device`."""
+    lib = load_library()
+    p, rows, cols = C.c_int32(), C.c_int64(), C.c_int64()
+    _check_host(lib.tsk_array_load(os.fsencode(path), None, 0, C.byref(p), C.byref(rows),
+                                   C.byref(cols)))
+    dtype = {v: k for k, v in _DTYPE_PREC.items()}[p.value]
+    h = torch.empty((rows.value, cols.value), dtype=dtype)
+    _check_host(lib.tsk_array_load(os.fsencode(path), C.c_void_p(h.data_ptr()),
+                                   h.numel() * h.element_size(), C.byref(p), C.byref(rows),
+                                   C.byref(cols)))
+    return h.to(device)
+
+
+def save_refine_checkpoint(path: str, dS: torch.Tensor, state: RefineState, steps: int,
+                           batch: int = 16, lr: float = 1e-3, eval_every: int = 100,
+                           seed: int = 20220929, order=None) -> None:
+    """Writes a resumable refiner run (tsk_refine_save): the run's options,
+    the steps taken, the current dS, the best validated dS and its loss."""
+    if dS.dtype not in (torch.float64, torch.float32) or dS.dim() != 2:
+        raise ValueError("dS must be a 2-D float64 or float32 tensor")
+    o = _refine_opts(steps, batch, lr, eval_every, seed, order)
+    d = dS.detach().to("cpu").contiguous()
+    b = state.best.detach().to("cpu", dS.dtype).contiguous()
+    sc = _RefineStateC(state.step, 0, state.best_loss, None)
+    _check_host(load_library().tsk_refine_save(
+        os.fsencode(path), _DTYPE_PREC[d.dtype], d.shape[0], d.shape[1], C.byref(o),
+        C.byref(sc), C.c_void_p(d.data_ptr()), C.c_void_p(b.data_ptr())))
+
+
+def load_refine_checkpoint(path: str, device="cuda") -> dict:
+    """Reads a refiner checkpoint: {"dS", "state" (a RefineState whose best
+    is on `device`), "steps", "batch", "lr", "eval_every", "seed",
+    "order_given"}; a run with order_given must be passed its order again."""
+    lib = load_library()
+    p, k, m, og = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
+    o, sc = RefineOpts(), _RefineStateC()
+    _check_host(lib.tsk_refine_load(os.fsencode(path), C.byref(p), C.byref(k), C.byref(m),
+                                    C.byref(o), C.byref(og), C.byref(sc), None, None, 0))
+    dtype = torch.float64 if p.value == FP64 else torch.float32
+    d = torch.empty((k.value, m.value), dtype=dtype)
+    b = torch.empty_like(d)
+    _check_host(lib.tsk_refine_load(os.fsencode(path), C.byref(p), C.byref(k), C.byref(m),
+                                    C.byref(o), C.byref(og), C.byref(sc),
+                                    C.c_void_p(d.data_ptr()), C.c_void_p(b.data_ptr()),
+                                    d.numel() * d.element_size()))
+    return {"dS": d.to(device), "state": RefineState(b.to(device), sc.step, sc.best_loss),
+            "steps": int(o.steps), "batch": int(o.batch), "lr": float(o.lr),
+            "eval_every": int(o.eval_every), "seed": int(o.seed),
+            "order_given": bool(og.value)}
 
 
 def header_functions(path: Optional[str] = None) -> List[str]:

@@ -1335,17 +1335,20 @@ extern "C" void tsk_default_refine_options(tsk_refine_opts* o) {
   o->order = nullptr;
 }
 
-extern "C" tsk_status tsk_refine_sketch(tsk_handle h, const tsk_mat_desc* train,
-                                        int64_t ntrain, const tsk_mat_desc* val, int64_t nval,
-                                        tsk_prec prec, const tsk_refine_opts* opts,
-                                        const void* S_tensor, void* dS, double* history,
-                                        tsk_stream stream) {
+extern "C" tsk_status tsk_refine_sketch_steps(tsk_handle h, const tsk_mat_desc* train,
+                                              int64_t ntrain, const tsk_mat_desc* val,
+                                              int64_t nval, tsk_prec prec,
+                                              const tsk_refine_opts* opts,
+                                              const void* S_tensor, void* dS,
+                                              tsk_refine_state* state, int32_t stop,
+                                              double* history, tsk_stream stream) {
   if (!h) return TSK_EINVAL;
   tsk_refine_opts o;
   tsk_default_refine_options(&o);
   if (opts) o = *opts;
   if (!train || ntrain < 1 || !val || nval < 1 || !S_tensor || !dS || o.steps < 0 ||
-      o.batch < 1 || o.eval_every < 1) {
+      o.batch < 1 || o.eval_every < 1 || !state || !state->best || state->step < 0 ||
+      state->step > stop || stop > o.steps) {
     set_err(h, "tsk_refine_sketch: bad arguments");
     return TSK_EINVAL;
   }
@@ -1362,7 +1365,10 @@ extern "C" tsk_status tsk_refine_sketch(tsk_handle h, const tsk_mat_desc* train,
   const size_t cs = dbl ? 8 : 4;
   const int B = o.batch;
   const long long km = (long long)train[0].k * train[0].m;
-  // batch order: the method's random draws, passed in or drawn here
+  const int t0 = state->step;
+  const int nrun = stop - t0;  // steps this call takes
+  // batch order of the whole run (the method's random draws, passed in or
+  // drawn here): step t takes its batch wherever the run was resumed
   std::vector<int32_t> order((size_t)o.steps * B);
   if (o.order) {
     for (size_t i = 0; i < order.size(); ++i) {
@@ -1383,24 +1389,25 @@ extern "C" tsk_status tsk_refine_sketch(tsk_handle h, const tsk_mat_desc* train,
   }
   GradWs g;
   TSK_CUDA(h, gradws_alloc(g, dbl, B, train[0].m, train[0].n, train[0].k, train[0].r, s));
-  // S_theta, grad, best dS, per-step descriptors, losses
+  // S_theta, grad, per-step descriptors, losses
   Carve cv;
-  const size_t o_St = cv.take(cs * km), o_gr = cv.take(cs * km), o_best = cv.take(cs * km);
-  const size_t o_desc = cv.take(sizeof(MatDev) * 2 * (size_t)std::max(1, o.steps) * B);
-  const size_t o_loss = cv.take(8 * (size_t)std::max(1, o.steps));
+  const size_t o_St = cv.take(cs * km), o_gr = cv.take(cs * km);
+  const size_t o_desc = cv.take(sizeof(MatDev) * 2 * (size_t)std::max(1, nrun) * B);
+  const size_t o_loss = cv.take(8 * (size_t)std::max(1, nrun));
   unsigned char* wb = nullptr;
   TSK_CUDA(h, cudaMallocAsync((void**)&wb, cv.off, s));
   void* St = wb + o_St;
   void* gr = wb + o_gr;
-  void* best = wb + o_best;
+  void* best = state->best;
   MatDev* dd = (MatDev*)(wb + o_desc);
   double* dloss = (double*)(wb + o_loss);
   {
-    std::vector<MatDev> all(2 * (size_t)std::max(1, o.steps) * B);
+    std::vector<MatDev> all(2 * (size_t)std::max(1, nrun) * B);
     std::vector<const tsk_mat_desc*> slots(B);
-    for (int t = 0; t < o.steps; ++t) {
-      for (int b = 0; b < B; ++b) slots[b] = &train[order[(size_t)t * B + b]];
-      gradws_descs(g, slots.data(), B, St, &all[(size_t)t * 2 * B], &all[(size_t)t * 2 * B + B]);
+    for (int i = 0; i < nrun; ++i) {
+      const size_t t = (size_t)(t0 + i);
+      for (int b = 0; b < B; ++b) slots[b] = &train[order[t * B + b]];
+      gradws_descs(g, slots.data(), B, St, &all[(size_t)i * 2 * B], &all[(size_t)i * 2 * B + B]);
     }
     TSK_CUDA(h, cudaMemcpyAsync(dd, all.data(), sizeof(MatDev) * all.size(),
                                 cudaMemcpyHostToDevice, s));
@@ -1436,18 +1443,23 @@ extern "C" tsk_status tsk_refine_sketch(tsk_handle h, const tsk_mat_desc* train,
     *out = l / nval;
     return TSK_OK;
   };
-  double best_loss = 0.0;
-  const int nhist = o.steps / o.eval_every + 1;
-  std::vector<double> hist;
-  st = validate(&best_loss);  // dS as given (zero: the plain tensor sketch)
-  if (st == TSK_OK) {
-    hist.push_back(best_loss);
-    cudaMemcpyAsync(best, dS, cs * km, cudaMemcpyDeviceToDevice, s);
+  if (t0 == 0) {
+    // the starting dS (zero: the plain tensor sketch) is the reference the
+    // result is never worse than
+    double l = 0.0;
+    st = validate(&l);
+    if (st == TSK_OK) {
+      state->best_loss = l;
+      if (history) history[0] = l;
+      cudaMemcpyAsync(best, dS, cs * km, cudaMemcpyDeviceToDevice, s);
+    }
   }
-  for (int t = 0; st == TSK_OK && t < o.steps; ++t) {
+  int t = t0;
+  for (; st == TSK_OK && t < stop; ++t) {
     cudaError_t e = launch_add(dbl, km, S_tensor, dS, St, s);
-    const MatDev* f = dd + (size_t)t * 2 * B;
-    if (e == cudaSuccess) e = gradws_run(g, (int)prec, B, f, f + B, gr, dloss + t, h->d_status, s);
+    const MatDev* f = dd + (size_t)(t - t0) * 2 * B;
+    if (e == cudaSuccess)
+      e = gradws_run(g, (int)prec, B, f, f + B, gr, dloss + (t - t0), h->d_status, s);
     if (e == cudaSuccess) e = launch_axpy(dbl, km, -o.lr, gr, dS, s);
     if (e != cudaSuccess) {
       set_err(h, "refiner step %d: %s", t, cudaGetErrorString(e));
@@ -1458,23 +1470,53 @@ extern "C" tsk_status tsk_refine_sketch(tsk_handle h, const tsk_mat_desc* train,
       double l = 0.0;
       st = validate(&l);
       if (st != TSK_OK) break;
-      hist.push_back(l);
-      if (l < best_loss) {
-        best_loss = l;
+      if (history) history[(t + 1) / o.eval_every] = l;
+      if (l < state->best_loss) {
+        state->best_loss = l;
         cudaMemcpyAsync(best, dS, cs * km, cudaMemcpyDeviceToDevice, s);
       }
     }
   }
-  // keep the best validated dS ("never worse" than the plain tensor sketch)
-  if (st == TSK_OK) cudaMemcpyAsync(dS, best, cs * km, cudaMemcpyDeviceToDevice, s);
+  state->step = t;
   cudaStreamSynchronize(s);
-  if (history) {
-    for (int i = 0; i < nhist; ++i) history[i] = i < (int)hist.size() ? hist[i] : NAN;
-  }
   plan_free(vplan);
   cudaFree(verr);
   cudaFreeAsync(wb, s);
   cudaFreeAsync(g.base, s);
+  cudaStreamSynchronize(s);
+  return st;
+}
+
+extern "C" tsk_status tsk_refine_sketch(tsk_handle h, const tsk_mat_desc* train,
+                                        int64_t ntrain, const tsk_mat_desc* val, int64_t nval,
+                                        tsk_prec prec, const tsk_refine_opts* opts,
+                                        const void* S_tensor, void* dS, double* history,
+                                        tsk_stream stream) {
+  if (!h) return TSK_EINVAL;
+  tsk_refine_opts o;
+  tsk_default_refine_options(&o);
+  if (opts) o = *opts;
+  if (!train || ntrain < 1 || !S_tensor || !dS || o.steps < 0 || o.eval_every < 1) {
+    set_err(h, "tsk_refine_sketch: bad arguments");
+    return TSK_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t cs = prec == TSK_FP64 ? 8 : 4;
+  const long long km = (long long)train[0].k * train[0].m;
+  if (km < 1) {
+    set_err(h, "tsk_refine_sketch: bad arguments");
+    return TSK_EINVAL;
+  }
+  const int nhist = o.steps / o.eval_every + 1;
+  if (history)
+    for (int i = 0; i < nhist; ++i) history[i] = NAN;
+  tsk_refine_state state{};
+  TSK_CUDA(h, cudaMallocAsync(&state.best, cs * km, s));
+  tsk_status st = tsk_refine_sketch_steps(h, train, ntrain, val, nval, prec, &o, S_tensor, dS,
+                                          &state, o.steps, history, stream);
+  // keep the best validated dS ("never worse" than the plain tensor sketch)
+  if (st == TSK_OK) cudaMemcpyAsync(dS, state.best, cs * km, cudaMemcpyDeviceToDevice, s);
+  cudaFreeAsync(state.best, s);
   cudaStreamSynchronize(s);
   return st;
 }

@@ -113,3 +113,52 @@ def test_c5_refined_sketch_is_not_worse_on_held_out_matrices(tsk):
         o = oracle.scw(A[i], Sr, spec.r, dense=False)
         assert abs(ref[i] - o["err"]) <= 1e-3 * o["err"], i
     h.close()
+
+
+def test_resumed_run_equals_the_uninterrupted_one(tsk, tmp_path):
+    """Checkpoint and resume of the refiner's SGD run: a run stopped after 20
+    of its 40 steps, written to a checkpoint file, read back and resumed
+    ends where the uninterrupted run ends -- the current dS, the best
+    validated dS, its loss and every validation loss -- up to the order of
+    the FP64 atomic sums of ||A||^2 in the gradient (1e-10 relative here);
+    the one-call refiner returns the uninterrupted run's best dS."""
+    spec, tr, te, S_o, _ = _setup(torch.float64)
+    h = tsk.Handle()
+    S_t = torch.tensor(S_o, device="cuda", dtype=torch.float64)
+    val = te[:6]
+    kw = dict(steps=40, batch=4, lr=2e-2, eval_every=10, seed=11)
+    dA = torch.zeros_like(S_t)
+    sA = tsk.RefineState(torch.empty_like(S_t))
+    hA = h.refine_sketch_steps(tr, val, S_t, spec.r, dA, sA, 40, **kw)
+    assert sA.step == 40 and not np.isnan(hA).any()
+    assert float(dA.norm()) > 0
+
+    dB = torch.zeros_like(S_t)
+    sB = tsk.RefineState(torch.empty_like(S_t))
+    hB = h.refine_sketch_steps(tr, val, S_t, spec.r, dB, sB, 20, **kw)
+    assert sB.step == 20 and np.isnan(hB[3:]).all() and not np.isnan(hB[:3]).any()
+    path = str(tmp_path / "refiner.ckpt")
+    tsk.save_refine_checkpoint(path, dB, sB, **kw)
+    c = tsk.load_refine_checkpoint(path)
+    assert c["state"].step == 20 and not c["order_given"]
+    opts = {k: c[k] for k in ("steps", "batch", "lr", "eval_every", "seed")}
+    assert opts == kw
+    hB = h.refine_sketch_steps(tr, val, S_t, spec.r, c["dS"], c["state"], 40, history=hB,
+                               **opts)
+    sB = c["state"]
+    assert sB.step == 40
+
+    def rel(a, b):
+        return float((a - b).norm() / b.norm())
+
+    assert rel(c["dS"], dA) <= 1e-10
+    assert rel(sB.best, sA.best) <= 1e-10
+    assert abs(sB.best_loss - sA.best_loss) <= 1e-10 * sA.best_loss
+    np.testing.assert_allclose(hB, hA, rtol=1e-10)
+    # the best is the minimum of the validations, the starting dS included
+    assert sA.best_loss == pytest.approx(min(hA), rel=0, abs=0)
+
+    d1, h1 = h.refine_sketch(tr, val, S_t, spec.r, **kw)
+    assert rel(d1, sA.best) <= 1e-10
+    np.testing.assert_allclose(h1, hA, rtol=1e-10)
+    h.close()

@@ -63,7 +63,7 @@ def test_partial_grams_sum_to_the_full_gram():
     rng = np.random.default_rng(0)
     As = [rng.standard_normal((12, 9)) for _ in range(7)]
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), As, out), nprocs=world, join=True)
     import oracle
@@ -111,7 +111,7 @@ def test_data_parallel_refiner_steps_match_one_process():
     S0 = np.linalg.qr(rng.standard_normal((10, 4)))[0].T
     r = 2
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_sgd_worker, args=(world, _free_port(), As, S0, r, out), nprocs=world, join=True)
     dS = np.zeros_like(S0)
