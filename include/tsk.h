@@ -193,8 +193,10 @@ tsk_status tsk_gram(tsk_handle h, const void* const* A, int64_t D, int64_t m,
    bytes in A8[d] (device, m x n, ld8 >= n bytes per row): with one
    power-of-two scale per row and per group of eight consecutive matrices,
    scales[(d / 8) * m + i] (device, ceil(D / 8) * m floats), the smallest
-   that keeps max_{d in group, j} |A_d[i, j]| / scale <= 448, each byte is
-   E4M3(A_d[i, j] / scale) rounded to nearest (ties to even).  E4M3 keeps 3
+   power of two >= 2^-149 (FP32's smallest positive value) with
+   max_{d in group, j} |A_d[i, j]| <= 448 scale (1 for a row of zeros), each
+   byte is E4M3(A_d[i, j] / scale) of the exact quotient, rounded to nearest
+   (ties to even).  E4M3 keeps 3
    mantissa bits: an element with |A| >= 2^-6 scale (the normal range) is
    stored within 2^-4 of itself, relatively; a smaller one within 2^-10 scale
    absolutely (subnormals, and zero below 2^-10 scale).  D <= 65535.

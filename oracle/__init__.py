@@ -19,6 +19,8 @@ float64 numpy, following the order and notation of the paper:
 * refiner: the IVY training loss (Eq. 2.1) of a dense sketch and its
   analytic gradient, used by the learned sketch refiner.
 * two_sided: two-sided SCW (Algorithm 3) and HOOI (Algorithm 5).
+* fp8: E4M3 copies of training matrices with per-row, per-group-of-eight
+  power-of-two scales, from the format's definition (the FP8 training Gram).
 
 Library primitives (matmul, numpy.linalg.qr/svd/eigh) serve as single steps;
 nothing is blocked, fused or reordered beyond what the paper states.  How
@@ -30,10 +32,13 @@ from .tensor_sketch import (gram_mode1, gram_mode2, leading_eigvecs,
 from .scw import scw, scw_svd_form, optimal_error, test_error, scw_batch
 from .refiner import ivy_loss, ivy_grad, scw_forward_parts
 from .two_sided import two_sided_scw, hooi
+from .fp8 import (e4m3_decode, e4m3_encode, row_scale, quantize_e4m3,
+                  dequantize_e4m3)
 
 __all__ = [
     "gram_mode1", "gram_mode2", "leading_eigvecs", "canonical_signs",
     "train_sketch", "scw", "scw_svd_form", "optimal_error", "test_error",
     "scw_batch", "ivy_loss", "ivy_grad", "scw_forward_parts",
-    "two_sided_scw", "hooi",
+    "two_sided_scw", "hooi", "e4m3_decode", "e4m3_encode", "row_scale",
+    "quantize_e4m3", "dequantize_e4m3",
 ]

@@ -2,9 +2,11 @@
 //
 // E4M3 keeps 3 mantissa bits and a largest finite value of 448.  Each row of
 // a group of eight consecutive training matrices (the matrices the Gram
-// kernel sums in one TMEM accumulator before it flushes) gets one
-// power-of-two scale s, the smallest with max |A_d[i, :]| / s <= 448 over
-// the group; the stored byte is E4M3(A_d[i, j] / s), rounded to nearest.
+// kernel sums in one accumulator before it goes to G) gets one power-of-two
+// scale s: for t = max |A_d[i, :]| over the group, the smallest s >= 2^-149
+// (FP32's smallest positive value) with t <= 448 s, and s = 1 where t = 0.
+// The stored byte is E4M3(A_d[i, j] / s), rounded to nearest even; the
+// quotient is exact (a power-of-two scaling that stays in FP32's range).
 // Since s is constant along a row and across the group,
 //
 //   sum_{d in group} A_d A_d^T  ~=  D_s (sum_{d in group} A8_d A8_d^T) D_s,
@@ -62,21 +64,27 @@ __device__ __forceinline__ uint32_t e4m3_byte(float x) {
   return (uint32_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
 }
 
+// x / s as x * inv.x * inv.y: 1 / s alone overflows FP32 for s < 2^-127,
+// so there the reciprocal is split into two powers of two; every product is
+// then exact (no intermediate leaves FP32's normal range).
+__device__ __forceinline__ uint32_t e4m3_q(float x, float2 inv) {
+  return e4m3_byte(x * inv.x * inv.y);
+}
+
 template <int V>
-__device__ __forceinline__ void e4m3_store(unsigned char* out, const float (&x)[V], float inv) {
+__device__ __forceinline__ void e4m3_store(unsigned char* out, const float (&x)[V], float2 inv) {
   if constexpr (V == 8) {
     uint2 b;
-    b.x = e4m3_byte(x[0] * inv) | e4m3_byte(x[1] * inv) << 8 | e4m3_byte(x[2] * inv) << 16 |
-          e4m3_byte(x[3] * inv) << 24;
-    b.y = e4m3_byte(x[4] * inv) | e4m3_byte(x[5] * inv) << 8 | e4m3_byte(x[6] * inv) << 16 |
-          e4m3_byte(x[7] * inv) << 24;
+    b.x = e4m3_q(x[0], inv) | e4m3_q(x[1], inv) << 8 | e4m3_q(x[2], inv) << 16 |
+          e4m3_q(x[3], inv) << 24;
+    b.y = e4m3_q(x[4], inv) | e4m3_q(x[5], inv) << 8 | e4m3_q(x[6], inv) << 16 |
+          e4m3_q(x[7], inv) << 24;
     *reinterpret_cast<uint2*>(out) = b;
   } else if constexpr (V == 4) {
-    *reinterpret_cast<uint32_t*>(out) = e4m3_byte(x[0] * inv) | e4m3_byte(x[1] * inv) << 8 |
-                                        e4m3_byte(x[2] * inv) << 16 |
-                                        e4m3_byte(x[3] * inv) << 24;
+    *reinterpret_cast<uint32_t*>(out) = e4m3_q(x[0], inv) | e4m3_q(x[1], inv) << 8 |
+                                        e4m3_q(x[2], inv) << 16 | e4m3_q(x[3], inv) << 24;
   } else {
-    out[0] = (unsigned char)e4m3_byte(x[0] * inv);
+    out[0] = (unsigned char)e4m3_q(x[0], inv);
   }
 }
 
@@ -128,14 +136,20 @@ e4m3_quant_kernel(const void* const* __restrict__ dA, long long D, long long m, 
   __syncthreads();
   float t = 0.f;
   for (int w = 0; w < 8; ++w) t = fmaxf(t, red[w]);
-  float s = 1.f;
+  // s = 2^es: with t = f 2^e, f in [0.5, 1) (exact), and 448 = 0.875 * 2^9,
+  // t <= 448 * 2^(e - 9) exactly when f <= 0.875, else 2^(e - 8) is the
+  // smallest; a zero (or non-finite) maximum keeps s = 1
+  int es = 0;
   if (t > 0.f && isfinite(t)) {
     int e = 0;
-    frexpf(t / 448.f, &e);  // t / 448 < 2^e
-    s = ldexpf(1.f, e);
+    const float f = frexpf(t, &e);
+    es = f <= 0.875f ? e - 9 : e - 8;
+    if (es < -149) es = -149;
   }
+  const float s = ldexpf(1.f, es);
   if (threadIdx.x == 0) scales[g * m + i] = s;
-  const float inv = 1.f / s;  // a power of two: exact
+  const float2 inv = es >= -126 ? make_float2(ldexpf(1.f, -es), 1.f)
+                                : make_float2(ldexpf(1.f, 64), ldexpf(1.f, -es - 64));
   unsigned char* outs[QG];
 #pragma unroll
   for (int q = 0; q < QG; ++q) outs[q] = q < nd ? dA8[d0 + q] + i * ld8 : nullptr;
@@ -158,7 +172,7 @@ e4m3_quant_kernel(const void* const* __restrict__ dA, long long D, long long m, 
 #pragma unroll
   for (int q = 0; q < QG; ++q)
     for (long long jj = nv * V + threadIdx.x; q < nd && jj < n; jj += blockDim.x)
-      outs[q][jj] = (unsigned char)e4m3_byte(e4m3_in(rows[q][jj]) * inv);
+      outs[q][jj] = (unsigned char)e4m3_q(e4m3_in(rows[q][jj]), inv);
 }
 
 }  // namespace

@@ -371,15 +371,6 @@ def test_expired_waits_report_a_timeout_and_leave_the_context_usable(tsk):
     h2.close()
 
 
-def _dequant(A8, scales, n):
-    """The values an E4M3 copy stands for: byte decoded by torch's float8
-    type, times the (group, row) scale."""
-    D, m, _ = A8.shape
-    vals = A8[:, :, :n].cpu().view(torch.float8_e4m3fn).to(torch.float64)
-    s = scales.cpu().to(torch.float64).repeat_interleave(8, dim=0)[:D]
-    return vals * s[:, :, None]
-
-
 @pytest.mark.parametrize("m,n,D,dtype,lda", [
     (320, 200, 11, torch.bfloat16, 200),   # 16-byte rows: vector loads
     (2048, 256, 20, torch.bfloat16, 256),
@@ -389,30 +380,37 @@ def _dequant(A8, scales, n):
     (64, 77, 17, torch.float32, 77),       # FP32, scalar
 ])
 def test_e4m3_quantization_and_gram(tsk, m, n, D, dtype, lda):
-    """FP8 training Gram: the quantizer's scales are the smallest powers of
-    two keeping |A| / scale <= 448 per (group of eight, row), its bytes are
-    E4M3 rounding of A / scale (torch's own conversion, bit for bit), and the
-    tensor-core Gram of the E4M3 copies (kind::f8f6f4 on CTA pairs) equals
-    the oracle's FP64 Gram of the values they stand for, entrywise."""
+    """FP8 training Gram: the quantizer's scales and bytes equal the oracle's
+    bit for bit (per (group of eight, row) the smallest power of two
+    s >= 2^-149 with max |A| <= 448 s, s = 1 for a zero row; each byte the
+    E4M3 rounding, to nearest even, of A / s).  Edge rows: maxima of exactly
+    448 (s = 1) and 896 (s = 2), a zero row, and a row at 2^-130 (s = 2^-138,
+    whose reciprocal leaves FP32's range).  The tensor-core Gram of the E4M3
+    copies (kind::f8f6f4 on CTA pairs) equals the oracle's FP64 Gram of the
+    values they stand for, entrywise."""
     g = torch.Generator(device="cuda").manual_seed(m + 3 * n + D)
     rows = torch.logspace(-3, 3, m, device="cuda")[:, None]  # rows of very unequal size
-    buf = (torch.randn(D, m, lda, generator=g, device="cuda") * rows).to(dtype)
+    buf = torch.randn(D, m, lda, generator=g, device="cuda") * rows
+    buf[:, 0] = buf[:, 0].clamp(-400, 400)
+    buf[:, 0, 0] = 448.0
+    buf[:, 1] = buf[:, 1].clamp(-800, 800)
+    buf[:, 1, n - 1] = -896.0
+    buf[:, 2] = 0.0
+    buf[:, 3] = buf[:, 3].clamp(-1.9, 1.9) * 2.0 ** -131
+    buf[:, 3, n // 2] = 2.0 ** -130
+    buf = buf.to(dtype)
     T = [buf[d, :, :n] for d in range(D)]
     h = tsk.Handle()
     A8, scales = h.quantize_e4m3(T)
     torch.cuda.synchronize()
-    sc = scales.cpu().double()
-    assert torch.all(torch.log2(sc) == torch.round(torch.log2(sc)))
-    Ad = torch.stack([t.double().cpu() for t in T])
-    for gi in range(sc.shape[0]):
-        mx = Ad[8 * gi:8 * gi + 8].abs().amax(dim=(0, 2))
-        assert torch.all(mx / sc[gi] < 448) and torch.all(mx / sc[gi] >= 224)
-    s_full = sc.repeat_interleave(8, dim=0)[:D]
-    ref = (Ad / s_full[:, :, None]).to(torch.float32).to(torch.float8_e4m3fn)
-    assert torch.equal(A8[:, :, :n].cpu(), ref.view(torch.uint8))
+    codes_o, scales_o = oracle.quantize_e4m3([t.double().cpu().numpy() for t in T])
+    assert np.array_equal(scales.cpu().double().numpy(), scales_o)
+    assert scales_o[0, 0] == 1.0 and scales_o[0, 1] == 2.0 and scales_o[0, 2] == 1.0
+    assert scales_o[0, 3] == 2.0 ** -138
+    assert np.array_equal(A8[:, :, :n].cpu().numpy(), codes_o)
     G = _np(h.gram_e4m3(A8, scales, n))
     assert h.sync_status() == 0
-    R = oracle.gram_mode1(list(_dequant(A8, scales, n).numpy()))
+    R = oracle.gram_mode1(list(oracle.dequantize_e4m3(codes_o, scales_o)))
     _gram_entrywise(G, R, 1e-5)
     assert np.array_equal(G, G.T)
     h.close()
