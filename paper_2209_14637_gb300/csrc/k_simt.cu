@@ -258,9 +258,11 @@ sketch_x_f32_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ it
     if (ch + 1 < nch) fetch((long long)(ch + 1) * BI);
 #pragma unroll 4
     for (int ii = 0; ii < BI; ++ii) {
+      // columns jg*4 .. +3 and 32 + jg*4 .. +3: the eight threads of a
+      // quarter-warp read 128 consecutive bytes, one per bank group
       float a[8], sv[CPT];
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][ii][jg * 8]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][ii][jg * 8 + 4]);
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][ii][jg * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][ii][32 + jg * 4]);
       a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
       a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
 #pragma unroll
@@ -278,7 +280,7 @@ sketch_x_f32_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ it
   float* __restrict__ Xm = X + md.offX;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const long long j = j0 + jg * 8 + q;
+    const long long j = j0 + (q < 4 ? jg * 4 + q : 32 + jg * 4 + q - 4);
     if (j < n) {
 #pragma unroll
       for (int p = 0; p < CPT; ++p) Xm[j * KP + cg * CPT + p] = acc[q][p];
@@ -294,8 +296,11 @@ template <typename Tin, int KP>
 __global__ void __launch_bounds__(128)
 sketch_y_f32_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ items,
                     const float* __restrict__ X, float* __restrict__ Y) {
-  constexpr int BI = 64, BJ = 32, CPT = KP / 16, LDT = BI + 4, XQ = BJ * KP / 4 / 128;
-  __shared__ __align__(16) float AsT[2][BJ][LDT];
+  constexpr int BI = 64, BJ = 32, CPT = KP / 16, XQ = BJ * KP / 4 / 128;
+  // A transposed: row jj holds the 64 rows ii of column jj as 16 float4
+  // slots, slot ii / 4 stored at slot (ii / 4) ^ ((jj / 4) & 7), so that the
+  // transposing stores and the float4 reads are both free of bank conflicts
+  __shared__ __align__(16) float AsT[2][BJ][BI];
   __shared__ __align__(16) float Xs[2][BJ][KP];
   const int2 it = items[blockIdx.x];
   const MatDev md = mats[it.x];
@@ -341,8 +346,9 @@ sketch_y_f32_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ it
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const int e4 = tid + 128 * t, ii = e4 >> 3, c4 = (e4 & 7) * 4;
+      const int slot = ((ii >> 2) ^ (e4 & 7)) * 4 + (ii & 3);  // (c4 + u) / 4 = e4 & 7
 #pragma unroll
-      for (int u = 0; u < 4; ++u) AsT[buf][c4 + u][ii] = va[t][u];
+      for (int u = 0; u < 4; ++u) AsT[buf][c4 + u][slot] = va[t][u];
     }
 #pragma unroll
     for (int q = 0; q < XQ; ++q) {
@@ -359,9 +365,11 @@ sketch_y_f32_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ it
     if (ch + 1 < nch) fetch((long long)(ch + 1) * BJ);
 #pragma unroll 4
     for (int jj = 0; jj < BJ; ++jj) {
+      // rows ig*4 .. +3 (slot ig) and 32 + ig*4 .. +3 (slot 8 + ig)
+      const int h = (jj >> 2) & 7;
       float a[8], xv[CPT];
-      const float4 a0 = *reinterpret_cast<const float4*>(&AsT[cur][jj][ig * 8]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&AsT[cur][jj][ig * 8 + 4]);
+      const float4 a0 = *reinterpret_cast<const float4*>(&AsT[cur][jj][(ig ^ h) * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&AsT[cur][jj][(8 + (ig ^ h)) * 4]);
       a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
       a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
 #pragma unroll
@@ -378,7 +386,7 @@ sketch_y_f32_kernel(const MatDev* __restrict__ mats, const int2* __restrict__ it
   float* __restrict__ Ym = Y + md.offY;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const long long i = i0 + ig * 8 + q;
+    const long long i = i0 + (q < 4 ? ig * 4 + q : 32 + ig * 4 + q - 4);
     if (i < m) {
 #pragma unroll
       for (int p = 0; p < CPT; ++p) Ym[i * KP + cg * CPT + p] = acc[q][p];
