@@ -17,6 +17,7 @@ than the 129 MB L2, so no flush is needed between steps).
 from __future__ import annotations
 
 import argparse
+import datetime
 import faulthandler
 import json
 import os
@@ -48,49 +49,92 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    """nvidia-smi samples of SM clock and throttle reasons around the timed
+    region, each stamped by nvidia-smi itself.
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Samples whose stamp falls inside [mark(), mark_end()] are the timed
+    region's.  A region shorter than a few sampling periods may hold none,
+    so after mark_end() the caller keeps running the same (untimed) step
+    until need_more() is false; those samples, taken with the GPU still on
+    the same work right after the region, are reported separately."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.lines = []
         self.thread = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
-        # nvidia-smi takes a moment to start: wait for its first sample, so
-        # that the samples kept (those that arrive between mark() and stop())
-        # fall inside the timed region
+        # nvidia-smi takes a moment to start: wait for its first sample
         t0 = time.time()
         while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
             time.sleep(0.01)
 
     def mark(self):
-        self.first = len(self.lines)
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    @staticmethod
+    def parse(item):
+        """(unix time, sm MHz, max sm MHz, set of active reasons) or None for
+        an (arrival time, line) pair; the time is nvidia-smi's own stamp,
+        else the line's arrival."""
+        arrived, line = item
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9:
+            return None
+        try:
+            sm, mx = float(parts[1]), float(parts[2])
+        except ValueError:
+            return None
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            ts = arrived
+        active = {nm for nm, v in zip(ClockSampler.REASONS, parts[5:9])
+                  if v.lower() == "active"}
+        return ts, sm, mx, active
+
+    def _after(self):
+        return sum(1 for ln in list(self.lines)
+                   if (p := self.parse(ln)) is not None and self.t1 is not None
+                   and p[0] > self.t1)
+
+    def need_more(self, want: int = 3, limit_s: float = 2.0) -> bool:
+        """True while fewer than `want` samples have arrived after the
+        region's end (for at most limit_s seconds)."""
+        if self.proc is None or self.t1 is None:
+            return False
+        return self._after() < want and time.time() - self.t1 < limit_s
 
     def stop(self):
         if self.proc is None:
             return None
-        last = len(self.lines)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -98,26 +142,29 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
-                 "sw_power_cap"]
-        kept = self.lines[getattr(self, "first", 0):last]
-        for ln in kept:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
+        return self.summary(self.lines, self.t0, self.t1)
+
+    @classmethod
+    def summary(cls, lines, t0, t1):
+        inside, after = [], []
+        for ln in lines:
+            p = cls.parse(ln)
+            if p is None or t0 is None or t1 is None or p[0] < t0:
                 continue
-            try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+            (inside if p[0] <= t1 else after).append(p)
+        kept = inside if inside else after
+        if not kept:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "samples": len(sm), "reasons": sorted(reasons)}
+        reasons = sorted(set().union(*[p[3] for p in kept]))
+        out = {"sm_mhz": statistics.median(p[1] for p in kept),
+               "sm_max_mhz": max(p[2] for p in kept), "reasons": reasons,
+               "samples": len(inside)}
+        if not inside:
+            out["samples_after_region"] = len(after)
+            out["window"] = (f"the timed region ({1e3 * (t1 - t0):.0f} ms) was shorter than the "
+                             f"{cls.PERIOD_MS} ms sampling period allowed for; samples taken "
+                             "right after it, the same step still running untimed")
+        return out
 
 
 def stage(msg):
@@ -416,6 +463,12 @@ def run_tsk(args):
     clocks.start()
     clocks.mark()
     total_ms, stage_ms = _timed_plan(plan, args.steps, ws, dist)
+    clocks.mark_end()
+    # untimed: the same step keeps the GPU busy until a few clock samples
+    # have landed after the region (a short region may hold none)
+    while clocks.need_more():
+        plan.execute()
+        torch.cuda.synchronize()
     clk = clocks.stop()
     assert h.sync_status() == 0
     max_ms = _max_over_ranks(total_ms, ws, dist)
