@@ -461,10 +461,17 @@ static tsk_status build_plan(tsk_handle h, int64_t count,
     return TSK_EINVAL;
   }
   int kmax = 1;
+  long long rows8 = 0, cols64 = 0;  // the largest item lists a plan launches over
   for (int64_t i = 0; i < count; ++i) {
     tsk_status st = check_desc(h, mats[i], i, prec);
     if (st != TSK_OK) return st;
     kmax = std::max(kmax, mats[i].k);
+    rows8 += (mats[i].m + 7) / 8;
+    cols64 += (mats[i].n + 63) / 64;
+  }
+  if (rows8 > 2147483647ll || cols64 > 2147483647ll) {
+    set_err(h, "batch too large for one plan (its per-block work items exceed a launch's grid)");
+    return TSK_EINVAL;
   }
   const int req = h->opts.kernel;
   // per matrix: tensor-core sketch (1) or CUDA-core sketch (0)
@@ -1540,6 +1547,7 @@ extern "C" tsk_status tsk_approx_two_sided(tsk_handle h, int64_t count,
   const bool dbl = prec == TSK_FP64;
   const size_t cs = compute_size(prec);
   int kmax = 1, lmax = 1;
+  long long rows64 = 0, cols64 = 0;  // the item lists of the sketch kernels
   for (int64_t i = 0; i < count; ++i) {
     const tsk_mat2_desc& d = mats[i];
     if (!d.A || !d.S || !d.W || d.m < 1 || d.n < 1 || d.lda < d.n || d.k < 1 || d.l < 1 ||
@@ -1556,6 +1564,13 @@ extern "C" tsk_status tsk_approx_two_sided(tsk_handle h, int64_t count,
     }
     kmax = std::max(kmax, d.k);
     lmax = std::max(lmax, d.l);
+    rows64 += (d.m + 63) / 64;
+    cols64 += (d.n + 63) / 64;
+  }
+  if (rows64 > 2147483647ll || cols64 > 2147483647ll) {
+    set_err(h, "tsk_approx_two_sided: batch too large (its per-block work items exceed a "
+               "launch's grid)");
+    return TSK_EINVAL;
   }
   const int kp = (kmax + 15) / 16 * 16, lp = (lmax + 15) / 16 * 16;
   // per-matrix descriptors: xm for X (n x kp) and Y (m x kp); zm for the
@@ -1713,6 +1728,12 @@ extern "C" tsk_status tsk_train_two_sided(tsk_handle h, const void* const* A, in
   }
   if (prec != TSK_FP64 && prec != TSK_FP32 && prec != TSK_BF16) {
     set_err(h, "tsk_train_two_sided: unknown precision");
+    return TSK_EINVAL;
+  }
+  // the sketch kernels take one CTA per (matrix, 64-wide block): D times the
+  // blocks of a matrix must fit a launch's grid
+  if (D > 2147483647ll / std::max((m + 63) / 64, (n + 63) / 64)) {
+    set_err(h, "tsk_train_two_sided: D * ceil(max(m, n) / 64) exceeds a launch's grid");
     return TSK_EINVAL;
   }
   for (int64_t d = 0; d < D; ++d)
