@@ -156,7 +156,12 @@ tsk_status tsk_destroy(tsk_handle h);
    With h == NULL, the last error of tsk_create on this thread. */
 const char* tsk_last_error(tsk_handle h);
 
-/* Fills *out with the defaults. */
+/* Fills *out with the defaults (the values noted in tsk_options).  Each
+   environment variable TSK_KERNEL, TSK_REFINE_Q, TSK_MAX_ITER, TSK_ERR_MODE,
+   TSK_EIG_TOL, TSK_SPIN_LIMIT, TSK_SMALL_FP64 and TSK_GRAM_TILE that is set
+   to a value valid for its field (an integer in the field's range; a number
+   in [0, 1] for TSK_EIG_TOL) replaces that default; others are ignored.  The
+   environment is read at every call. */
 void tsk_default_options(tsk_options* out);
 
 /* Synchronises the stream, then returns and clears the device status word:

@@ -177,18 +177,35 @@ def default_options() -> Options:
 class Handle:
     """A library handle bound to the current CUDA device."""
 
-    def __init__(self, kernel: int = KERNEL_AUTO, refine_q: int = REFINE_AUTO,
-                 max_iter: int = 300, eig_tol: float = 0.0,
-                 spin_limit: int = 1 << 24, err_mode: int = 0,
-                 small_fp64: bool = False, gram_tile: int = 0):
+    def __init__(self, kernel: Optional[int] = None, refine_q: Optional[int] = None,
+                 max_iter: Optional[int] = None, eig_tol: Optional[float] = None,
+                 spin_limit: Optional[int] = None, err_mode: Optional[int] = None,
+                 small_fp64: Optional[bool] = None, gram_tile: Optional[int] = None):
+        """Options left as None take the library's defaults
+        (tsk_default_options, which the TSK_* environment variables can
+        change): KERNEL_AUTO, REFINE_AUTO, max_iter 300, eig_tol 0 (the
+        precision's own), spin_limit 2^24, err_mode 0, small_fp64 off,
+        gram_tile 0."""
         lib = load_library()
         if not torch.cuda.is_available():
             raise RuntimeError("libtsk needs a CUDA device; none is available")
         o = default_options()
-        o.kernel, o.refine_q, o.max_iter = kernel, int(refine_q), max_iter
-        o.eig_tol, o.spin_limit, o.err_mode = eig_tol, spin_limit, err_mode
-        o.small_fp64 = int(bool(small_fp64))
-        o.gram_tile = int(gram_tile)
+        if kernel is not None:
+            o.kernel = int(kernel)
+        if refine_q is not None:
+            o.refine_q = int(refine_q)
+        if max_iter is not None:
+            o.max_iter = int(max_iter)
+        if eig_tol is not None:
+            o.eig_tol = float(eig_tol)
+        if spin_limit is not None:
+            o.spin_limit = int(spin_limit)
+        if err_mode is not None:
+            o.err_mode = int(err_mode)
+        if small_fp64 is not None:
+            o.small_fp64 = int(bool(small_fp64))
+        if gram_tile is not None:
+            o.gram_tile = int(gram_tile)
         h = C.c_void_p()
         st = lib.tsk_create(C.byref(h), C.byref(o))
         if st != 0:

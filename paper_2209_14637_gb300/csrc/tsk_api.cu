@@ -16,6 +16,34 @@
 
 #include "tsk_internal.cuh"
 
+// NVTX ranges name each entry point on a profiler's timeline (no cost when
+// no tool is attached); without the header they compile to nothing.
+#if defined(__has_include)
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define TSK_NVTX 1
+#endif
+#endif
+namespace {
+struct NvtxRange {
+  explicit NvtxRange(const char* name) {
+#ifdef TSK_NVTX
+    nvtxRangePushA(name);
+#else
+    (void)name;
+#endif
+  }
+  ~NvtxRange() {
+#ifdef TSK_NVTX
+    nvtxRangePop();
+#endif
+  }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
+#define TSK_NVTX_RANGE(name) NvtxRange tsk_nvtx_range_(name)
+
 using namespace tsk;
 
 struct tsk_plan_s {
@@ -117,6 +145,27 @@ static size_t elt_size(tsk_prec p) {
 static size_t compute_size(tsk_prec p) { return p == TSK_FP64 ? 8 : 4; }
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// An integer (or, for env_real, a number) from environment variable `name`,
+// when it is set, parses completely and lies in [lo, hi].
+static bool env_int(const char* name, long long lo, long long hi, long long* v) {
+  const char* s = getenv(name);
+  if (!s || !*s) return false;
+  char* end = nullptr;
+  const long long x = strtoll(s, &end, 10);
+  if (*end != '\0' || x < lo || x > hi) return false;
+  *v = x;
+  return true;
+}
+static bool env_real(const char* name, double lo, double hi, double* v) {
+  const char* s = getenv(name);
+  if (!s || !*s) return false;
+  char* end = nullptr;
+  const double x = strtod(s, &end);
+  if (*end != '\0' || !(x >= lo && x <= hi)) return false;
+  *v = x;
+  return true;
+}
+
 extern "C" void tsk_default_options(tsk_options* o) {
   if (!o) return;
   memset(o, 0, sizeof(*o));
@@ -128,6 +177,16 @@ extern "C" void tsk_default_options(tsk_options* o) {
   o->spin_limit = 1ll << 24;
   o->small_fp64 = 0;
   o->gram_tile = 0;
+  long long v = 0;
+  if (env_int("TSK_KERNEL", 0, 2, &v)) o->kernel = (int32_t)v;
+  if (env_int("TSK_REFINE_Q", 0, 2, &v)) o->refine_q = (int32_t)v;
+  if (env_int("TSK_MAX_ITER", 1, 1000000, &v)) o->max_iter = (int32_t)v;
+  if (env_int("TSK_ERR_MODE", 0, 2, &v)) o->err_mode = (int32_t)v;
+  if (env_int("TSK_SPIN_LIMIT", 1, 1ll << 40, &v)) o->spin_limit = v;
+  if (env_int("TSK_SMALL_FP64", 0, 1, &v)) o->small_fp64 = (int32_t)v;
+  if (env_int("TSK_GRAM_TILE", 0, 1, &v)) o->gram_tile = (int32_t)v;
+  double t = 0.0;
+  if (env_real("TSK_EIG_TOL", 0.0, 1.0, &t)) o->eig_tol = t;
 }
 
 extern "C" tsk_status tsk_create(tsk_handle* out, const tsk_options* opts) {
@@ -749,11 +808,13 @@ extern "C" tsk_status tsk_plan_create(tsk_handle h, int64_t count,
                                       const tsk_mat_desc* mats, tsk_prec prec,
                                       const tsk_mat_out* outs, double* err,
                                       double* normA2, tsk_plan* plan) {
+  TSK_NVTX_RANGE("tsk_plan_create");
   if (!h || !plan) return TSK_EINVAL;
   return build_plan(h, count, mats, prec, outs, err, normA2, plan);
 }
 
 extern "C" tsk_status tsk_plan_execute(tsk_plan p, tsk_stream stream) {
+  TSK_NVTX_RANGE("tsk_plan_execute");
   if (!p || !p->exec) return TSK_EINVAL;
   TSK_CUDA(p->h, cudaGraphLaunch(p->exec, (cudaStream_t)stream));
   return TSK_OK;
@@ -828,6 +889,7 @@ extern "C" tsk_status tsk_approx_batch(tsk_handle h, int64_t count,
                                        const tsk_mat_desc* mats, tsk_prec prec,
                                        const tsk_mat_out* outs, double* err,
                                        double* normA2, tsk_stream stream) {
+  TSK_NVTX_RANGE("tsk_approx_batch");
   if (!h) return TSK_EINVAL;
   if (count < 1 || !mats) {
     set_err(h, "count must be >= 1 and mats non-NULL");
@@ -864,6 +926,7 @@ extern "C" tsk_status tsk_error(tsk_handle h, int64_t count,
                                 const tsk_mat_desc* mats, tsk_prec prec,
                                 const tsk_mat_out* outs, double* err,
                                 tsk_stream stream) {
+  TSK_NVTX_RANGE("tsk_error");
   if (!h) return TSK_EINVAL;
   if (count < 1 || !mats || !outs || !err) {
     set_err(h, "tsk_error: count >= 1 and non-NULL mats, outs, err required");
@@ -918,6 +981,7 @@ extern "C" tsk_status tsk_gram(tsk_handle h, const void* const* A, int64_t D,
                                int64_t m, int64_t n, int64_t lda,
                                tsk_prec prec, int32_t mode, double* G,
                                int32_t accumulate, tsk_stream stream) {
+  TSK_NVTX_RANGE("tsk_gram");
   if (!h) return TSK_EINVAL;
   if (!A || !G || D < 1 || m < 1 || n < 1 || lda < n || (mode != 1 && mode != 2)) {
     set_err(h, "tsk_gram: need A, G non-NULL, D, m, n >= 1, lda >= n, mode 1 or 2");
@@ -962,6 +1026,7 @@ extern "C" tsk_status tsk_sketch_from_gram(tsk_handle h, const double* G,
                                            int64_t dim, int32_t k,
                                            tsk_prec prec, void* S, double* eig,
                                            tsk_stream stream) {
+  TSK_NVTX_RANGE("tsk_sketch_from_gram");
   if (!h) return TSK_EINVAL;
   if (!G || !S || dim < 1 || k < 1 || k > dim || k > TSK_MAX_K) {
     set_err(h, "tsk_sketch_from_gram: need G, S non-NULL and 1 <= k <= min(dim, %d)",
@@ -1108,6 +1173,7 @@ extern "C" tsk_status tsk_train_sketch(tsk_handle h, const void* const* A,
                                        int64_t lda, tsk_prec prec, int32_t k,
                                        int32_t l, void* S, void* W,
                                        double* eig, tsk_stream stream) {
+  TSK_NVTX_RANGE("tsk_train_sketch");
   if (!h) return TSK_EINVAL;
   if (k < 1 || k > std::min(m, n) || k > TSK_MAX_K || l < 0 ||
       (l > 0 && (l > std::min(m, n) || l > TSK_MAX_K || !W)) || !S) {
@@ -1304,6 +1370,7 @@ tsk_status check_refine_batch(tsk_handle h, const tsk_mat_desc* mats, int64_t co
 extern "C" tsk_status tsk_ivy_grad(tsk_handle h, int64_t count, const tsk_mat_desc* mats,
                                    tsk_prec prec, const void* S, void* grad, double* loss,
                                    tsk_stream stream) {
+  TSK_NVTX_RANGE("tsk_ivy_grad");
   if (!h) return TSK_EINVAL;
   if (count < 1 || !mats || !S || !grad) {
     set_err(h, "tsk_ivy_grad: count >= 1 and non-NULL mats, S, grad required");
@@ -1349,6 +1416,7 @@ extern "C" tsk_status tsk_refine_sketch_steps(tsk_handle h, const tsk_mat_desc* 
                                               const void* S_tensor, void* dS,
                                               tsk_refine_state* state, int32_t stop,
                                               double* history, tsk_stream stream) {
+  TSK_NVTX_RANGE("tsk_refine_sketch_steps");
   if (!h) return TSK_EINVAL;
   tsk_refine_opts o;
   tsk_default_refine_options(&o);
@@ -1535,6 +1603,7 @@ extern "C" tsk_status tsk_approx_two_sided(tsk_handle h, int64_t count,
                                            const tsk_mat2_desc* mats, tsk_prec prec,
                                            const tsk_mat_out* outs, double* err,
                                            double* normA2, tsk_stream stream) {
+  TSK_NVTX_RANGE("tsk_approx_two_sided");
   if (!h) return TSK_EINVAL;
   if (count < 1 || !mats || count > (1 << 22)) {
     set_err(h, "tsk_approx_two_sided: count >= 1 and non-NULL mats required");
@@ -1719,6 +1788,7 @@ extern "C" tsk_status tsk_train_two_sided(tsk_handle h, const void* const* A, in
                                           int32_t k, int32_t l, int32_t max_sweeps, double tol,
                                           void* S, void* W, double* core_energy,
                                           int32_t* sweeps_out, tsk_stream stream) {
+  TSK_NVTX_RANGE("tsk_train_two_sided");
   if (!h) return TSK_EINVAL;
   if (!A || D < 1 || m < 1 || n < 1 || lda < n || k < 1 || l < 1 || k > std::min(m, n) ||
       l > std::min(m, n) || k > TSK_MAX_K || l > TSK_MAX_K || !S || !W || max_sweeps < 0) {
@@ -1884,6 +1954,7 @@ extern "C" tsk_status tsk_train_two_sided(tsk_handle h, const void* const* A, in
 // ---------------------------------------------------------------------------
 extern "C" tsk_status tsk_autotune(tsk_handle h, int64_t count, const tsk_mat_desc* mats,
                                    tsk_prec prec, int32_t reps, tsk_stream stream) {
+  TSK_NVTX_RANGE("tsk_autotune");
   if (!h) return TSK_EINVAL;
   if (count < 1 || !mats || prec != TSK_BF16) {
     set_err(h, "tsk_autotune: count >= 1, non-NULL mats and TSK_BF16 required");
@@ -2049,6 +2120,7 @@ extern "C" tsk_status tsk_quantize_e4m3(tsk_handle h, const void* const* A, int6
                                         int64_t m, int64_t n, int64_t lda, tsk_prec prec,
                                         void* const* A8, int64_t ld8, float* scales,
                                         tsk_stream stream) {
+  TSK_NVTX_RANGE("tsk_quantize_e4m3");
   if (!h) return TSK_EINVAL;
   if (!A || !A8 || !scales || D < 1 || D > 65535 || m < 1 || n < 1 || lda < n || ld8 < n ||
       (prec != TSK_FP32 && prec != TSK_BF16)) {
@@ -2087,6 +2159,7 @@ extern "C" tsk_status tsk_quantize_e4m3(tsk_handle h, const void* const* A, int6
 extern "C" tsk_status tsk_gram_e4m3(tsk_handle h, const void* const* A8, const float* scales,
                                     int64_t D, int64_t m, int64_t n, int64_t ld8, double* G,
                                     int32_t accumulate, tsk_stream stream) {
+  TSK_NVTX_RANGE("tsk_gram_e4m3");
   if (!h) return TSK_EINVAL;
   if (!A8 || !scales || !G || D < 1 || m < 1 || n < 1 || ld8 < n || ld8 % 16 != 0) {
     set_err(h, "tsk_gram_e4m3: need A8, scales, G non-NULL, D, m, n >= 1, ld8 >= n and a "

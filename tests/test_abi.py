@@ -67,3 +67,25 @@ def test_struct_layouts_match_header():
     # tsk_mat2_desc: 3 pointers, 3 int64, 4 int32
     assert C.sizeof(tsk.Mat2Desc) == 3 * 8 + 3 * 8 + 4 * 4
     assert C.sizeof(tsk.Options) == 4 * 4 + 8 + 8 + 2 * 4
+
+
+def test_environment_overrides_the_default_options(lib, monkeypatch):
+    """tsk_default_options: TSK_* variables with valid values replace the
+    defaults; unset, unparsable or out-of-range ones leave them (no GPU)."""
+    names = ["TSK_KERNEL", "TSK_REFINE_Q", "TSK_MAX_ITER", "TSK_ERR_MODE", "TSK_EIG_TOL",
+             "TSK_SPIN_LIMIT", "TSK_SMALL_FP64", "TSK_GRAM_TILE"]
+    for n in names:
+        monkeypatch.delenv(n, raising=False)
+    d = tsk.default_options()
+    assert (d.kernel, d.refine_q, d.max_iter, d.err_mode, d.eig_tol, d.spin_limit,
+            d.small_fp64, d.gram_tile) == (0, 2, 300, 0, 0.0, 1 << 24, 0, 0)
+    for n, v in zip(names, ["1", "0", "50", "2", "1e-9", "4096", "1", "1"]):
+        monkeypatch.setenv(n, v)
+    o = tsk.default_options()
+    assert (o.kernel, o.refine_q, o.max_iter, o.err_mode, o.eig_tol, o.spin_limit,
+            o.small_fp64, o.gram_tile) == (1, 0, 50, 2, 1e-9, 4096, 1, 1)
+    for n, v in zip(names, ["3", "x", "0", "-1", "2.5", "12q", "7", ""]):
+        monkeypatch.setenv(n, v)
+    o = tsk.default_options()
+    assert (o.kernel, o.refine_q, o.max_iter, o.err_mode, o.eig_tol, o.spin_limit,
+            o.small_fp64, o.gram_tile) == (0, 2, 300, 0, 0.0, 1 << 24, 0, 0)
